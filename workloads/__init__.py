@@ -1,0 +1,351 @@
+"""Seeded, synthetic problem descriptions for the time-domain Casimir method.
+
+This module only *describes* geometries (grid sizes, objects, boundary kinds,
+stress contours, harmonic counts, k-points).  It holds none of the method's
+arithmetic: no field update, no basis, no g(t), no rasterisation.  Both the
+CPU oracle and the CUDA path consume the same plain dictionaries.
+
+Problem dictionary (all lengths in units of the geometry's length scale a,
+c = eps0 = mu0 = hbar = 1; the computational cell spans [0, n_a / resolution]
+along each axis a):
+
+    dims          2 or 3
+    n             [nx, ny, nz] cells (nz == 1 when dims == 2)
+    resolution    cells per unit length (Delta = 1 / resolution)
+    courant       S_c, Delta_t = S_c * Delta
+    n_steps       number of time steps T
+    sigma         uniform conductivity of the complex-frequency contour
+    background    {"eps": .., "mu": ..}
+    objects       list of {"shape": "box"|"sphere", "lo","hi" | "center","radius",
+                  "kind": "pec"|"pmc"|"dielectric"|"lorentz", "eps", "mu",
+                  "eps_inf", "delta_eps", "omega0"}; later objects win
+    bc            per axis "pec" | "pml" | "periodic"
+    pml_cells     per axis CPML thickness in cells (for "pml" axes)
+    faces         stress-surface faces {"axis", "sign", "pos", "lo", "hi"}
+    n_harm        cosine harmonics per tangential axis of every face
+    polarization  "TM" | "TE" | "TE+TM" (two-dimensional, k_z = 0) or
+                  "full" (all six source components)
+    k_points      [{"k": [kx, ky, kz], "weight": w}]
+    force_axis    0, 1 or 2
+    g_variant     "plain" | "zinv"
+    precision     "fp64" | "fp32"
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "box_faces", "plates_box_2d", "config1_plates", "config2_piston",
+    "config2_heights", "config3_waveguides", "config3_gaps", "config3_kz_points",
+    "config4_sphere_notch", "serving_requests", "piston_small",
+]
+
+
+def box_faces(lo, hi, dims):
+    """The closed axis-aligned contour around the box [lo, hi] as outward faces."""
+    faces = []
+    for a in range(dims):
+        for sign, pos in ((-1, lo[a]), (+1, hi[a])):
+            flo = list(lo) + [0.0] * (3 - len(lo))
+            fhi = list(hi) + [0.0] * (3 - len(hi))
+            flo[a] = fhi[a] = pos
+            faces.append({"axis": a, "sign": sign, "pos": float(pos),
+                          "lo": [float(v) for v in flo], "hi": [float(v) for v in fhi]})
+    return faces
+
+
+def _base(dims, n, resolution, n_steps, sigma=1.0, courant=0.5):
+    return {
+        "dims": dims, "n": list(n), "resolution": float(resolution),
+        "courant": float(courant), "n_steps": int(n_steps), "sigma": float(sigma),
+        "background": {"eps": 1.0, "mu": 1.0}, "objects": [],
+        "bc": ["pec", "pec", "pec"], "pml_cells": [0, 0, 0], "faces": [],
+        "n_harm": 1, "polarization": "TM",
+        "k_points": [{"k": [0.0, 0.0, 0.0], "weight": 1.0}],
+        "force_axis": 0, "g_variant": "plain", "precision": "fp64",
+    }
+
+
+def plates_box_2d(resolution, width, *, lines=("inner",), n_harm=None, polarization="TM",
+                  n_steps=None, t_max=None, sigma=1.0, g_variant="plain",
+                  courant=0.5, fill_eps=1.0):
+    """Two thin PEC plates at y = 0.5 and y = 1.5 inside a width x 2 PEC box.
+
+    The inner cavity (separation 1) and the upper outer cavity (separation 0.5)
+    each get a wall-to-wall stress line through their middle (y = 1.0 and
+    y = 1.75).  With both lines, oriented away from the upper plate, the
+    contour is closed through the PEC sidewalls around that plate.
+    """
+    nx = int(round(width * resolution))
+    ny = int(round(2 * resolution))
+    if n_steps is None:
+        t_max = 100.0 if t_max is None else t_max
+        n_steps = int(round(t_max / (courant / resolution)))
+    p = _base(2, (nx, ny, 1), resolution, n_steps, sigma=sigma, courant=courant)
+    p["background"] = {"eps": float(fill_eps), "mu": 1.0}
+    p["objects"] = [
+        {"shape": "box", "lo": [0.0, 0.5, 0.0], "hi": [float(width), 0.5, 0.0], "kind": "pec"},
+        {"shape": "box", "lo": [0.0, 1.5, 0.0], "hi": [float(width), 1.5, 0.0], "kind": "pec"},
+    ]
+    faces = []
+    for which in lines:
+        if which == "inner":        # below the upper plate: outward normal -y
+            faces.append({"axis": 1, "sign": -1, "pos": 1.0, "lo": [0.0, 1.0, 0.0],
+                          "hi": [float(width), 1.0, 0.0]})
+        elif which == "inner_up":   # the same line with normal +y (open line)
+            faces.append({"axis": 1, "sign": +1, "pos": 1.0, "lo": [0.0, 1.0, 0.0],
+                          "hi": [float(width), 1.0, 0.0]})
+        elif which == "outer":      # above the upper plate: outward normal +y
+            faces.append({"axis": 1, "sign": +1, "pos": 1.75, "lo": [0.0, 1.75, 0.0],
+                          "hi": [float(width), 1.75, 0.0]})
+        else:
+            raise ValueError(which)
+    p["faces"] = faces
+    p["n_harm"] = int(nx if n_harm is None else n_harm)
+    p["polarization"] = polarization
+    p["force_axis"] = 1
+    p["g_variant"] = g_variant
+    return p
+
+
+def config1_plates():
+    """2D k_z = 0 TM plates: 3 x 2 PEC box, plates at y = 0.5 and 1.5, resolution 20,
+    open midway line y = 1 with cosine harmonics n = 0..7, Courant 0.5, 4000 steps, FP64."""
+    p = plates_box_2d(20, 3.0, lines=("inner_up",), n_harm=8, polarization="TM", n_steps=4000)
+    p["precision"] = "fp64"
+    return p
+
+
+def config2_heights():
+    """Sidewall half-gaps h: 8 evenly spaced values in [0.5, 3], snapped to 1/40."""
+    return [round(40.0 * (0.5 + j * 2.5 / 7.0)) / 40.0 for j in range(8)]
+
+
+def config2_piston(h, *, resolution=40, n_harm=40, n_steps=20000, polarization="TE+TM",
+                   precision="fp32", g_variant="zinv"):
+    """Two 1 x 1 PEC blocks (gap 1 along x) between PEC sidewalls at y = +-(1/2 + h).
+
+    Cell: x in [0, 10] (PEC ends at x = +-5 about the centre), y in [0, 1 + 2h].
+    Stress contour: the rectangle one pixel outside the right block; force along x.
+    """
+    d = 1.0 / resolution
+    nx = int(round(10 * resolution))
+    ny = int(round((1 + 2 * h) * resolution))
+    p = _base(2, (nx, ny, 1), resolution, n_steps)
+    yc = 0.5 + h
+    p["objects"] = [
+        {"shape": "box", "lo": [3.5, yc - 0.5, 0.0], "hi": [4.5, yc + 0.5, 0.0], "kind": "pec"},
+        {"shape": "box", "lo": [5.5, yc - 0.5, 0.0], "hi": [6.5, yc + 0.5, 0.0], "kind": "pec"},
+    ]
+    p["faces"] = box_faces([5.5 - d, yc - 0.5 - d], [6.5 + d, yc + 0.5 + d], 2)
+    p["n_harm"] = n_harm
+    p["polarization"] = polarization
+    p["force_axis"] = 0
+    p["g_variant"] = g_variant
+    p["precision"] = precision
+    return p
+
+
+def piston_small(h=0.5, *, resolution=10, n_harm=6, n_steps=600, polarization="TE+TM",
+                 precision="fp32", g_variant="zinv", block_offset=0.0):
+    """A coarse version of the piston geometry (parity-test size)."""
+    d = 1.0 / resolution
+    nx = int(round(6 * resolution))
+    ny = int(round((1 + 2 * h) * resolution))
+    p = _base(2, (nx, ny, 1), resolution, n_steps)
+    yc = 0.5 + h
+    p["objects"] = [
+        {"shape": "box", "lo": [1.5 + block_offset, yc - 0.5, 0.0], "hi": [2.5 + block_offset, yc + 0.5, 0.0], "kind": "pec"},
+        {"shape": "box", "lo": [3.5, yc - 0.5, 0.0], "hi": [4.5, yc + 0.5, 0.0], "kind": "pec"},
+    ]
+    p["faces"] = box_faces([3.5 - d, yc - 0.5 - d], [4.5 + d, yc + 0.5 + d], 2)
+    p["n_harm"] = n_harm
+    p["polarization"] = polarization
+    p["force_axis"] = 0
+    p["g_variant"] = g_variant
+    p["precision"] = precision
+    return p
+
+
+def config3_gaps():
+    """Waveguide gaps 0.3 .. 1.0 in steps of 0.1, snapped to 1/16 (two cells at resolution 32)."""
+    return [round(16.0 * (0.3 + 0.1 * j)) / 16.0 for j in range(8)]
+
+
+def config3_kz_points(gap, n=32):
+    """Gauss-Legendre nodes on u in (-1, 1) mapped to k_z = c (1+u)/(1-u), c = 1/gap.
+
+    The weight includes the Jacobian 2c/(1-u)^2 and the 1/pi of the k_z measure.
+    """
+    u, w = np.polynomial.legendre.leggauss(n)
+    c = 1.0 / gap
+    out = []
+    for ui, wi in zip(u, w):
+        k = c * (1 + ui) / (1 - ui)
+        jac = 2 * c / (1 - ui) ** 2
+        out.append({"k": [0.0, 0.0, float(k)], "weight": float(wi * jac / math.pi)})
+    return out
+
+
+def config3_waveguides(gap, *, resolution=32, n_cells=256, pml_units=1.0, n_harm=30,
+                       n_steps=3840, k_points=None, precision="fp32"):
+    """Two suspended single-Lorentz-pole waveguides (1 wide along x, 0.5 tall) in vacuum,
+    CPML on all four sides; force along x on the right waveguide."""
+    d = 1.0 / resolution
+    L = n_cells * d
+    p = _base(2, (n_cells, n_cells, 1), resolution, n_steps)
+    xc, yc = L / 2, L / 2
+    mat = {"kind": "lorentz", "eps_inf": 1.0, "delta_eps": 10.7, "omega0": 3.0}
+    p["objects"] = [
+        dict(shape="box", lo=[xc - gap / 2 - 1.0, yc - 0.25, 0.0], hi=[xc - gap / 2, yc + 0.25, 0.0], **mat),
+        dict(shape="box", lo=[xc + gap / 2, yc - 0.25, 0.0], hi=[xc + gap / 2 + 1.0, yc + 0.25, 0.0], **mat),
+    ]
+    p["bc"] = ["pml", "pml", "pec"]
+    pc = int(round(pml_units * resolution))
+    p["pml_cells"] = [pc, pc, 0]
+    p["faces"] = box_faces([xc + gap / 2 - d, yc - 0.25 - d], [xc + gap / 2 + 1.0 + d, yc + 0.25 + d], 2)
+    p["n_harm"] = n_harm
+    p["polarization"] = "full"
+    p["k_points"] = config3_kz_points(gap) if k_points is None else k_points
+    p["force_axis"] = 0
+    p["g_variant"] = "plain"
+    p["precision"] = precision
+    return p
+
+
+def config4_sphere_notch(height, *, seed=0, resolution=40, n_cells=160, pml_cells=12,
+                         n_harm=6, n_steps=3200, precision="fp32", substrate_top=1.0):
+    """Dielectric sphere (r = 0.5, eps 2.1) above an indented PEC substrate in a fluid
+    (eps 1.8): a flat PEC plane with a 1.0-wide, 0.5-deep square notch whose centre is
+    offset laterally by a seeded dx in [0, 0.2]; cubic stress surface around the sphere,
+    force along z."""
+    rng = np.random.default_rng(seed)
+    dx_off = float(rng.uniform(0.0, 0.2))
+    d = 1.0 / resolution
+    L = n_cells * d
+    p = _base(3, (n_cells, n_cells, n_cells), resolution, n_steps)
+    p["background"] = {"eps": 1.8, "mu": 1.0}
+    cx = cy = L / 2
+    zs = substrate_top
+    r = 0.5
+    cz = zs + height + r
+    nx0 = cx + dx_off
+    p["objects"] = [
+        {"shape": "box", "lo": [0.0, 0.0, 0.0], "hi": [L, L, zs], "kind": "pec"},
+        {"shape": "box", "lo": [nx0 - 0.5, cy - 0.5, zs - 0.5], "hi": [nx0 + 0.5, cy + 0.5, zs + 1e-9],
+         "kind": "dielectric", "eps": 1.8, "mu": 1.0},
+        {"shape": "sphere", "center": [cx, cy, cz], "radius": r, "kind": "dielectric", "eps": 2.1, "mu": 1.0},
+    ]
+    p["bc"] = ["pml", "pml", "pml"]
+    p["pml_cells"] = [pml_cells] * 3
+    h = r + 2 * d
+    lo = [round((cx - h) * resolution) * d, round((cy - h) * resolution) * d, round((cz - h) * resolution) * d]
+    hi = [lo[0] + 2 * h, lo[1] + 2 * h, lo[2] + 2 * h]
+    p["faces"] = box_faces(lo, hi, 3)
+    p["n_harm"] = n_harm
+    p["polarization"] = "full"
+    p["force_axis"] = 2
+    p["g_variant"] = "plain"
+    p["precision"] = precision
+    p["meta"] = {"dx": dx_off}
+    return p
+
+
+def serving_requests(seed, n_requests=200, rate=50.0, *, scale=1.0):
+    """Poisson arrivals (mean `rate` per second) of force requests drawn from `seed`.
+
+    Mix: 60% 2D piston / waveguide grids (side 64..512, 10..60 harmonics), 30% periodic
+    grooved-membrane cells 128 x 512 with 16 Bloch k_x points, 10% 3D sphere-substrate
+    grids (side 64..128).  `scale` < 1 shrinks every grid side (for tests).
+    Returns a list of (arrival_time_s, problem_dict).
+    """
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n_requests):
+        t += float(rng.exponential(1.0 / rate))
+        u = float(rng.uniform())
+        if u < 0.6:
+            side = int(rng.integers(64, 513))
+            side = max(16, int(round(side * scale)) // 4 * 4)
+            nh = int(rng.integers(10, 61))
+            prob = _serving_piston(side, nh, rng)
+        elif u < 0.9:
+            prob = _serving_grating(scale, rng)
+        else:
+            side = int(rng.integers(64, 129))
+            side = max(16, int(round(side * scale)) // 4 * 4)
+            prob = _serving_sphere(side, rng)
+        out.append((t, prob))
+    return out
+
+
+def _serving_piston(side, n_harm, rng):
+    res = side / 8.0
+    d = 1.0 / res
+    p = _base(2, (side, side, 1), res, int(round(40.0 / (0.5 * d))))
+    h = float(rng.uniform(0.5, 2.5))
+    yc = 4.0
+    p["objects"] = [
+        {"shape": "box", "lo": [0.0, yc - 0.5 - h, 0.0], "hi": [8.0, yc - 0.5 - h, 0.0], "kind": "pec"},
+        {"shape": "box", "lo": [0.0, yc + 0.5 + h, 0.0], "hi": [8.0, yc + 0.5 + h, 0.0], "kind": "pec"},
+        {"shape": "box", "lo": [2.5, yc - 0.5, 0.0], "hi": [3.5, yc + 0.5, 0.0], "kind": "pec"},
+        {"shape": "box", "lo": [4.5, yc - 0.5, 0.0], "hi": [5.5, yc + 0.5, 0.0], "kind": "pec"},
+    ]
+    lo = [round((4.5) * res - 1) * d, round((yc - 0.5) * res - 1) * d]
+    hi = [round((5.5) * res + 1) * d, round((yc + 0.5) * res + 1) * d]
+    p["faces"] = box_faces(lo, hi, 2)
+    nmax = int(round((hi[1] - lo[1]) * res))
+    p["n_harm"] = int(min(n_harm, nmax))
+    p["polarization"] = "TE+TM"
+    p["force_axis"] = 0
+    p["g_variant"] = "zinv"
+    p["precision"] = "fp32"
+    p["kind"] = "piston"
+    return p
+
+
+def _serving_grating(scale, rng):
+    nx = max(16, int(round(128 * scale)) // 4 * 4)
+    ny = max(32, int(round(512 * scale)) // 4 * 4)
+    res = nx / 1.0                     # period 1 along x
+    d = 1.0 / res
+    Ly = ny * d
+    p = _base(2, (nx, ny, 1), res, int(round(30.0 / (0.5 * d))))
+    pc = max(4, ny // 16)
+    p["bc"] = ["periodic", "pml", "pec"]
+    p["pml_cells"] = [0, pc, 0]
+    gap = float(rng.uniform(0.3, 1.0))
+    yb = Ly / 2 - gap / 2
+    # membrane below the gap with grooves of depth 0.5 and period 1 (half-period teeth)
+    p["objects"] = [
+        {"shape": "box", "lo": [0.0, yb - 1.0, 0.0], "hi": [1.0, yb - 0.5, 0.0], "kind": "dielectric", "eps": 11.7, "mu": 1.0},
+        {"shape": "box", "lo": [0.25, yb - 0.5, 0.0], "hi": [0.75, yb, 0.0], "kind": "dielectric", "eps": 11.7, "mu": 1.0},
+        {"shape": "box", "lo": [0.0, Ly / 2 + gap / 2, 0.0], "hi": [1.0, Ly / 2 + gap / 2 + 0.5, 0.0], "kind": "dielectric", "eps": 11.7, "mu": 1.0},
+    ]
+    ytop = round((Ly / 2 + gap / 2 + 0.5) * res + 1) * d
+    ybot = round((Ly / 2 + gap / 2) * res - 1) * d
+    p["faces"] = [
+        {"axis": 1, "sign": -1, "pos": ybot, "lo": [0.0, ybot, 0.0], "hi": [1.0, ybot, 0.0]},
+        {"axis": 1, "sign": +1, "pos": ytop, "lo": [0.0, ytop, 0.0], "hi": [1.0, ytop, 0.0]},
+    ]
+    p["n_harm"] = int(min(8, nx))
+    p["polarization"] = "full"
+    nk = 16
+    p["k_points"] = [{"k": [2 * math.pi * m / nk, 0.0, 0.0], "weight": 1.0 / nk} for m in range(nk)]
+    p["force_axis"] = 1
+    p["g_variant"] = "plain"
+    p["precision"] = "fp32"
+    p["kind"] = "grating"
+    return p
+
+
+def _serving_sphere(side, rng):
+    res = side / 4.0
+    p = config4_sphere_notch(float(rng.uniform(0.3, 0.8)), seed=int(rng.integers(0, 2**31)),
+                             resolution=res, n_cells=side, pml_cells=max(4, int(round(0.3 * res))),
+                             n_harm=2, n_steps=int(round(30.0 / (0.5 / res))))
+    p["kind"] = "sphere"
+    return p
