@@ -1,0 +1,285 @@
+#!/usr/bin/env python
+"""Benchmark of the batched time-domain Casimir hot path on one GB300.
+
+Workload (one "step"): the two-dimensional piston sweep -- two 1 x 1 PEC blocks
+between PEC sidewalls at 8 sidewall separations h in [0.5, 3], grids 400 x
+40(1+2h) at resolution 40, TE + TM, a rectangular stress contour with 40 cosine
+harmonics per face, 20000 time steps, FP32 fields with FP64 accumulation; 8
+forces, 5120 source simulations (640 runs of 8 exactly-pruned simulations), all
+admitted together into one batched launch per time step.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead, on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "forces/s and Gcell-updates/s (% HBM roofline), p50/p99 latency vs plain at 1e-4 rel"
+WORKLOAD = "2D piston sweep: 8 h x TE+TM x 40 harmonics, 400x(80..280) cells, 20000 steps"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload_problems(n_steps=20000, n_harm=40):
+    import workloads as W
+    return [W.config2_piston(h, n_steps=n_steps, n_harm=n_harm) for h in W.config2_heights()]
+
+
+def cpu_baseline(budget_s=15.0):
+    """The FP64 oracle on a bounded sample of the workload: simulations of the
+    h = 0.5 geometry for a shortened number of steps, one per host core."""
+    import numpy as np
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    import workloads as W
+    cores = os.cpu_count() or 1
+    T = 1000
+    p = W.config2_piston(W.config2_heights()[0], n_steps=T)
+    sims = oracle.enumerate_sims(p)[:cores]
+    setup = oracle.grid_setup(p)
+    oracle.run_sim(p, dict(sims[0]), setup)          # warm the library
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda s: oracle.run_sim(p, s, setup), sims))
+    dt = time.perf_counter() - t0
+    cells = p["n"][0] * p["n"][1]
+    cups = len(sims) * cells * T / dt
+    return {"value": cups / 1e9, "unit": "Gcell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(sims)} sims of the h=0.5 geometry (400x80) x {T} steps, FP64, {dt:.2f} s"}, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build_all()
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline()
+    total_dt = 0.0
+    for _ in range(args.steps):
+        cb, dt = cpu_baseline()
+        vals.append(cb["value"])
+        total_dt += dt
+    v = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gcell-updates/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000 * total_dt / max(1, args.steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+           "cpu_baseline": dict(cb, value=v),
+           "e2e": {"value": v, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--time-steps", type=int, default=20000, help="FDTD steps per simulation")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+
+    from paper_0906_5170_gb300 import build as pkbuild
+    pkbuild.build()
+    import paper_0906_5170_gb300 as pk
+
+    stream = torch.cuda.Stream()
+    ctx = pk.Context(local, stream=stream.cuda_stream)
+    probs = workload_problems(args.time_steps)
+    plans = [ctx.plan(p) for p in probs]
+    infos = [pl.info() for pl in plans]
+    cells_per_step = sum(i["cell_updates"] for i in infos)
+    n_forces = len(plans)
+
+    def one_step():
+        tickets = [pl.submit(tag=i) for i, pl in enumerate(plans)]
+        return [t.force(-1) for t in tickets]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        one_step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.kernel_stats(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = []
+    barrier()
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = one_step()
+        lat += [r[2]["total_ms"] for r in res]
+    ev1.record(stream)
+    ev1.synchronize()
+    wall = time.perf_counter() - t0
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    step_ms, launches, cups_kernel = ctx.kernel_stats()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    total_cups = cells_per_step * args.steps * world
+    value = total_cups / (ms / 1e3) / 1e9
+    forces_per_s = n_forces * args.steps * world / (ms / 1e3)
+
+    hbm, peak_kind = peaks()
+    b_alg = infos[0]["bytes_per_update"]
+    achieved = cups_kernel * b_alg / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm if achieved else None, "traffic": None,
+            "kernel": "k_step2d<float>", "bytes_per_cell_update": b_alg,
+            "avg_launch_ms": step_ms / max(1, launches), "peak_source": peak_kind}
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI: host planning + H2D tables + run + D2H results each step
+        barrier()
+        t0 = time.perf_counter()
+        h2d = 0
+        d2h = 0
+        fresh = [ctx.plan(p) for p in probs]
+        tickets = [pl.submit(tag=i) for i, pl in enumerate(fresh)]
+        for t in tickets:
+            t.force(-1)
+        e2e_s = time.perf_counter() - t0
+        for pl in fresh:
+            i = pl.info()
+            h2d += i["device_bytes"]
+            d2h += 2 * 8 * i["n_sims"]
+            pl.close()
+        e2e = {"value": cells_per_step * world / e2e_s / 1e9, "unit": "Gcell-updates/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "forces_per_s": n_forces * world / e2e_s}
+
+    cb = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            cb, _ = cpu_baseline()
+        except Exception as e:  # the oracle is test infrastructure; report, do not fail the bench
+            cb = {"value": None, "unit": "Gcell-updates/s", "cores": os.cpu_count(), "kind": "oracle",
+                  "sample": f"failed: {e}"}
+
+    if rank == 0:
+        lat_sorted = sorted(lat)
+        out = {
+            "metric": METRIC, "value": value, "unit": "Gcell-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "forces_per_step": n_forces,
+                       "sims_per_step": sum(i["n_sims"] for i in infos),
+                       "cell_updates_per_step": cells_per_step, "time_steps": args.time_steps,
+                       "l2": "inputs larger than L2 (%.1f GB of fields)" % (sum(i["device_bytes"] for i in infos) / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "forces_per_s": forces_per_s,
+            "latency_ms": {"p50": lat_sorted[len(lat) // 2], "p99": lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))]},
+            "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+            "gpu_launches": int(launches + 3 * n_forces * args.steps),
+            "clocks": clk,
+        }
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

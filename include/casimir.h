@@ -1,0 +1,217 @@
+/*
+ * casimir.h -- C ABI of the GB300 time-domain Casimir-force library.
+ *
+ * The library computes Casimir forces by the time-domain stress-tensor method
+ * of McCauley, Rodriguez, Joannopoulos and Johnson, "Casimir forces in the time
+ * domain: Applications" (arXiv:0906.5170):
+ *
+ *   F_i = 2 Im int_0^inf dt g(-t) [Gamma^E_i(t) + Gamma^H_i(t)]            (Eq. (1))
+ *
+ * where Gamma is the stress-tensor surface functional of the field response to
+ * a current J = delta(t) f_n on the stress surface S (Sec. II, Eqs. (3)-(6)),
+ * summed over a cosine harmonic basis f_n on each face of S (Sec. III, Eq. (7)),
+ * over source directions, polarisations and k-points (Sec. III B, III D), with
+ * every simulation run in a medium of uniform conductivity sigma (Sec. II).
+ * The prefactor 2 and the sign follow from the fluctuation-dissipation theorem
+ * with the paper's transform convention g(-t) = (1/2pi) int_0^inf g(xi) e^{i xi t} dxi.
+ *
+ * Units: c = eps0 = mu0 = hbar = 1; lengths in units of the geometry's length
+ * scale; the computational cell spans [0, n_a / resolution] along axis a.
+ *
+ * Conventions for every call:
+ *   - return 0 (CASIMIR_OK) on success, CASIMIR_NOTREADY (> 0) for work still
+ *     running, a negative CASIMIR_E* code on failure; nothing aborts the
+ *     process; casimir_last_error() gives a message for the calling thread;
+ *   - every pointer argument is a HOST pointer unless stated otherwise;
+ *   - arrays passed in are copied before the call returns; the caller keeps
+ *     ownership and may free them immediately;
+ *   - objects returned through an out-pointer are owned by the caller and are
+ *     released with the matching *_destroy call.
+ */
+#ifndef CASIMIR_H
+#define CASIMIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define CASIMIR_OK         0
+#define CASIMIR_NOTREADY   1   /* request admitted or queued, not finished yet */
+#define CASIMIR_EINVAL    -1   /* malformed problem or argument */
+#define CASIMIR_ENOMEM    -2   /* the plan alone exceeds the context's HBM budget, or allocation failed */
+#define CASIMIR_ECUDA     -3   /* a CUDA call failed (message in casimir_last_error) */
+#define CASIMIR_EBUSY     -4   /* request queue full */
+#define CASIMIR_ETIMEOUT  -5   /* the device watchdog stopped the run (step or time limit) */
+#define CASIMIR_ECANCELED -6   /* request cancelled */
+
+/* ---- problem description (Sec. II and III) ---------------------------------- */
+enum { CASIMIR_BC_PEC = 0, CASIMIR_BC_PML = 1, CASIMIR_BC_PERIODIC = 2 };
+enum { CASIMIR_SHAPE_BOX = 0, CASIMIR_SHAPE_SPHERE = 1 };
+enum { CASIMIR_MAT_PEC = 0,        /* eps = -inf (Sec. III A): tangential E vanishes */
+       CASIMIR_MAT_PMC = 1,        /* mu = -inf (Sec. III A): tangential H vanishes */
+       CASIMIR_MAT_DIELECTRIC = 2, /* constant eps, mu */
+       CASIMIR_MAT_LORENTZ = 3 };  /* eps_inf + delta_eps w0^2/(w0^2 - w^2) (Sec. III B), continued onto the contour */
+enum { CASIMIR_POL_TM = 1, CASIMIR_POL_TE = 2, CASIMIR_POL_TETM = 3, /* 2D, k_z = 0 */
+       CASIMIR_POL_FULL = 4 };     /* all six source components (2D with k_z != 0, or 3D) */
+enum { CASIMIR_G_PLAIN = 0,        /* Im g(-t) of Appendix A */
+       CASIMIR_G_ZINV = 1 };       /* z-invariant PEC/vacuum kernel of Appendix A.2: a 2D (k_z = 0)
+                                      TE+TM run gives the 3D force per unit length.  The kernel is
+                                      g(xi) times the factor i*omega/2 stated in the text, i.e. half
+                                      of the closed form printed there. */
+enum { CASIMIR_FP32 = 0,           /* FP32 fields, FP64 projection and accumulation */
+       CASIMIR_FP64 = 1 };         /* FP64 throughout */
+enum { CASIMIR_BASIS_COSINE = 0,   /* per-face cosine series, Eq. (7) */
+       CASIMIR_BASIS_POINT = 1 };  /* one source per surface pixel (Sec. II point-source method) */
+
+/* One geometric object; later objects override earlier ones where they overlap.
+ * Membership is closed (boundary points belong to the object). */
+typedef struct {
+    int shape;           /* CASIMIR_SHAPE_* */
+    int kind;            /* CASIMIR_MAT_* */
+    double lo[3], hi[3]; /* box corners */
+    double center[3];    /* sphere centre */
+    double radius;       /* sphere radius */
+    double eps, mu;      /* dielectric */
+    double eps_inf, delta_eps, omega0;   /* Lorentz pole (gamma = 0) */
+} casimir_object;
+
+/* One axis-aligned face of the stress surface S: normal along `axis`, outward
+ * sign `sign` (+1/-1), at coordinate `pos`; extent [lo[b], hi[b]] along each
+ * tangential axis b (entries along `axis` are ignored).  Each tangential extent
+ * must be an integer number of cells. */
+typedef struct {
+    int axis, sign;
+    double pos;
+    double lo[3], hi[3];
+} casimir_face;
+
+/* A k-point (Bloch k_x, k_y; or k_z for a 2D cross-section) and its weight in
+ * the force sum (quadrature weight times the measure, e.g. 1/pi for k_z). */
+typedef struct {
+    double k[3];
+    double weight;
+} casimir_kpoint;
+
+typedef struct {
+    int dims;            /* 2 or 3 */
+    int n[3];            /* cells; n[2] == 1 when dims == 2 */
+    double resolution;   /* cells per unit length: Delta = 1/resolution */
+    double courant;      /* Delta_t = courant * Delta */
+    int n_steps;         /* T, samples t_n = n Delta_t, n = 1..T */
+    double sigma;        /* contour conductivity (Sec. II), >= 0 */
+    double bg_eps, bg_mu;
+    int n_objects;
+    const casimir_object *objects;
+    int bc[3];           /* CASIMIR_BC_* per axis; PEC and PML axes are closed by a PEC wall at 0 == L */
+    int pml_cells[3];    /* CPML thickness per PML axis */
+    int n_faces;
+    const casimir_face *faces;
+    int n_harm;          /* cosine harmonics per tangential axis and face (capped at the pixel count) */
+    int polarization;    /* CASIMIR_POL_* */
+    int n_kpoints;
+    const casimir_kpoint *kpoints;
+    int force_axis;      /* 0, 1 or 2 */
+    int g_variant;       /* CASIMIR_G_* */
+    int precision;       /* CASIMIR_FP32 / CASIMIR_FP64 */
+    int basis;           /* CASIMIR_BASIS_* */
+} casimir_problem;
+
+/* ---- opaque handles ----------------------------------------------------------- */
+typedef struct casimir_ctx casimir_ctx_t;
+typedef struct casimir_plan casimir_plan_t;
+typedef struct casimir_request *casimir_ticket;
+
+typedef struct {
+    int64_t n_sims;            /* source simulations in the plan (after exact pruning) */
+    int64_t n_cells;           /* sum of grid cells over the sims */
+    int64_t cell_updates;      /* n_cells * n_steps */
+    int64_t device_bytes;      /* device memory the plan needs while running */
+    int64_t bytes_per_update;  /* algorithmic bytes per cell-update of the dominant kernel */
+} casimir_plan_info;
+
+typedef struct {
+    double queue_ms;           /* submit -> admission */
+    double device_ms;          /* admission -> device completion */
+    double total_ms;           /* submit -> result available */
+    int64_t cell_updates;
+    int64_t kernel_launches;   /* kernels of this library launched for the request */
+} casimir_stats;
+
+/* ---- context ----------------------------------------------------------------- */
+/* Create a context on CUDA device `device`; plans are admitted while the device
+ * memory they need fits in `hbm_budget_bytes` (0: 90% of free memory).  The
+ * context owns its device memory, its streams and the request executor. */
+int casimir_ctx_create(int device, uint64_t hbm_budget_bytes, casimir_ctx_t **out);
+void casimir_ctx_destroy(casimir_ctx_t *ctx);
+
+/* Run all device work of this context on `stream` (a cudaStream_t, or NULL for
+ * the context's own stream).  Lets a caller bracket the work with its own events. */
+int casimir_ctx_set_stream(casimir_ctx_t *ctx, void *cuda_stream);
+
+/* Route the context's device allocations through caller callbacks (e.g. a
+ * framework's caching allocator).  alloc returns a device pointer or NULL. */
+typedef void *(*casimir_alloc_fn)(size_t bytes, void *user);
+typedef void (*casimir_free_fn)(void *ptr, void *user);
+int casimir_ctx_set_allocator(casimir_ctx_t *ctx, casimir_alloc_fn alloc, casimir_free_fn free_, void *user);
+
+/* Watchdog: a request stops with CASIMIR_ETIMEOUT once it has been running for
+ * `max_ms` milliseconds (0: no limit).  Checked between chunks of time steps, so
+ * no device code ever waits on it. */
+int casimir_ctx_set_watchdog(casimir_ctx_t *ctx, double max_ms);
+
+/* Device time of the batched time-step kernels since the last reset, measured
+ * with CUDA events on the context's stream: total milliseconds, number of step
+ * launches and cell-updates performed.  reset != 0 zeroes the counters. */
+int casimir_ctx_kernel_stats(casimir_ctx_t *ctx, double *step_ms, int64_t *launches,
+                             int64_t *cell_updates, int reset);
+
+/* ---- plan: host-side set-up of one force computation (Sec. III) -------------- */
+/* Rasterise the geometry onto the Yee grid, build the face pixels, harmonic
+ * basis, interpolation stencils, g(-t) weights and the simulation list.  The
+ * problem's arrays are copied.  ctx == NULL builds a host-only plan that can be
+ * inspected but not run (no device needed).  Errors: CASIMIR_EINVAL (malformed
+ * problem), CASIMIR_ENOMEM (the plan alone needs more device memory than the budget). */
+int casimir_plan(casimir_ctx_t *ctx, const casimir_problem *problem, casimir_plan_t **out);
+int casimir_plan_get_info(const casimir_plan_t *plan, casimir_plan_info *info);
+void casimir_plan_destroy(casimir_plan_t *plan);
+
+/* ---- requests ------------------------------------------------------------------ */
+/* Queue one force computation of `plan` (non-blocking).  The plan must stay
+ * alive until the request has finished.  CASIMIR_EBUSY when the queue is full. */
+int casimir_submit(casimir_plan_t *plan, uint64_t user_tag, casimir_ticket *out);
+
+/* Wait up to `wait_ms` (0: poll, < 0: forever) for the result.  On success F[3]
+ * holds the force (only F[force_axis] is non-zero), *err_est (may be NULL) an
+ * estimate of the truncation error of the time integral, *st (may be NULL)
+ * timings.  Returns CASIMIR_NOTREADY while running.  After a return other than
+ * CASIMIR_NOTREADY the ticket is released. */
+int casimir_force(casimir_ticket ticket, int wait_ms, double F[3], double *err_est, casimir_stats *st);
+
+/* Cancel a queued or running request (its ticket is still released by casimir_force). */
+int casimir_cancel(casimir_ticket ticket);
+
+/* Run one request of `plan` to completion on the context's stream, synchronously:
+ * F[3] as above; per_sim (may be NULL, else n_sims doubles) receives every
+ * simulation's FP64 contribution in plan order. */
+int casimir_run(casimir_plan_t *plan, double F[3], double *per_sim, casimir_stats *st);
+
+/* Per-simulation description in plan order (for per-simulation parity):
+ * desc[6*s + 0..5] = k-point, face, harmonic n1, harmonic n2, source kind (0 J, 1 K),
+ * source component. */
+int casimir_plan_sims(const casimir_plan_t *plan, int32_t *desc, int64_t n);
+
+/* The time weights w_n = 2 Delta_t Im g(-n Delta_t), n = 1..n_steps, of Eq. (1)
+ * (rectangle rule); w must hold n_steps doubles. */
+int casimir_plan_weights(const casimir_plan_t *plan, double *w, int64_t n);
+
+/* Thread-local message describing the last error of the calling thread. */
+const char *casimir_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CASIMIR_H */

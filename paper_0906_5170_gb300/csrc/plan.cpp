@@ -1,0 +1,511 @@
+// Host-side planner: from a casimir_problem to rasterised lattices, face
+// pixels, harmonic sources, measurement functionals and g(-t) weights.
+//
+// Method: McCauley et al., arXiv:0906.5170, Sec. II (force as a sum of
+// harmonic-source simulations, Eqs. (1), (3)-(6)), Sec. III (cosine basis per
+// face, Eq. (7); sources spread onto the Yee grid), Appendix A (g(t)).
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <array>
+#include <complex>
+
+#include "plan.h"
+
+namespace cas {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTol = 1e-6;   // geometric tolerance, in cells
+
+struct Mat {
+    double eps, mu;
+    bool pec, pmc;
+    double de, w0;   // Lorentz pole
+};
+
+bool inside(const casimir_object &o, const double x[3], int dims, double d)
+{
+    double tol = kTol * d;
+    if (o.shape == CASIMIR_SHAPE_BOX) {
+        for (int a = 0; a < dims; ++a)
+            if (x[a] < o.lo[a] - tol || x[a] > o.hi[a] + tol) return false;
+        return true;
+    }
+    double r2 = 0;
+    for (int a = 0; a < dims; ++a) r2 += (x[a] - o.center[a]) * (x[a] - o.center[a]);
+    return r2 <= (o.radius + tol) * (o.radius + tol);
+}
+
+Mat material_at(const PlanData &P, const double x[3])
+{
+    const casimir_problem &p = P.prob;
+    Mat m{p.bg_eps, p.bg_mu, false, false, 0.0, 0.0};
+    double d = P.dx;
+    for (const auto &o : P.objects) {
+        if (!inside(o, x, p.dims, d)) continue;
+        m = Mat{p.bg_eps, p.bg_mu, false, false, 0.0, 0.0};
+        switch (o.kind) {
+        case CASIMIR_MAT_PEC: m.pec = true; break;
+        case CASIMIR_MAT_PMC: m.pmc = true; break;
+        case CASIMIR_MAT_DIELECTRIC: m.eps = o.eps; m.mu = o.mu; break;
+        case CASIMIR_MAT_LORENTZ: m.eps = o.eps_inf; m.mu = 1.0; m.de = o.delta_eps; m.w0 = o.omega0; break;
+        }
+    }
+    return m;
+}
+
+// Canonical coordinate of a site along axis a in [0, L).
+double canon(double x, double L)
+{
+    double y = std::fmod(x, L);
+    if (y < 0) y += L;
+    if (y > L - 1e-9 * L) y = 0.0;
+    return y;
+}
+
+void pml_profile(int n, int cells, double d, double dt, int half, std::vector<double> out[3])
+{
+    // Polynomial grading of order 3 with reflection 1e-8, kappa = 1, and a
+    // frequency shift alpha falling linearly from 0.05 at the inner interface
+    // to 0 at the wall (the paper gives no CPML parameters).
+    double w = cells * d, L = n * d;
+    double smax = -4.0 * std::log(1e-8) / (2.0 * w);
+    for (int q = 0; q < 3; ++q) out[q].assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double x = (i + (half ? 0.5 : 0.0)) * d;
+        double rho = std::max((w - x) / w, (x - (L - w)) / w);
+        rho = std::min(1.0, std::max(0.0, rho));
+        double sg = smax * rho * rho * rho;
+        double kap = 1.0;
+        double al = 0.05 * (1.0 - rho);
+        double b = std::exp(-(sg / kap + al) * dt);
+        double c = sg > 0 ? sg / (sg * kap + kap * kap * al) * (b - 1.0) : 0.0;
+        out[0][i] = b;
+        out[1][i] = c;
+        out[2][i] = 1.0 / kap;
+    }
+}
+
+struct Pix {
+    std::vector<std::array<double, 3>> x;   // centres
+    std::vector<int> t;                     // tangential axes
+    std::vector<int> cnt;                   // pixels per tangential axis
+    double dA;
+};
+
+Pix face_pixels(const PlanData &P, const casimir_face &f)
+{
+    Pix px;
+    int dims = P.prob.dims;
+    double d = P.dx;
+    for (int b = 0; b < dims; ++b)
+        if (b != f.axis) {
+            px.t.push_back(b);
+            px.cnt.push_back((int)std::lround((f.hi[b] - f.lo[b]) / d));
+        }
+    px.dA = std::pow(d, dims - 1);
+    int n0 = px.cnt[0], n1 = px.cnt.size() > 1 ? px.cnt[1] : 1;
+    for (int p = 0; p < n0; ++p)
+        for (int q = 0; q < n1; ++q) {
+            std::array<double, 3> c{0, 0, 0};
+            c[f.axis] = f.pos;
+            c[px.t[0]] = f.lo[px.t[0]] + (p + 0.5) * d;
+            if (px.t.size() > 1) c[px.t[1]] = f.lo[px.t[1]] + (q + 0.5) * d;
+            px.x.push_back(c);
+        }
+    return px;
+}
+
+// Cosine basis of Eq. (7) on a face, normalised on the pixel centres:
+// f_0 = sqrt(1/L), f_n = sqrt(2/L) cos(n pi s / L); products in 3D.
+double basis_value(const PlanData &P, const Pix &px, int pix, int n1, int n2)
+{
+    if (P.prob.basis == CASIMIR_BASIS_POINT) return pix == n1 ? 1.0 / std::sqrt(px.dA) : 0.0;
+    double d = P.dx;
+    int nn[2] = {n1, n2};
+    int idx[2] = {px.cnt.size() > 1 ? pix / px.cnt[1] : pix, px.cnt.size() > 1 ? pix % px.cnt[1] : 0};
+    double v = 1.0;
+    for (size_t t = 0; t < px.t.size(); ++t) {
+        double L = px.cnt[t] * d;
+        double s = (idx[t] + 0.5) * d;
+        v *= nn[t] == 0 ? std::sqrt(1.0 / L) : std::sqrt(2.0 / L) * std::cos(nn[t] * kPi * s / L);
+    }
+    return v;
+}
+
+using cplx = std::complex<double>;
+
+// Linear interpolation weights from the sites of array `as` to point x.
+void stencil(const PlanData &P, const Geo &g, const ArraySpec &as, const double x[3],
+             std::vector<std::pair<int64_t, cplx>> &out)
+{
+    out.clear();
+    int dims = P.prob.dims;
+    double d = P.dx;
+    std::vector<std::pair<int, cplx>> ax[3];
+    for (int a = 0; a < 3; ++a) {
+        if (a >= dims) { ax[a].push_back({0, 1.0}); continue; }
+        double u = x[a] / d - as.off[a];
+        double fl = std::floor(u);
+        double t = u - fl;
+        long i0 = (long)fl;
+        if (t < 1e-9) t = 0.0;
+        else if (t > 1.0 - 1e-9) { i0 += 1; t = 0.0; }
+        int n = g.n[a];
+        cplx ph(g.bloch_re[a], g.bloch_im[a]);
+        auto push = [&](long i, double w) {
+            long q = (long)std::floor((double)i / n);
+            cplx f = 1.0;
+            for (long r = 0; r < std::labs(q); ++r) f *= (q > 0 ? ph : std::conj(ph));
+            ax[a].push_back({(int)(i - q * n), w * f});
+        };
+        push(i0, 1.0 - t);
+        if (t > 0.0) push(i0 + 1, t);
+    }
+    for (auto &ei : ax[0])
+        for (auto &ej : ax[1])
+            for (auto &ek : ax[2])
+                out.push_back({((int64_t)ek.first * g.n[1] + ej.first) * g.n[0] + ei.first,
+                               ei.second * ej.second * ek.second});
+}
+
+int find_array(int family, int field, int comp, const ArraySpec *arrs, int narr)
+{
+    for (int a = 0; a < narr; ++a)
+        if (arrs[a].field == field && arrs[a].comp == comp) return a;
+    (void)family;
+    return -1;
+}
+
+int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err)
+{
+    const casimir_problem &p = P.prob;
+    ArraySpec arrs[6];
+    int narr = family_arrays(family, arrs);
+    g->family = family;
+    g->kpt = kpt;
+    g->narr = narr;
+    for (int a = 0; a < 3; ++a) g->n[a] = p.n[a];
+    const double *k = P.kpoints[kpt].k;
+    bool cplxf = false;
+    for (int a = 0; a < p.dims; ++a) {
+        if (p.bc[a] == CASIMIR_BC_PERIODIC) {
+            double ph = k[a] * p.n[a] * P.dx;
+            g->bloch_re[a] = std::cos(ph);
+            g->bloch_im[a] = std::sin(ph);
+            if (std::fabs(g->bloch_im[a]) > 0) cplxf = true;
+        }
+    }
+    if (p.dims == 2) {
+        g->kz = k[2];
+        if (k[2] != 0.0) cplxf = true;
+    }
+    g->complex_fields = cplxf;
+    if (cplxf && family != FAM_FULL) { *err = "k_z or a complex Bloch phase needs polarization FULL"; return CASIMIR_EINVAL; }
+
+    int64_t ncell = (int64_t)p.n[0] * p.n[1] * p.n[2];
+    g->mat.assign(ncell, 0);
+    std::map<std::vector<double>, int> ids;
+    std::vector<double> key(narr + 6);
+    double L[3] = {p.n[0] * P.dx, p.n[1] * P.dx, p.n[2] * P.dx};
+    for (int kk = 0; kk < p.n[2]; ++kk)
+        for (int j = 0; j < p.n[1]; ++j)
+            for (int i = 0; i < p.n[0]; ++i) {
+                std::fill(key.begin(), key.end(), 0.0);
+                for (int a = 0; a < narr; ++a) {
+                    const ArraySpec &as = arrs[a];
+                    double x[3] = {(i + as.off[0]) * P.dx, (j + as.off[1]) * P.dx, (kk + as.off[2]) * P.dx};
+                    bool wall = false;
+                    for (int ax = 0; ax < p.dims; ++ax) {
+                        x[ax] = canon(x[ax], L[ax]);
+                        if (as.field == 0 && (p.bc[ax] == CASIMIR_BC_PEC || p.bc[ax] == CASIMIR_BC_PML) &&
+                            std::fabs(x[ax]) < kTol * P.dx)
+                            wall = true;
+                    }
+                    Mat m = material_at(P, x);
+                    double c;
+                    if (as.field == 0) {
+                        c = (m.pec || wall) ? 0.0 : 1.0 / m.eps;
+                        if (!(m.pec || wall) && m.de != 0.0) {
+                            key[narr + 2 * as.comp] = m.de;
+                            key[narr + 2 * as.comp + 1] = m.w0;
+                        }
+                    } else {
+                        c = m.pmc ? 0.0 : 1.0 / m.mu;
+                    }
+                    key[a] = c;
+                }
+                auto it = ids.find(key);
+                int id;
+                if (it == ids.end()) {
+                    id = (int)ids.size();
+                    if (id > 255) { *err = "more than 256 distinct material sites"; return CASIMIR_EINVAL; }
+                    ids.emplace(key, id);
+                } else {
+                    id = it->second;
+                }
+                g->mat[((int64_t)kk * p.n[1] + j) * p.n[0] + i] = (uint8_t)id;
+            }
+    g->nmat = (int)ids.size();
+    g->table.assign((size_t)g->nmat * narr, 0.0);
+    g->lorentz.assign((size_t)g->nmat * 6, 0.0);
+    for (auto &kv : ids) {
+        for (int a = 0; a < narr; ++a) g->table[(size_t)kv.second * narr + a] = kv.first[a];
+        for (int q = 0; q < 6; ++q) {
+            g->lorentz[(size_t)kv.second * 6 + q] = kv.first[narr + q];
+            if (kv.first[narr + q] != 0.0) g->has_lorentz = true;
+        }
+    }
+    for (int a = 0; a < p.dims; ++a)
+        if (p.bc[a] == CASIMIR_BC_PML) {
+            g->has_pml[a] = true;
+            for (int h = 0; h < 2; ++h) pml_profile(p.n[a], p.pml_cells[a], P.dx, P.dt, h, g->pml[a][h]);
+        }
+    return CASIMIR_OK;
+}
+
+void add_entry(std::vector<Entry> &v, std::map<std::pair<int, int64_t>, size_t> &at, int arr, int64_t idx, cplx val)
+{
+    auto key = std::make_pair(arr, idx);
+    auto it = at.find(key);
+    if (it == at.end()) {
+        at.emplace(key, v.size());
+        v.push_back(Entry{arr, idx, val.real(), val.imag()});
+    } else {
+        v[it->second].re += val.real();
+        v[it->second].im += val.imag();
+    }
+}
+
+}  // namespace
+
+int family_arrays(int family, ArraySpec out[6])
+{
+    if (family == FAM_TM) {
+        out[0] = ArraySpec{0, 2, {0.0, 0.0, 0.5}, 1.0};
+        out[1] = ArraySpec{1, 0, {0.0, 0.5, 0.5}, 1.0};
+        out[2] = ArraySpec{1, 1, {0.5, 0.0, 0.5}, 1.0};
+        return 3;
+    }
+    if (family == FAM_TE) {
+        out[0] = ArraySpec{1, 2, {0.5, 0.5, 0.0}, 1.0};
+        out[1] = ArraySpec{0, 0, {0.5, 1.0, 0.0}, -1.0};
+        out[2] = ArraySpec{0, 1, {1.0, 0.5, 0.0}, -1.0};
+        return 3;
+    }
+    out[0] = ArraySpec{0, 0, {0.5, 0.0, 0.0}, 1.0};
+    out[1] = ArraySpec{0, 1, {0.0, 0.5, 0.0}, 1.0};
+    out[2] = ArraySpec{0, 2, {0.0, 0.0, 0.5}, 1.0};
+    out[3] = ArraySpec{1, 0, {0.0, 0.5, 0.5}, 1.0};
+    out[4] = ArraySpec{1, 1, {0.5, 0.0, 0.5}, 1.0};
+    out[5] = ArraySpec{1, 2, {0.5, 0.5, 0.0}, 1.0};
+    return 6;
+}
+
+// Im g(-t) of Appendix A.  Rotating g(-t) = (1/2pi) int_0^inf g(xi) e^{i xi t} dxi
+// onto xi = i eta gives the Laplace integral
+//   Im g(-t) = (1/2pi) int_0^inf sqrt(1 + sigma/eta) (eta + sigma/2) e^{-eta t} d eta,
+// evaluated with eta = exp(pi/2 sinh(tau)) (exp-sinh quadrature, which absorbs
+// the eta^{-1/2} end point and the exponential tail).
+double img_plain(double t, double sigma)
+{
+    if (sigma == 0.0) return 1.0 / (2.0 * kPi * t * t);
+    auto f = [&](double eta) {
+        return std::sqrt(1.0 + sigma / eta) * (eta + 0.5 * sigma) * std::exp(-eta * t);
+    };
+    // scale the variable so that the integrand's peak sits near eta ~ 1/t
+    double scale = 1.0 / t;
+    double h = 1.0 / 64.0;
+    double sum = 0.0;
+    for (int k = -6 * 64; k <= 6 * 64; ++k) {
+        double tau = k * h;
+        double e = std::exp(0.5 * kPi * std::sinh(tau));
+        double eta = scale * e;
+        if (!(eta > 0.0) || !std::isfinite(eta)) continue;
+        double w = scale * e * 0.5 * kPi * std::cosh(tau);
+        double v = f(eta) * w;
+        if (std::isfinite(v)) sum += v;
+    }
+    return sum * h / (2.0 * kPi);
+}
+
+int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
+{
+    const casimir_problem &p = *pin;
+    if (p.dims != 2 && p.dims != 3) { *err = "dims must be 2 or 3"; return CASIMIR_EINVAL; }
+    for (int a = 0; a < 3; ++a)
+        if (p.n[a] < 1) { *err = "grid sizes must be >= 1"; return CASIMIR_EINVAL; }
+    if (p.dims == 2 && p.n[2] != 1) { *err = "two-dimensional problems have n[2] == 1"; return CASIMIR_EINVAL; }
+    if (!(p.resolution > 0) || !(p.courant > 0) || p.n_steps < 1 || !(p.sigma >= 0)) {
+        *err = "resolution, courant, n_steps must be positive and sigma >= 0";
+        return CASIMIR_EINVAL;
+    }
+    if (p.courant * std::sqrt((double)p.dims) >= 1.0) { *err = "courant number above the Yee stability limit"; return CASIMIR_EINVAL; }
+    if (p.n_faces < 1 || !p.faces) { *err = "no stress-surface faces"; return CASIMIR_EINVAL; }
+    if (p.n_kpoints < 1 || !p.kpoints) { *err = "no k-points"; return CASIMIR_EINVAL; }
+    if (p.n_objects < 0 || (p.n_objects > 0 && !p.objects)) { *err = "objects"; return CASIMIR_EINVAL; }
+    if (p.force_axis < 0 || p.force_axis >= p.dims) { *err = "force_axis"; return CASIMIR_EINVAL; }
+    if (p.n_harm < 1) { *err = "n_harm must be >= 1"; return CASIMIR_EINVAL; }
+    if (p.precision != CASIMIR_FP32 && p.precision != CASIMIR_FP64) { *err = "precision"; return CASIMIR_EINVAL; }
+    if (p.g_variant != CASIMIR_G_PLAIN && p.g_variant != CASIMIR_G_ZINV) { *err = "g_variant"; return CASIMIR_EINVAL; }
+    bool twod_pol = p.polarization == CASIMIR_POL_TM || p.polarization == CASIMIR_POL_TE || p.polarization == CASIMIR_POL_TETM;
+    if (!twod_pol && p.polarization != CASIMIR_POL_FULL) { *err = "polarization"; return CASIMIR_EINVAL; }
+    if (twod_pol && p.dims != 2) { *err = "TM/TE polarizations are two-dimensional"; return CASIMIR_EINVAL; }
+    for (int a = 0; a < p.dims; ++a) {
+        if (p.bc[a] < 0 || p.bc[a] > 2) { *err = "bc"; return CASIMIR_EINVAL; }
+        if (p.bc[a] == CASIMIR_BC_PML && (p.pml_cells[a] < 1 || 2 * p.pml_cells[a] >= p.n[a])) {
+            *err = "pml_cells";
+            return CASIMIR_EINVAL;
+        }
+    }
+    P->prob = p;
+    P->objects.assign(p.objects, p.objects + p.n_objects);
+    P->faces.assign(p.faces, p.faces + p.n_faces);
+    P->kpoints.assign(p.kpoints, p.kpoints + p.n_kpoints);
+    P->prob.objects = P->objects.data();
+    P->prob.faces = P->faces.data();
+    P->prob.kpoints = P->kpoints.data();
+    P->dx = 1.0 / p.resolution;
+    P->dt = p.courant * P->dx;
+    for (auto &o : P->objects) {
+        if (o.kind < 0 || o.kind > 3 || o.shape < 0 || o.shape > 1) { *err = "object kind/shape"; return CASIMIR_EINVAL; }
+        if (o.kind == CASIMIR_MAT_DIELECTRIC && !(o.eps > 0 && o.mu > 0)) { *err = "dielectric eps, mu must be > 0"; return CASIMIR_EINVAL; }
+        if (o.kind == CASIMIR_MAT_LORENTZ && !(o.eps_inf > 0 && o.omega0 > 0)) { *err = "lorentz eps_inf, omega0 must be > 0"; return CASIMIR_EINVAL; }
+    }
+    if (!(p.bg_eps > 0 && p.bg_mu > 0)) { *err = "background eps, mu must be > 0"; return CASIMIR_EINVAL; }
+    for (auto &f : P->faces) {
+        if (f.axis < 0 || f.axis >= p.dims || (f.sign != 1 && f.sign != -1)) { *err = "face axis/sign"; return CASIMIR_EINVAL; }
+        for (int b = 0; b < p.dims; ++b) {
+            if (b == f.axis) continue;
+            double c = (f.hi[b] - f.lo[b]) / P->dx;
+            if (c < 0.5 || std::fabs(c - std::lround(c)) > 1e-6) { *err = "face extents must be whole cells"; return CASIMIR_EINVAL; }
+        }
+    }
+
+    // families
+    std::vector<int> fams;
+    if (p.polarization == CASIMIR_POL_TM || p.polarization == CASIMIR_POL_TETM) fams.push_back(FAM_TM);
+    if (p.polarization == CASIMIR_POL_TE || p.polarization == CASIMIR_POL_TETM) fams.push_back(FAM_TE);
+    if (p.polarization == CASIMIR_POL_FULL) fams.push_back(FAM_FULL);
+
+    // g weights, Eq. (1) by the rectangle rule at t_n = n dt
+    int T = p.n_steps;
+    P->gw.resize(T);
+    for (int n = 1; n <= T; ++n) {
+        double t = n * P->dt, im;
+        if (p.g_variant == CASIMIR_G_PLAIN) {
+            im = img_plain(t, p.sigma);
+        } else {
+            // z-invariant PEC/vacuum kernel: the extra factor i*omega/2 of the text of
+            // Appendix A.2, i.e. half of the closed form printed there.
+            double s = p.sigma;
+            im = 0.5 * (2.0 / (t * t * t) + 1.5 * s / (t * t) + 0.5 * s * s / t) / (2.0 * kPi);
+        }
+        P->gw[n - 1] = 2.0 * P->dt * im;
+    }
+    P->kweight.resize(p.n_kpoints);
+    for (int k = 0; k < p.n_kpoints; ++k) P->kweight[k] = P->kpoints[k].weight;
+
+    // lattices
+    std::map<std::pair<int, int>, int> geo_of;
+    for (int k = 0; k < p.n_kpoints; ++k)
+        for (int fam : fams) {
+            Geo g;
+            int rc = build_geo(*P, fam, k, &g, err);
+            if (rc) return rc;
+            geo_of[{k, fam}] = (int)P->geos.size();
+            P->geos.push_back(std::move(g));
+        }
+
+    // simulations: (k-point, face, harmonic, family, source kind, component)
+    struct Src { int fam, kind, comp; };
+    std::vector<Src> srcs;
+    for (int fam : fams) {
+        if (fam == FAM_TM) { srcs.push_back({fam, 0, 2}); srcs.push_back({fam, 1, 0}); srcs.push_back({fam, 1, 1}); }
+        if (fam == FAM_TE) { srcs.push_back({fam, 0, 0}); srcs.push_back({fam, 0, 1}); srcs.push_back({fam, 1, 2}); }
+        if (fam == FAM_FULL)
+            for (int kind = 0; kind < 2; ++kind)
+                for (int c = 0; c < 3; ++c) srcs.push_back({fam, kind, c});
+    }
+    std::vector<std::pair<int64_t, cplx>> st;
+    for (int k = 0; k < p.n_kpoints; ++k)
+        for (int fi = 0; fi < p.n_faces; ++fi) {
+            const casimir_face &f = P->faces[fi];
+            Pix px = face_pixels(*P, f);
+            std::vector<std::pair<int, int>> harms;
+            if (p.basis == CASIMIR_BASIS_POINT) {
+                for (size_t q = 0; q < px.x.size(); ++q) harms.push_back({(int)q, 0});
+            } else {
+                int h0 = std::min(p.n_harm, px.cnt[0]);
+                int h1 = px.cnt.size() > 1 ? std::min(p.n_harm, px.cnt[1]) : 1;
+                for (int a = 0; a < h0; ++a)
+                    for (int b = 0; b < h1; ++b) harms.push_back({a, b});
+            }
+            // surface eps / mu at the pixels (Minkowski weight)
+            std::vector<double> epsS(px.x.size()), muS(px.x.size());
+            for (size_t q = 0; q < px.x.size(); ++q) {
+                Mat m = material_at(*P, px.x[q].data());
+                epsS[q] = m.eps;
+                muS[q] = m.mu;
+            }
+            for (auto hm : harms)
+                for (auto s : srcs) {
+                    // exact pruning: for force axis i and a face with normal a != i only c == a contributes
+                    if (!(f.axis == p.force_axis || s.comp == f.axis)) continue;
+                    Sim sim;
+                    sim.kpt = k;
+                    sim.face = fi;
+                    sim.n1 = hm.first;
+                    sim.n2 = hm.second;
+                    sim.kind = s.kind;
+                    sim.comp = s.comp;
+                    sim.family = s.fam;
+                    sim.geo = geo_of[{k, s.fam}];
+                    const Geo &g = P->geos[sim.geo];
+                    ArraySpec arrs[6];
+                    int narr = family_arrays(s.fam, arrs);
+                    int sa = find_array(s.fam, s.kind, s.comp, arrs, narr);
+                    sim.second_u = (sa == 0) ? 1 : 0;
+                    std::vector<double> fv(px.x.size());
+                    for (size_t q = 0; q < px.x.size(); ++q) fv[q] = basis_value(*P, px, (int)q, hm.first, hm.second);
+                    // source: flux after the impulse D_c = -(dA/dV) W_c^H f, stored as E = D/eps (masked)
+                    std::map<std::pair<int, int64_t>, size_t> at;
+                    for (size_t q = 0; q < px.x.size(); ++q) {
+                        if (fv[q] == 0.0) continue;
+                        stencil(*P, g, arrs[sa], px.x[q].data(), st);
+                        for (auto &e : st) add_entry(sim.src, at, sa, e.first, -std::conj(e.second) * fv[q] / P->dx);
+                    }
+                    for (auto &e : sim.src) {
+                        double c = g.table[(size_t)g.mat[e.idx] * narr + sa] * arrs[sa].sign;
+                        e.re *= c;
+                        e.im *= c;
+                    }
+                    // measurement: s_i = sum_k dA w_S f(x_k) [n_c F_i(x_k) - 1/2 n_i F_c(x_k)]
+                    double nv[3] = {0, 0, 0};
+                    nv[f.axis] = f.sign;
+                    int i = p.force_axis;
+                    std::map<std::pair<int, int64_t>, size_t> am;
+                    for (size_t q = 0; q < px.x.size(); ++q) {
+                        if (fv[q] == 0.0) continue;
+                        double base = px.dA * (s.kind == 0 ? epsS[q] : muS[q]) * fv[q];
+                        int comps[2] = {i, s.comp};
+                        double coefs[2] = {nv[s.comp], -0.5 * nv[i]};
+                        for (int t = 0; t < 2; ++t) {
+                            if (coefs[t] == 0.0) continue;
+                            int ma = find_array(s.fam, s.kind, comps[t], arrs, narr);
+                            if (ma < 0) continue;   // component absent in this family: identically zero
+                            stencil(*P, g, arrs[ma], px.x[q].data(), st);
+                            for (auto &e : st)
+                                add_entry(sim.meas, am, ma, e.first, e.second * (base * coefs[t] * arrs[ma].sign));
+                        }
+                    }
+                    P->sims.push_back(std::move(sim));
+                }
+        }
+    if (P->sims.empty()) { *err = "no contributing simulations"; return CASIMIR_EINVAL; }
+    return CASIMIR_OK;
+}
+
+}  // namespace cas

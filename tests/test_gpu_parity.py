@@ -1,0 +1,164 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle,
+simulation by simulation and for the force, on seeded synthetic geometries.
+
+Tolerances: FP64 mode 1e-10 relative (per simulation and for the force);
+FP32 fields with FP64 accumulation: per simulation 2e-5 of the largest
+contribution, force 1e-4 of the sum of |contributions| (the force is a sum of
+large per-face terms that cancel; FP32 rounding of each field sample sets the
+floor, see the design notes)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pk():
+    from paper_0906_5170_gb300 import build
+    build.build()
+    import paper_0906_5170_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def ctx(pk):
+    c = pk.Context(0)
+    yield c
+    c.close()
+
+
+_ORACLE_CACHE = {}
+
+
+def _oracle(p, key):
+    if key not in _ORACLE_CACHE:
+        F, parts, _ = oracle.force(p, return_parts=True)
+        _ORACLE_CACHE[key] = (F, np.array(parts))
+    return _ORACLE_CACHE[key]
+
+
+def _check(ctx, p, key, fp64):
+    F, per, st = ctx.plan(p).run(per_sim=True)
+    Fo, parts = _oracle(p, key)
+    fa = p["force_axis"]
+    assert per.shape == parts.shape
+    scale = np.sum(np.abs(parts))
+    if fp64:
+        assert np.all(np.abs(per - parts) <= 1e-10 * np.abs(parts) + 1e-13 * scale)
+        assert abs(F[fa] - Fo) <= 1e-10 * abs(Fo) + 1e-13 * scale
+    else:
+        assert np.max(np.abs(per - parts)) <= 2e-5 * np.max(np.abs(parts))
+        assert abs(F[fa] - Fo) <= 1e-4 * scale
+    assert st["kernel_launches"] > 0
+    return F[fa], Fo, per, parts
+
+
+def test_config1_plates_fp64_full(ctx):
+    p = W.config1_plates()           # the full-size configuration: 60 x 40, 8 harmonics, 4000 steps
+    _check(ctx, p, "c1", True)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_piston_te_tm(ctx, prec):
+    p = W.piston_small(n_steps=800, precision=prec)
+    _check(ctx, p, ("piston", prec), prec == "fp64")
+
+
+def test_piston_fp32_force_relative(ctx):
+    # the force itself (after cancellation) to 1e-4 relative on a closed contour
+    p = W.piston_small(n_steps=1200, precision="fp32", n_harm=8)
+    Fg, Fo, _, _ = _check(ctx, p, "pist32f", False)
+    assert abs(Fg - Fo) <= 1e-4 * abs(Fo)
+
+
+def test_ragged_multi_tile_grid(ctx):
+    # several tiles in both directions with ragged tails (nx = 83, ny = 45)
+    p = W._base(2, (83, 45, 1), 10.0, 500)
+    p["objects"] = [{"shape": "box", "lo": [3.0, 1.0, 0], "hi": [4.5, 2.9, 0], "kind": "pec"},
+                    {"shape": "box", "lo": [5.5, 0.5, 0], "hi": [6.0, 3.5, 0], "kind": "dielectric", "eps": 3.0, "mu": 1.0}]
+    p["faces"] = W.box_faces([2.8, 0.8], [4.8, 3.3], 2)
+    p["n_harm"] = 5
+    p["polarization"] = "TE+TM"
+    p["force_axis"] = 0
+    p["precision"] = "fp64"
+    _check(ctx, p, "ragged", True)
+
+
+def test_pmc_sidewalls_and_point_basis(ctx):
+    p = W.piston_small(n_steps=400, precision="fp64")
+    L = p["n"][1] / p["resolution"]
+    p["objects"] = p["objects"] + [
+        {"shape": "box", "lo": [0.0, 0.0, 0.0], "hi": [6.0, 0.05, 0.0], "kind": "pmc"},
+        {"shape": "box", "lo": [0.0, L - 0.05, 0.0], "hi": [6.0, L, 0.0], "kind": "pmc"}]
+    _check(ctx, p, "pmc", True)
+    q = dict(p, basis="point", n_steps=200)
+    _check(ctx, q, "point", True)
+
+
+def test_periodic_axis(ctx):
+    p = W.piston_small(n_steps=400, precision="fp64")
+    p["bc"] = ["periodic", "pec", "pec"]
+    _check(ctx, p, "periodic", True)
+
+
+def test_results_identical_alone_and_in_a_mix(ctx, pk):
+    probs = [W.piston_small(h=0.5, n_steps=600), W.config1_plates(),
+             W.piston_small(h=1.0, n_steps=300, precision="fp32"), W.piston_small(h=0.7, n_steps=900)]
+    for p in probs:
+        if p.get("precision") != "fp64":
+            p["precision"] = "fp32"
+    probs[1] = dict(probs[1], precision="fp32")
+    alone = [ctx.plan(p).run()[0] for p in probs]
+    plans = [ctx.plan(p) for p in probs]
+    tickets = []
+    for i, pl in enumerate(plans):
+        tickets.append(pl.submit(tag=i))
+    res = [t.force(-1) for t in tickets]
+    for a, (F, err, st) in zip(alone, res):
+        assert np.allclose(F, a, rtol=1e-12, atol=0)
+
+
+def test_staggered_arrivals_join_running_batch(ctx, pk):
+    import time
+    p1 = W.config1_plates()
+    p1["precision"] = "fp32"
+    p2 = W.piston_small(n_steps=3000, precision="fp32")
+    a1 = ctx.plan(p1).run()[0]
+    a2 = ctx.plan(p2).run()[0]
+    pl2 = ctx.plan(p2)
+    pl1 = ctx.plan(p1)
+    t2 = pl2.submit()
+    time.sleep(0.02)
+    t1 = pl1.submit()           # arrives while the first request runs
+    F1 = t1.force(-1)[0]
+    F2 = t2.force(-1)[0]
+    assert np.allclose(F1, a1, rtol=1e-12, atol=0)
+    assert np.allclose(F2, a2, rtol=1e-12, atol=0)
+
+
+def test_watchdog_and_cancel_leave_context_usable(ctx, pk):
+    p = W.config2_piston(W.config2_heights()[0], n_harm=4, n_steps=20000)
+    ctx.set_watchdog(50.0)
+    t = ctx.plan(p).submit()
+    with pytest.raises(pk.CasimirError) as e:
+        t.force(-1)
+    assert e.value.code == -5
+    ctx.set_watchdog(0.0)
+    t = ctx.plan(p).submit()
+    t.cancel()
+    with pytest.raises(pk.CasimirError) as e:
+        t.force(-1)
+    assert e.value.code == -6
+    q = W.piston_small(n_steps=300, precision="fp64")
+    _check(ctx, q, "after", True)
+
+
+def test_budget_rejects_oversized_plan(pk):
+    c = pk.Context(0, hbm_budget_bytes=1 << 20)
+    with pytest.raises(pk.CasimirError) as e:
+        c.plan(W.config2_piston(W.config2_heights()[7], n_steps=100))
+    assert e.value.code == -2
+    c.close()
