@@ -177,6 +177,7 @@ int casimir_ctx_kernel_stats(casimir_ctx_t *ctx, double *step_ms, int64_t *launc
  * problem), CASIMIR_ENOMEM (the plan alone needs more device memory than the budget). */
 int casimir_plan(casimir_ctx_t *ctx, const casimir_problem *problem, casimir_plan_t **out);
 int casimir_plan_get_info(const casimir_plan_t *plan, casimir_plan_info *info);
+/* Release a plan; blocks until the plan's queued or running requests have finished. */
 void casimir_plan_destroy(casimir_plan_t *plan);
 
 /* ---- requests ------------------------------------------------------------------ */

@@ -468,18 +468,31 @@ def _setups(problem):
     return [_Setup(problem, kp["k"]) for kp in problem["k_points"]]
 
 
+def run_vectors(problem, setup, magnetic, src, meas, pol="full"):
+    """Run the leapfrog from an explicit post-impulse flux and record an explicit
+    functional: src maps (component, site) -> D (or B) value, meas maps
+    (component, site) -> weight.  Returns s(n), n = 1..T."""
+    sim = {"kind": "K" if magnetic else "J", "pol": pol, "comp": 0}
+    return _run(problem, setup, sim, src, meas)
+
+
 def run_sim(problem, sim, setup=None):
     """Run one sim; return the complex series s(n), n = 1..T."""
     if setup is None:
         setup = _Setup(problem, problem["k_points"][sim["k"]]["k"])
     src, meas = _sim_vectors(problem, setup, sim)
-    c = sim["comp"]
+    src = {(sim["comp"], k): v for k, v in src.items()}
+    return _run(problem, setup, sim, src, meas)
+
+
+def _run(problem, setup, sim, src, meas):
     s = _OgSim()
     s.magnetic = 1 if sim["kind"] == "K" else 0
     s.nsteps = problem["n_steps"]
-    sk = np.array(sorted(src), dtype=np.int32)
-    sv = np.array([src[k] for k in sk], dtype=np.complex128)
-    scomp = np.full(len(sk), c, dtype=np.int32)
+    skeys = sorted(src)
+    sk = np.array([k[1] for k in skeys], dtype=np.int32)
+    sv = np.array([src[k] for k in skeys], dtype=np.complex128)
+    scomp = np.array([k[0] for k in skeys], dtype=np.int32)
     sre, sim_ = np.ascontiguousarray(sv.real), np.ascontiguousarray(sv.imag)
     s.nsrc = len(sk)
     s.src_comp, s.src_idx, s.src_re, s.src_im = _ip(scomp), _ip(sk), _dp(sre), _dp(sim_)

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -196,6 +197,7 @@ class Context:
         h = ctypes.c_void_p()
         check(lib().casimir_ctx_create(int(device), int(hbm_budget_bytes), ctypes.byref(h)))
         self.h = h
+        self._plans = weakref.WeakSet()
         if stream is not None:
             check(lib().casimir_ctx_set_stream(self.h, ctypes.c_void_p(int(stream))))
 
@@ -222,6 +224,8 @@ class Context:
 
     def close(self):
         if self.h:
+            for p in list(self._plans):      # plans must be released before their context
+                p.close()
             lib().casimir_ctx_destroy(self.h)
             self.h = None
 
@@ -242,6 +246,8 @@ class Plan:
         h = ctypes.c_void_p()
         check(lib().casimir_plan(ctx.h if ctx else None, ctypes.byref(self._m.struct), ctypes.byref(h)))
         self.h = h
+        if ctx is not None:
+            ctx._plans.add(self)
 
     def info(self):
         i = PlanInfo()
@@ -275,7 +281,7 @@ class Plan:
     def submit(self, tag=0):
         t = ctypes.c_void_p()
         check(lib().casimir_submit(self.h, int(tag), ctypes.byref(t)))
-        return Ticket(t)
+        return Ticket(t, self)
 
     def close(self):
         if self.h:
@@ -290,8 +296,9 @@ class Plan:
 
 
 class Ticket:
-    def __init__(self, h):
+    def __init__(self, h, plan):
         self.h = h
+        self.plan = plan        # the plan must outlive its requests
         self.done = False
 
     def force(self, wait_ms=-1):

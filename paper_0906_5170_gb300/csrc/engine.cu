@@ -422,7 +422,9 @@ static int run_chunk(casimir_ctx *c, int k)
     return CASIMIR_OK;
 }
 
-static void finish_request(casimir_ctx *c, casimir_request *r)
+// Publish a request's result.  The state store is the last access to *r: once
+// it is visible, casimir_force may release the request.
+static void finish_request(casimir_ctx *c, casimir_request *r, int status)
 {
     casimir_plan_t *P = r->plan;
     const PlanData &D = P->data;
@@ -445,9 +447,9 @@ static void finish_request(casimir_ctx *c, casimir_request *r)
     c->used -= align256(P->field_elems * P->rsize) + 2 * align256(ns * 8);
     r->block = nullptr;
     r->t_done = now_ms();
-    r->state = 2;
-    r->status = CASIMIR_OK;
+    r->status = status;
     P->inflight--;
+    r->state.store(status == CASIMIR_OK ? 2 : 3, std::memory_order_release);
 }
 
 // One engine iteration: run a chunk, then issue copy-backs for finished requests
@@ -497,10 +499,8 @@ static int engine_iterate(casimir_ctx *c)
     for (size_t q = 0; q < c->active.size();) {
         casimir_request *r = c->active[q];
         if (r->copy_issued && cudaEventQuery(r->done_ev) == cudaSuccess) {
-            int st = r->status;
-            finish_request(c, r);
-            if (st != CASIMIR_OK) { r->status = st; r->state = 3; }
             c->active.erase(c->active.begin() + q);
+            finish_request(c, r, r->status.load());
             changed = true;
         } else {
             ++q;
@@ -526,9 +526,9 @@ static void worker_main(casimir_ctx *c)
             casimir_request *r = c->queue.front();
             if (r->cancel) {
                 c->queue.pop_front();
-                r->state = 3;
                 r->status = CASIMIR_ECANCELED;
                 r->plan->inflight--;
+                r->state = 3;
                 c->cv.notify_all();
                 continue;
             }
@@ -536,9 +536,9 @@ static void worker_main(casimir_ctx *c)
             c->queue.pop_front();
             int rc = admit(c, r);
             if (rc) {
-                r->state = 3;
                 r->status = rc;
                 r->plan->inflight--;
+                r->state = 3;
                 c->cv.notify_all();
             }
         }
@@ -552,9 +552,11 @@ static void worker_main(casimir_ctx *c)
         if (rc) {
             std::string msg = g_err;
             for (casimir_request *r : c->active) {
-                r->state = 3;
+                dev_free(c, r->block);
+                r->block = nullptr;
                 r->status = rc;
                 r->plan->inflight--;
+                r->state = 3;
             }
             c->active.clear();
             c->dirty = true;
@@ -719,6 +721,11 @@ void casimir_plan_destroy(casimir_plan_t *P)
 {
     if (!P) return;
     casimir_ctx *c = P->ctx;
+    if (c) {
+        // requests of this plan still queued or running finish first
+        std::unique_lock<std::mutex> lk(c->mu);
+        c->cv.wait(lk, [&] { return P->inflight.load() == 0; });
+    }
     if (c && P->dev.block) {
         std::lock_guard<std::mutex> lk(c->mu);
         cudaStreamSynchronize(c->stream);
