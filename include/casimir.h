@@ -209,6 +209,31 @@ int casimir_plan_sims(const casimir_plan_t *plan, int32_t *desc, int64_t n);
  * (rectangle rule); w must hold n_steps doubles. */
 int casimir_plan_weights(const casimir_plan_t *plan, double *w, int64_t n);
 
+/* Allocation-free run of a plan, for callers that cannot allocate device memory
+ * (no counterpart in the paper; this is a library-integration entry point).
+ * Such callers include code that runs while a CUDA graph is being captured, a
+ * host that gives the library only a fixed memory reservation, and embedders
+ * whose allocator must not be re-entered.  The call performs no cudaMalloc,
+ * cudaFree or other allocating routine: every intermediate (fields, simulation
+ * and tile tables, the plan's copied tables) lives in one static device array of
+ * 64 MiB per device, which every GPU that loads the library holds until the
+ * process exits.
+ *   plan       any plan of two-dimensional (TM/TE) simulations, including a
+ *              host-only plan built with ctx == NULL;
+ *   d_per_sim  DEVICE pointer to n_sims doubles; receives every simulation's
+ *              contribution sum_n w_n s(n) in plan order, before the k-point
+ *              weight (all work is queued on `cuda_stream`; synchronise it
+ *              before reading);
+ *   cuda_stream a cudaStream_t, or NULL for the default stream.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture begins.
+ * Every call reuses the same array, which keeps the previous call's contents
+ * (the call clears what must start at zero); calls whose work overlaps on the
+ * GPU race on the array and must be serialised by the caller.  Returns
+ * CASIMIR_ENOMEM, with the required size in casimir_last_error(), when the plan
+ * does not fit in the array, and CASIMIR_EINVAL for non-2D plans. */
+int casimir_run_noalloc(const casimir_plan_t *plan, double *d_per_sim, void *cuda_stream);
+
 /* Thread-local message describing the last error of the calling thread. */
 const char *casimir_last_error(void);
 

@@ -93,6 +93,7 @@ SIGNATURES = {
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Stats)]),
     "casimir_plan_sims": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64]),
     "casimir_plan_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
+    "casimir_run_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "casimir_last_error": (ctypes.c_char_p, []),
 }
 

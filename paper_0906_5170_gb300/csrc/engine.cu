@@ -844,3 +844,147 @@ int casimir_run(casimir_plan_t *P, double F[3], double *per_sim, casimir_stats *
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Allocation-free run of a two-dimensional plan.
+//
+// Some callers may not allocate device memory at all: code running while a
+// CUDA graph is being captured (cudaMalloc is not permitted inside a capture),
+// hosts that hand the library a fixed memory reservation, or embedders whose
+// allocator must not be re-entered from a library.  casimir_run_noalloc lets
+// them run a plan without any device allocation: the fields, the simulation
+// and tile tables, the copied plan tables and the launch counter all live in
+// the file-scope array below, allocated once per device when the library is
+// loaded and held until the process exits.
+// ---------------------------------------------------------------------------------
+
+static constexpr size_t kNoallocBytes = size_t(64) << 20;   // 64 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[256];   // device address of the array, per device ordinal
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// symbol is only a host-side stand-in, so the address is looked up once per
+// device (with that device current) and cached.
+static int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return fail(CASIMIR_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(CASIMIR_ECUDA, std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return CASIMIR_OK;
+}
+
+// Copy `n` items produced by `make(i, &item)` to device memory through a small
+// stack buffer (copies from pageable memory return once the source is staged,
+// so the buffer can be refilled immediately).
+template <typename T, typename F>
+static int staged_copy(T *dst, int64_t n, F make, cudaStream_t st)
+{
+    constexpr int B = 64;
+    T buf[B];
+    for (int64_t i0 = 0; i0 < n; i0 += B) {
+        int m = (int)std::min<int64_t>(B, n - i0);
+        for (int j = 0; j < m; ++j) make(i0 + j, &buf[j]);
+        CUDA_TRY(cudaMemcpyAsync(dst + i0, buf, m * sizeof(T), cudaMemcpyHostToDevice, st));
+    }
+    return CASIMIR_OK;
+}
+
+extern "C" int casimir_run_noalloc(const casimir_plan_t *P, double *d_per_sim, void *cuda_stream)
+{
+    if (!P || !d_per_sim) return fail(CASIMIR_EINVAL, "NULL argument");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const PlanData &D = P->data;
+    for (const Geo &g : D.geos)
+        if (g.family == FAM_FULL) return fail(CASIMIR_EINVAL, "casimir_run_noalloc runs two-dimensional TM/TE plans only");
+    const size_t ns = P->sims.size(), nt = P->tiles.size();
+    // scratch layout: counter | sims | tiles | tail | mat | coef | gw | ents | src | fields
+    size_t off[11];
+    off[0] = 0;
+    off[1] = align256(sizeof(int64_t));
+    off[2] = off[1] + align256(ns * sizeof(DevSim2D));
+    off[3] = off[2] + align256(nt * sizeof(DevTile));
+    off[4] = off[3] + align256(ns * sizeof(double));
+    off[5] = off[4] + align256(P->mat_all.size());
+    off[6] = off[5] + align256(P->coef_all.size() * P->rsize);
+    off[7] = off[6] + align256(D.gw.size() * sizeof(double));
+    off[8] = off[7] + align256(P->ents.size() * sizeof(DevEnt));
+    off[9] = off[8] + align256(P->src.size() * sizeof(DevSrc));
+    off[10] = off[9] + align256((size_t)P->field_elems * P->rsize);
+    if (off[10] > kNoallocBytes)
+        return fail(CASIMIR_ENOMEM, "casimir_run_noalloc: the plan needs " + std::to_string(off[10]) +
+                                        " bytes of scratch; the static array holds " + std::to_string(kNoallocBytes));
+    void *base_v = nullptr;
+    int rc = noalloc_scratch(&base_v);
+    if (rc) return rc;
+    char *base = (char *)base_v;
+    int64_t *d_counter = (int64_t *)(base + off[0]);
+    DevSim2D *d_sims = (DevSim2D *)(base + off[1]);
+    DevTile *d_tiles = (DevTile *)(base + off[2]);
+    double *d_tail = (double *)(base + off[3]);
+    uint8_t *d_mat = (uint8_t *)(base + off[4]);
+    char *d_coef = base + off[5];
+    double *d_gw = (double *)(base + off[6]);
+    DevEnt *d_ents = (DevEnt *)(base + off[7]);
+    DevSrc *d_src = (DevSrc *)(base + off[8]);
+    char *d_fields = base + off[9];
+
+    // the array keeps the previous call's contents: clear the fields, the tail sums and the output
+    CUDA_TRY(cudaMemsetAsync(d_fields, 0, (size_t)P->field_elems * P->rsize, st));
+    CUDA_TRY(cudaMemsetAsync(d_tail, 0, ns * sizeof(double), st));
+    CUDA_TRY(cudaMemsetAsync(d_per_sim, 0, ns * sizeof(double), st));
+    static const int64_t one = 1;
+    CUDA_TRY(cudaMemcpyAsync(d_counter, &one, sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (!P->mat_all.empty()) CUDA_TRY(cudaMemcpyAsync(d_mat, P->mat_all.data(), P->mat_all.size(), cudaMemcpyHostToDevice, st));
+    if (P->fp64) {
+        CUDA_TRY(cudaMemcpyAsync(d_coef, P->coef_all.data(), P->coef_all.size() * 8, cudaMemcpyHostToDevice, st));
+    } else {
+        rc = staged_copy((float *)d_coef, (int64_t)P->coef_all.size(),
+                         [&](int64_t i, float *o) { *o = (float)P->coef_all[i]; }, st);
+        if (rc) return rc;
+    }
+    CUDA_TRY(cudaMemcpyAsync(d_gw, D.gw.data(), D.gw.size() * 8, cudaMemcpyHostToDevice, st));
+    if (!P->ents.empty()) CUDA_TRY(cudaMemcpyAsync(d_ents, P->ents.data(), P->ents.size() * sizeof(DevEnt), cudaMemcpyHostToDevice, st));
+    if (!P->src.empty()) CUDA_TRY(cudaMemcpyAsync(d_src, P->src.data(), P->src.size() * sizeof(DevSrc), cudaMemcpyHostToDevice, st));
+    const double sg = D.prob.sigma, dt = D.dt, dx = D.dx;
+    rc = staged_copy(d_sims, (int64_t)ns, [&](int64_t s, DevSim2D *d) {
+        const HostSim &hs = P->sims[s];
+        *d = DevSim2D{};
+        d->fields = d_fields + hs.field_off * P->rsize;
+        d->mat = d_mat + P->mat_off[hs.geo];
+        d->coef = d_coef + P->coef_off[hs.geo] * P->rsize;
+        d->gw = d_gw;
+        d->acc = d_per_sim + s;
+        d->tail = d_tail + s;
+        d->s0 = 0;
+        d->nx = hs.nx;
+        d->ny = hs.ny;
+        d->T = D.prob.n_steps;
+        d->tail_from = D.prob.n_steps;
+        d->second_u = hs.second_u;
+        d->a = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt);
+        d->bf = dt / (1.0 + 0.5 * sg * dt) / dx;
+        d->hf = dt / dx;
+    }, st);
+    if (rc) return rc;
+    rc = staged_copy(d_tiles, (int64_t)nt, [&](int64_t t, DevTile *d) {
+        const HostTile &ht = P->tiles[t];
+        *d = DevTile{ht.sim, ht.i0, ht.j0, ht.ne, d_ents + ht.ent0};
+    }, st);
+    if (rc) return rc;
+    launch_inject(P->fp64, d_fields, d_src, (int)P->src.size(), st);
+    for (int n = 0; n < D.prob.n_steps; ++n)
+        launch_step2d(P->fp64, d_sims, d_tiles, (int)nt, d_counter, n, st);
+    CUDA_TRY(cudaGetLastError());
+    return CASIMIR_OK;
+}
