@@ -200,6 +200,12 @@ int casimir_cancel(casimir_ticket ticket);
  * simulation's FP64 contribution in plan order. */
 int casimir_run(casimir_plan_t *plan, double F[3], double *per_sim, casimir_stats *st);
 
+/* The same computation without batching, as a point of comparison for the
+ * batched executor: simulations run one after another, each time step issues
+ * its field-update launches and a separate projection launch, and no CUDA graph
+ * is used.  Arguments and results as for casimir_run. */
+int casimir_run_plain(casimir_plan_t *plan, double F[3], double *per_sim, casimir_stats *st);
+
 /* Per-simulation description in plan order (for per-simulation parity):
  * desc[6*s + 0..5] = k-point, face, harmonic n1, harmonic n2, source kind (0 J, 1 K),
  * source component. */

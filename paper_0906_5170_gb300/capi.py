@@ -91,6 +91,8 @@ SIGNATURES = {
     "casimir_cancel": (ctypes.c_int, [ctypes.c_void_p]),
     "casimir_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Stats)]),
+    "casimir_run_plain": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Stats)]),
     "casimir_plan_sims": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64]),
     "casimir_plan_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
     "casimir_run_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -267,8 +269,9 @@ class Plan:
         check(lib().casimir_plan_weights(self.h, w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), T))
         return w
 
-    def run(self, per_sim=False):
-        """Synchronous run: returns (F[3], per-sim contributions or None, stats dict)."""
+    def run(self, per_sim=False, plain=False):
+        """Synchronous run: returns (F[3], per-sim contributions or None, stats dict).
+        plain=True uses the unbatched comparison path (casimir_run_plain)."""
         F = (ctypes.c_double * 3)()
         st = Stats()
         ps = None
@@ -276,7 +279,8 @@ class Plan:
         if per_sim:
             ps = np.zeros(self.info()["n_sims"])
             ptr = ps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        check(lib().casimir_run(self.h, F, ptr, ctypes.byref(st)))
+        fn = lib().casimir_run_plain if plain else lib().casimir_run
+        check(fn(self.h, F, ptr, ctypes.byref(st)))
         return np.array(F[:]), ps, {f: getattr(st, f) for f, _ in Stats._fields_}
 
     def submit(self, tag=0):

@@ -10,10 +10,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -23,27 +25,19 @@
 #include <thread>
 #include <vector>
 
-#include "casimir.h"
-#include "kernels.h"
-#include "plan.h"
-
-using namespace cas;
+#include "engine_internal.h"
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace cas {
 
 int fail(int code, const std::string &msg)
 {
     g_err = msg;
     return code;
 }
-
-#define CUDA_TRY(expr)                                                                        \
-    do {                                                                                      \
-        cudaError_t e_ = (expr);                                                              \
-        if (e_ != cudaSuccess) return fail(CASIMIR_ECUDA, std::string(#expr ": ") + cudaGetErrorString(e_)); \
-    } while (0)
 
 double now_ms()
 {
@@ -53,119 +47,13 @@ double now_ms()
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-}  // namespace
-
-// ---------------------------------------------------------------------------------
-// host-side device tables of a plan
-// ---------------------------------------------------------------------------------
-
-struct HostSim {
-    int geo;
-    int nx, ny;
-    int second_u;
-    int64_t field_off;     // element offset of this sim's 6 arrays inside the request's field block
-    int tile0, ntile;      // range in the plan's tile list
-    int ent0, nent;        // range in the plan's entry list (bucketed by tile)
-    int src0, nsrc;        // range in the plan's source list
-};
-
-struct HostTile {
-    int sim, i0, j0, ent0, ne;
-};
-
-struct DevPlan {           // device copies of a plan's static tables (kept while the plan lives)
-    uint8_t *mat = nullptr;
-    void *coef = nullptr;
-    double *gw = nullptr;
-    DevEnt *ents = nullptr;
-    DevSrc *src = nullptr;
-    size_t bytes = 0;
-    void *block = nullptr;
-};
-
-struct casimir_ctx;
-
-struct casimir_plan {
-    casimir_ctx *ctx = nullptr;
-    PlanData data;
-    int fp64 = 0;
-    size_t rsize = 4;
-    std::vector<HostSim> sims;
-    std::vector<HostTile> tiles;
-    std::vector<DevEnt> ents;
-    std::vector<DevSrc> src;
-    std::vector<int64_t> mat_off;     // per geo, bytes
-    std::vector<int64_t> coef_off;    // per geo, elements
-    std::vector<uint8_t> mat_all;
-    std::vector<double> coef_all;
-    int64_t field_elems = 0;          // per request
-    int64_t cells = 0;
-    int64_t table_bytes = 0;
-    int64_t request_bytes = 0;
-    DevPlan dev;
-    std::atomic<int> inflight{0};
-};
-
-struct casimir_request {
-    casimir_plan_t *plan = nullptr;
-    uint64_t tag = 0;
-    std::atomic<int> state{0};   // 0 queued, 1 running, 2 done, 3 failed
-    std::atomic<int> status{0};
-    std::atomic<bool> cancel{false};
-    double F[3] = {0, 0, 0};
-    double err = 0;
-    double t_submit = 0, t_admit = 0, t_done = 0;
-    int64_t s0 = 0;
-    int64_t launches = 0;
-    void *block = nullptr;   // fields, acc, tail
-    double *acc = nullptr, *tail = nullptr;
-    double *h_acc = nullptr;  // pinned copy-back (acc then tail)
-    cudaEvent_t done_ev = nullptr;
-    bool copy_issued = false;
-    std::vector<double> per_sim;
-};
-
-struct casimir_ctx {
-    int device = 0;
-    uint64_t budget = 0;
-    uint64_t used = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    casimir_alloc_fn alloc = nullptr;
-    casimir_free_fn freef = nullptr;
-    void *user = nullptr;
-    double watchdog_ms = 0;
-    int64_t *d_launch = nullptr;
-    int64_t h_launch = 1;            // index of the next launch
-    // active set
-    std::vector<casimir_request *> active;
-    DevSim2D *d_sims = nullptr;
-    DevTile *d_tiles = nullptr;
-    size_t sims_cap = 0, tiles_cap = 0;
-    int ntiles = 0;
-    int fp64_active = -1;
-    bool dirty = true;
-    std::map<int, cudaGraphExec_t> graphs;    // per chunk length, for the current active set
-    // statistics
-    double step_ms = 0;
-    int64_t step_launches = 0;
-    int64_t cell_updates = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // worker
-    std::mutex mu;
-    std::condition_variable cv;
-    std::deque<casimir_request *> queue;
-    std::thread worker;
-    bool worker_on = false;
-    bool stop = false;
-    std::atomic<int> sync_busy{0};
-};
+}  // namespace cas
 
 // ---------------------------------------------------------------------------------
 // memory helpers
 // ---------------------------------------------------------------------------------
 
-static int dev_alloc(casimir_ctx *c, size_t bytes, void **out)
+int dev_alloc(casimir_ctx *c, size_t bytes, void **out)
 {
     if (c->alloc) {
         *out = c->alloc(bytes, c->user);
@@ -180,7 +68,7 @@ static int dev_alloc(casimir_ctx *c, size_t bytes, void **out)
     return CASIMIR_OK;
 }
 
-static void dev_free(casimir_ctx *c, void *p)
+void dev_free(casimir_ctx *c, void *p)
 {
     if (!p) return;
     if (c->freef) c->freef(p, c->user);
@@ -196,8 +84,6 @@ static int prepare_plan(casimir_plan_t *P)
     PlanData &D = P->data;
     P->fp64 = D.prob.precision == CASIMIR_FP64;
     P->rsize = P->fp64 ? 8 : 4;
-    for (auto &g : D.geos)
-        if (g.family == FAM_FULL) return fail(CASIMIR_EINVAL, "polarization FULL (k_z, Bloch, 3D) is not supported by this build");
     // geometry tables
     for (auto &g : D.geos) {
         P->mat_off.push_back((int64_t)P->mat_all.size());
@@ -207,6 +93,17 @@ static int prepare_plan(casimir_plan_t *P)
         P->coef_off.push_back((int64_t)P->coef_all.size());
         P->coef_all.insert(P->coef_all.end(), g.table.begin(), g.table.end());
         while (P->coef_all.size() % 32) P->coef_all.push_back(0.0);
+        P->lor_off.push_back((int64_t)P->lor_all.size());
+        if (g.family == FAM_FULL) P->lor_all.insert(P->lor_all.end(), g.lorentz.begin(), g.lorentz.end());
+        std::array<int64_t, 3> po{-1, -1, -1};
+        for (int a = 0; a < 3; ++a)
+            if (g.has_pml[a]) {
+                po[a] = (int64_t)P->pml_all.size();
+                for (int h = 0; h < 2; ++h)
+                    for (int q = 0; q < 3; ++q) P->pml_all.insert(P->pml_all.end(), g.pml[a][h][q].begin(), g.pml[a][h][q].end());
+                while (P->pml_all.size() % 32) P->pml_all.push_back(0.0);
+            }
+        P->pml_off.push_back(po);
     }
     // sims, tiles, entries, sources
     int64_t off = 0;
@@ -217,82 +114,154 @@ static int prepare_plan(casimir_plan_t *P)
         hs.geo = sm.geo;
         hs.nx = g.n[0];
         hs.ny = g.n[1];
+        hs.nz = g.n[2];
         hs.second_u = sm.second_u;
+        hs.full = g.family == FAM_FULL;
+        hs.magnetic = sm.kind;
         hs.field_off = off;
-        int64_t N = (int64_t)hs.nx * hs.ny;
-        off += 6 * N;
-        off = (off + 63) & ~(int64_t)63;
+        hs.psi_off = -1;
+        hs.lor_off = -1;
+        int64_t N = (int64_t)hs.nx * hs.ny * hs.nz;
         P->cells += N;
-        int tx = (hs.nx + TILE_X - 1) / TILE_X, ty = (hs.ny + TILE_Y - 1) / TILE_Y;
-        hs.tile0 = (int)P->tiles.size();
-        hs.ntile = tx * ty;
-        // bucket measurement entries by tile
-        std::vector<std::vector<DevEnt>> bucket(hs.ntile);
-        for (const Entry &e : sm.meas) {
-            int i = (int)(e.idx % hs.nx), j = (int)(e.idx / hs.nx);
-            int ti = i / TILE_X, tj = j / TILE_Y;
-            int loc = (j - tj * TILE_Y) * TILE_X + (i - ti * TILE_X);
-            bucket[tj * tx + ti].push_back(DevEnt{loc | (e.arr << 16), 0, e.re});
-        }
-        hs.ent0 = (int)P->ents.size();
-        for (int tj = 0; tj < ty; ++tj)
-            for (int ti = 0; ti < tx; ++ti) {
-                auto &b = bucket[tj * tx + ti];
-                HostTile ht{(int)s, ti * TILE_X, tj * TILE_Y, (int)P->ents.size(), (int)b.size()};
-                P->ents.insert(P->ents.end(), b.begin(), b.end());
-                P->tiles.push_back(ht);
+        if (!hs.full) {
+            off += 6 * N;
+            off = (off + 63) & ~(int64_t)63;
+            int tx = (hs.nx + TILE_X - 1) / TILE_X, ty = (hs.ny + TILE_Y - 1) / TILE_Y;
+            hs.tile0 = (int)P->tiles.size();
+            hs.ntile = tx * ty;
+            std::vector<std::vector<DevEnt>> bucket(hs.ntile);
+            for (const Entry &e : sm.meas) {
+                int i = (int)(e.idx % hs.nx), j = (int)(e.idx / hs.nx);
+                int ti = i / TILE_X, tj = j / TILE_Y;
+                int loc = (j - tj * TILE_Y) * TILE_X + (i - ti * TILE_X);
+                bucket[tj * tx + ti].push_back(DevEnt{loc | (e.arr << 16), 0, e.re});
             }
-        hs.nent = (int)P->ents.size() - hs.ent0;
-        hs.src0 = (int)P->src.size();
-        for (const Entry &e : sm.src) P->src.push_back(DevSrc{hs.field_off + e.arr * N + e.idx, e.re});
-        hs.nsrc = (int)P->src.size() - hs.src0;
+            hs.ent0 = (int)P->ents.size();
+            for (int tj = 0; tj < ty; ++tj)
+                for (int ti = 0; ti < tx; ++ti) {
+                    auto &b = bucket[tj * tx + ti];
+                    HostTile ht{(int)s, ti * TILE_X, tj * TILE_Y, (int)P->ents.size(), (int)b.size()};
+                    P->ents.insert(P->ents.end(), b.begin(), b.end());
+                    P->tiles.push_back(ht);
+                }
+            hs.nent = (int)P->ents.size() - hs.ent0;
+            hs.src0 = (int)P->src.size();
+            for (const Entry &e : sm.src) P->src.push_back(DevSrc{hs.field_off + e.arr * N + e.idx, e.re});
+            hs.nsrc = (int)P->src.size() - hs.src0;
+        } else {
+            hs.cplx = g.complex_fields ? 1 : 0;
+            int cf = hs.cplx ? 2 : 1;
+            // real fields: the source's set {Ex, Ey, Hz} or {Ez, Hx, Hy} is stored as is, the other
+            // divided by i; d/dz = i kz then acts as +kz on the stored source set and -kz on the other
+            int sarr = sm.src.empty() ? 0 : sm.src[0].arr;
+            auto inA = [](int arr) { return arr == 0 || arr == 1 || arr == 5; };
+            double sgn = inA(sarr) ? 1.0 : -1.0;
+            hs.kzA = sgn * g.kz;
+            hs.kzB = -sgn * g.kz;
+            off += 6 * cf * N;
+            if (g.has_pml[0] || g.has_pml[1] || g.has_pml[2]) {
+                hs.psi_off = off;
+                for (int a = 0; a < 3; ++a)
+                    if (g.has_pml[a]) off += 4 * cf * (N / g.n[a]) * 2 * D.prob.pml_cells[a];
+            }
+            if (g.has_lorentz) {
+                hs.lor_off = off;
+                off += 6 * cf * N;
+            }
+            off = (off + 63) & ~(int64_t)63;
+            int ntile = (int)((N + 255) / 256);
+            hs.tile0 = (int)P->tiles6.size();
+            hs.ntile = ntile;
+            std::vector<std::vector<DevEnt6>> bucket(ntile);
+            for (const Entry &e : sm.meas) {
+                if (!hs.cplx && g.n[2] == 1 && D.prob.dims == 2 && inA(e.arr) != inA(sarr)) continue;   // contributes i * real: no real part
+                int tl = (int)(e.idx / 256);
+                bucket[tl].push_back(DevEnt6{(int)(e.idx - (int64_t)tl * 256), e.arr, e.re, e.im});
+            }
+            hs.ent0 = (int)P->ents6.size();
+            for (int tl = 0; tl < ntile; ++tl) {
+                auto &b = bucket[tl];
+                HostTile6 ht{(int)s, (int)std::min<int64_t>(256, N - (int64_t)tl * 256), (int64_t)tl * 256,
+                             (int)P->ents6.size(), (int)b.size()};
+                P->ents6.insert(P->ents6.end(), b.begin(), b.end());
+                P->tiles6.push_back(ht);
+            }
+            hs.nent = (int)P->ents6.size() - hs.ent0;
+            hs.src0 = (int)P->src6.size();
+            for (const Entry &e : sm.src) {
+                if (hs.cplx)
+                    P->src6.push_back(DevSrc6{hs.field_off + (2 * e.arr) * N + e.idx, hs.field_off + (2 * e.arr + 1) * N + e.idx, e.re, e.im});
+                else
+                    P->src6.push_back(DevSrc6{hs.field_off + e.arr * N + e.idx, -1, e.re, 0.0});
+            }
+            hs.nsrc = (int)P->src6.size() - hs.src0;
+        }
         P->sims.push_back(hs);
     }
     P->field_elems = off;
     P->table_bytes = (int64_t)(align256(P->mat_all.size()) + align256(P->coef_all.size() * P->rsize) +
                                align256(D.gw.size() * 8) + align256(P->ents.size() * sizeof(DevEnt)) +
-                               align256(P->src.size() * sizeof(DevSrc)));
+                               align256(P->src.size() * sizeof(DevSrc)) + align256(P->ents6.size() * sizeof(DevEnt6)) +
+                               align256(P->src6.size() * sizeof(DevSrc6)) + align256(P->lor_all.size() * 8) +
+                               align256(P->pml_all.size() * P->rsize));
     P->request_bytes = (int64_t)(align256(P->field_elems * P->rsize) + 2 * align256(P->sims.size() * 8) +
-                                 P->tiles.size() * sizeof(DevTile) + P->sims.size() * sizeof(DevSim2D));
+                                 P->tiles.size() * sizeof(DevTile) + P->tiles6.size() * sizeof(DevTile6) +
+                                 P->sims.size() * std::max(sizeof(DevSim2D), sizeof(DevSim6)));
     return CASIMIR_OK;
 }
 
-static int upload_plan(casimir_plan_t *P, cudaStream_t st)
+template <typename T>
+static int put_table(const std::vector<T> &v, void *dst, cudaStream_t st)
+{
+    if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return CASIMIR_OK;
+}
+
+static int put_real(const std::vector<double> &v, void *dst, int fp64, cudaStream_t st)
+{
+    if (v.empty()) return CASIMIR_OK;
+    if (fp64) return put_table(v, dst, st);
+    std::vector<float> f(v.begin(), v.end());
+    CUDA_TRY(cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return CASIMIR_OK;
+}
+
+int upload_plan(casimir_plan_t *P, cudaStream_t st)
 {
     if (P->dev.block) return CASIMIR_OK;
     casimir_ctx *c = P->ctx;
-    size_t b_mat = align256(P->mat_all.size()), b_coef = align256(P->coef_all.size() * P->rsize),
-           b_gw = align256(P->data.gw.size() * 8), b_ent = align256(P->ents.size() * sizeof(DevEnt)),
-           b_src = align256(P->src.size() * sizeof(DevSrc));
-    size_t total = b_mat + b_coef + b_gw + b_ent + b_src;
+    size_t sz[9] = {align256(P->mat_all.size()), align256(P->coef_all.size() * P->rsize),
+                    align256(P->data.gw.size() * 8), align256(P->ents.size() * sizeof(DevEnt)),
+                    align256(P->src.size() * sizeof(DevSrc)), align256(P->ents6.size() * sizeof(DevEnt6)),
+                    align256(P->src6.size() * sizeof(DevSrc6)), align256(P->lor_all.size() * 8),
+                    align256(P->pml_all.size() * P->rsize)};
+    size_t total = 0;
+    for (size_t q : sz) total += q;
     void *blk;
-    int rc = dev_alloc(c, total, &blk);
+    int rc = dev_alloc(c, std::max<size_t>(total, 256), &blk);
     if (rc) return rc;
     char *p = (char *)blk;
     P->dev.block = blk;
     P->dev.bytes = total;
-    P->dev.mat = (uint8_t *)p;
-    p += b_mat;
-    P->dev.coef = p;
-    p += b_coef;
-    P->dev.gw = (double *)p;
-    p += b_gw;
-    P->dev.ents = (DevEnt *)p;
-    p += b_ent;
-    P->dev.src = (DevSrc *)p;
-    CUDA_TRY(cudaMemcpyAsync(P->dev.mat, P->mat_all.data(), P->mat_all.size(), cudaMemcpyHostToDevice, st));
-    if (P->fp64) {
-        CUDA_TRY(cudaMemcpyAsync(P->dev.coef, P->coef_all.data(), P->coef_all.size() * 8, cudaMemcpyHostToDevice, st));
-    } else {
-        std::vector<float> f(P->coef_all.begin(), P->coef_all.end());
-        CUDA_TRY(cudaMemcpyAsync(P->dev.coef, f.data(), f.size() * 4, cudaMemcpyHostToDevice, st));
-        CUDA_TRY(cudaStreamSynchronize(st));
-    }
-    CUDA_TRY(cudaMemcpyAsync(P->dev.gw, P->data.gw.data(), P->data.gw.size() * 8, cudaMemcpyHostToDevice, st));
-    if (!P->ents.empty())
-        CUDA_TRY(cudaMemcpyAsync(P->dev.ents, P->ents.data(), P->ents.size() * sizeof(DevEnt), cudaMemcpyHostToDevice, st));
-    if (!P->src.empty())
-        CUDA_TRY(cudaMemcpyAsync(P->dev.src, P->src.data(), P->src.size() * sizeof(DevSrc), cudaMemcpyHostToDevice, st));
+    P->dev.mat = (uint8_t *)p; p += sz[0];
+    P->dev.coef = p; p += sz[1];
+    P->dev.gw = (double *)p; p += sz[2];
+    P->dev.ents = (DevEnt *)p; p += sz[3];
+    P->dev.src = (DevSrc *)p; p += sz[4];
+    P->dev.ents6 = (DevEnt6 *)p; p += sz[5];
+    P->dev.src6 = (DevSrc6 *)p; p += sz[6];
+    P->dev.lor = (double *)p; p += sz[7];
+    P->dev.pml = p;
+    if ((rc = put_table(P->mat_all, P->dev.mat, st))) return rc;
+    if ((rc = put_real(P->coef_all, P->dev.coef, P->fp64, st))) return rc;
+    if ((rc = put_table(P->data.gw, P->dev.gw, st))) return rc;
+    if ((rc = put_table(P->ents, P->dev.ents, st))) return rc;
+    if ((rc = put_table(P->src, P->dev.src, st))) return rc;
+    if ((rc = put_table(P->ents6, P->dev.ents6, st))) return rc;
+    if ((rc = put_table(P->src6, P->dev.src6, st))) return rc;
+    if ((rc = put_table(P->lor_all, P->dev.lor, st))) return rc;
+    if ((rc = put_real(P->pml_all, P->dev.pml, P->fp64, st))) return rc;
     c->used += total;
     return CASIMIR_OK;
 }
@@ -323,6 +292,7 @@ static int admit(casimir_ctx *c, casimir_request *r)
     CUDA_TRY(cudaMemsetAsync(blk, 0, bf + 2 * ba, c->stream));
     // sources: offsets are relative to the request's field block
     launch_inject(P->fp64, blk, P->dev.src, (int)P->src.size(), c->stream);
+    launch_inject6(P->fp64, blk, P->dev.src6, (int)P->src6.size(), c->stream);
     CUDA_TRY(cudaGetLastError());
     if (!r->h_acc) CUDA_TRY(cudaMallocHost((void **)&r->h_acc, std::max<size_t>(1, 2 * P->sims.size()) * 8));
     r->s0 = c->h_launch - 1;
@@ -333,78 +303,188 @@ static int admit(casimir_ctx *c, casimir_request *r)
     return CASIMIR_OK;
 }
 
+// Device descriptor of simulation s of plan P whose request block is `blk`.
+void make_sim2d(const casimir_plan_t *P, char *blk, double *acc, double *tail, int64_t s0, size_t s, DevSim2D *d)
+{
+    const PlanData &D = P->data;
+    const HostSim &hs = P->sims[s];
+    double sg = D.prob.sigma, dt = D.dt, dx = D.dx;
+    *d = DevSim2D{};
+    d->fields = blk + hs.field_off * P->rsize;
+    d->mat = P->dev.mat + P->mat_off[hs.geo];
+    d->coef = (char *)P->dev.coef + P->coef_off[hs.geo] * P->rsize;
+    d->gw = P->dev.gw;
+    d->acc = acc + s;
+    d->tail = tail + s;
+    d->s0 = s0;
+    d->nx = hs.nx;
+    d->ny = hs.ny;
+    d->T = D.prob.n_steps;
+    d->tail_from = D.prob.n_steps - std::max(1, D.prob.n_steps / 8);
+    d->second_u = hs.second_u;
+    d->a = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt);
+    d->bf = dt / (1.0 + 0.5 * sg * dt) / dx;
+    d->hf = dt / dx;
+}
+
+void make_sim6(const casimir_plan_t *P, char *blk, double *acc, double *tail, int64_t s0, size_t s, DevSim6 *d)
+{
+    const PlanData &D = P->data;
+    const HostSim &hs = P->sims[s];
+    const Geo &g = D.geos[hs.geo];
+    double sg = D.prob.sigma, dt = D.dt, dx = D.dx;
+    *d = DevSim6{};
+    d->fields = blk + hs.field_off * P->rsize;
+    d->psi = hs.psi_off >= 0 ? blk + hs.psi_off * P->rsize : nullptr;
+    d->lor = hs.lor_off >= 0 ? blk + hs.lor_off * P->rsize : nullptr;
+    d->mat = P->dev.mat + P->mat_off[hs.geo];
+    d->coef = (char *)P->dev.coef + P->coef_off[hs.geo] * P->rsize;
+    d->lorentz = P->dev.lor + P->lor_off[hs.geo];
+    d->pml = P->dev.pml;
+    d->gw = P->dev.gw;
+    d->acc = acc + s;
+    d->tail = tail + s;
+    d->s0 = s0;
+    int64_t N = (int64_t)hs.nx * hs.ny * hs.nz;
+    int64_t po = 0;
+    int cf = hs.cplx ? 2 : 1;
+    for (int a = 0; a < 3; ++a) {
+        d->n[a] = g.n[a];
+        d->pml_d[a] = g.has_pml[a] ? D.prob.pml_cells[a] : 0;
+        d->pml_off[a] = g.has_pml[a] ? P->pml_off[hs.geo][a] : 0;
+        d->slab[a] = g.has_pml[a] ? (N / g.n[a]) * 2 * D.prob.pml_cells[a] : 0;
+        d->psi_off[a] = po;
+        po += g.has_pml[a] ? 4 * cf * d->slab[a] : 0;
+        d->bre[a] = g.bloch_re[a];
+        d->bim[a] = g.bloch_im[a];
+    }
+    d->dims = D.prob.dims;
+    d->magnetic = hs.magnetic;
+    d->T = D.prob.n_steps;
+    d->tail_from = D.prob.n_steps - std::max(1, D.prob.n_steps / 8);
+    d->a = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt);
+    d->bs = dt / (1.0 + 0.5 * sg * dt);
+    d->dt = dt;
+    d->dt_full = dt;
+    d->sigma = sg;
+    d->inv_dx = 1.0 / dx;
+    d->kz = g.kz;
+    d->kzA = hs.kzA;
+    d->kzB = hs.kzB;
+}
+
+static int grow(casimir_ctx *c, void **p, size_t *cap, size_t need)
+{
+    if (need <= *cap) return CASIMIR_OK;
+    dev_free(c, *p);
+    *p = nullptr;
+    size_t n = std::max(need, 2 * *cap);
+    int rc = dev_alloc(c, n, p);
+    if (rc) { *cap = 0; return rc; }
+    *cap = n;
+    return CASIMIR_OK;
+}
+
 static int rebuild(casimir_ctx *c)
 {
-    std::vector<DevSim2D> sims;
-    std::vector<DevTile> tiles;
-    int fp64 = -1;
+    std::vector<DevSim2D> s2[2];
+    std::vector<DevTile> t2[2];
+    std::vector<DevSim6> s6[4];
+    std::vector<DevTile6> t6[4];
     for (casimir_request *r : c->active) {
         casimir_plan_t *P = r->plan;
-        if (fp64 < 0) fp64 = P->fp64;
-        int base = (int)sims.size();
-        const PlanData &D = P->data;
-        double sg = D.prob.sigma, dt = D.dt, dx = D.dx;
         for (size_t s = 0; s < P->sims.size(); ++s) {
             const HostSim &hs = P->sims[s];
-            DevSim2D d{};
-            d.fields = (char *)r->block + hs.field_off * P->rsize;
-            d.mat = P->dev.mat + P->mat_off[hs.geo];
-            d.coef = (char *)P->dev.coef + P->coef_off[hs.geo] * P->rsize;
-            d.gw = P->dev.gw;
-            d.acc = r->acc + s;
-            d.tail = r->tail + s;
-            d.s0 = r->s0;
-            d.nx = hs.nx;
-            d.ny = hs.ny;
-            d.T = D.prob.n_steps;
-            d.tail_from = D.prob.n_steps - std::max(1, D.prob.n_steps / 8);
-            d.second_u = hs.second_u;
-            d.a = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt);
-            d.bf = dt / (1.0 + 0.5 * sg * dt) / dx;
-            d.hf = dt / dx;
-            sims.push_back(d);
-            for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
-                const HostTile &ht = P->tiles[t];
-                tiles.push_back(DevTile{base + (int)s, ht.i0, ht.j0, ht.ne, P->dev.ents + ht.ent0});
+            char *blk = (char *)r->block;
+            if (!hs.full) {
+                auto &sv = s2[P->fp64];
+                auto &tv = t2[P->fp64];
+                int idx = (int)sv.size();
+                DevSim2D d;
+                make_sim2d(P, blk, r->acc, r->tail, r->s0, s, &d);
+                sv.push_back(d);
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile &ht = P->tiles[t];
+                    tv.push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.ents + ht.ent0});
+                }
+            } else {
+                int gi = 2 * P->fp64 + hs.cplx;
+                auto &sv = s6[gi];
+                auto &tv = t6[gi];
+                int idx = (int)sv.size();
+                DevSim6 d;
+                make_sim6(P, blk, r->acc, r->tail, r->s0, s, &d);
+                sv.push_back(d);
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile6 &ht = P->tiles6[t];
+                    tv.push_back(DevTile6{idx, ht.count, ht.cell0, ht.ne, 0, P->dev.ents6 + ht.ent0});
+                }
             }
         }
     }
-    if (sims.size() > c->sims_cap) {
-        dev_free(c, c->d_sims);
-        size_t cap = std::max<size_t>(sims.size(), 2 * c->sims_cap);
-        void *p;
-        int rc = dev_alloc(c, cap * sizeof(DevSim2D), &p);
+    c->ntiles = 0;
+    for (int gi = 0; gi < 6; ++gi) {
+        auto &G = c->groups[gi];
+        size_t ns, nt, ss, ts;
+        const void *sp, *tp;
+        if (gi < 2) { ns = s2[gi].size(); nt = t2[gi].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile); sp = s2[gi].data(); tp = t2[gi].data(); }
+        else { ns = s6[gi - 2].size(); nt = t6[gi - 2].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile6); sp = s6[gi - 2].data(); tp = t6[gi - 2].data(); }
+        int rc = grow(c, &G.sims, &G.sims_cap, ns * ss);
         if (rc) return rc;
-        c->d_sims = (DevSim2D *)p;
-        c->sims_cap = cap;
-    }
-    if (tiles.size() > c->tiles_cap) {
-        dev_free(c, c->d_tiles);
-        size_t cap = std::max<size_t>(tiles.size(), 2 * c->tiles_cap);
-        void *p;
-        int rc = dev_alloc(c, cap * sizeof(DevTile), &p);
+        rc = grow(c, &G.tiles, &G.tiles_cap, nt * ts);
         if (rc) return rc;
-        c->d_tiles = (DevTile *)p;
-        c->tiles_cap = cap;
+        if (ns) CUDA_TRY(cudaMemcpyAsync(G.sims, sp, ns * ss, cudaMemcpyHostToDevice, c->stream));
+        if (nt) CUDA_TRY(cudaMemcpyAsync(G.tiles, tp, nt * ts, cudaMemcpyHostToDevice, c->stream));
+        G.ntiles = (int)nt;
+        c->ntiles += (int)nt;
     }
-    if (!sims.empty()) CUDA_TRY(cudaMemcpyAsync(c->d_sims, sims.data(), sims.size() * sizeof(DevSim2D), cudaMemcpyHostToDevice, c->stream));
-    if (!tiles.empty()) CUDA_TRY(cudaMemcpyAsync(c->d_tiles, tiles.data(), tiles.size() * sizeof(DevTile), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));   // host vectors die here
-    c->ntiles = (int)tiles.size();
-    c->fp64_active = fp64;
     drop_graphs(c);
     c->dirty = false;
     return CASIMIR_OK;
 }
 
-// Launch `k` consecutive steps (as a cached CUDA graph) and advance the launch counter.
+static void launch_steps(casimir_ctx *c, int k)
+{
+    for (int j = 0; j < k; ++j) {
+        for (int p = 0; p < 2; ++p)
+            launch_step2d(p, (const DevSim2D *)c->groups[p].sims, (const DevTile *)c->groups[p].tiles,
+                          c->groups[p].ntiles, c->d_launch, j, c->stream);
+        for (int phase = 0; phase < 2; ++phase)
+            for (int gi = 2; gi < 6; ++gi)
+                launch_full((gi - 2) >> 1, (gi - 2) & 1, (const DevSim6 *)c->groups[gi].sims,
+                            (const DevTile6 *)c->groups[gi].tiles, c->groups[gi].ntiles, c->d_launch, j, phase,
+                            c->stream);
+    }
+    launch_bump(c->d_launch, k, c->stream);
+}
+
+// Launch `k` consecutive steps (as a cached CUDA graph, or directly when the
+// environment sets CASIMIR_NO_GRAPHS, e.g. for kernel profiling) and advance
+// the launch counter.
 static int run_chunk(casimir_ctx *c, int k)
 {
+    static const bool no_graphs = std::getenv("CASIMIR_NO_GRAPHS") != nullptr;
+    if (no_graphs) {
+        CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+        launch_steps(c, k);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    }
     auto it = c->graphs.find(k);
-    if (it == c->graphs.end()) {
+    if (!no_graphs && it == c->graphs.end()) {
         cudaGraph_t g;
         CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        for (int j = 0; j < k; ++j) launch_step2d(c->fp64_active, c->d_sims, c->d_tiles, c->ntiles, c->d_launch, j, c->stream);
+        for (int j = 0; j < k; ++j) {
+            for (int p = 0; p < 2; ++p)
+                launch_step2d(p, (const DevSim2D *)c->groups[p].sims, (const DevTile *)c->groups[p].tiles,
+                              c->groups[p].ntiles, c->d_launch, j, c->stream);
+            for (int phase = 0; phase < 2; ++phase)
+                for (int gi = 2; gi < 6; ++gi)
+                    launch_full((gi - 2) >> 1, (gi - 2) & 1, (const DevSim6 *)c->groups[gi].sims,
+                                (const DevTile6 *)c->groups[gi].tiles, c->groups[gi].ntiles, c->d_launch, j, phase,
+                                c->stream);
+        }
         launch_bump(c->d_launch, k, c->stream);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (e != cudaSuccess) return fail(CASIMIR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -414,16 +494,19 @@ static int run_chunk(casimir_ctx *c, int k)
         if (e != cudaSuccess) return fail(CASIMIR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
         it = c->graphs.emplace(k, ex).first;
     }
-    CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
-    CUDA_TRY(cudaGraphLaunch(it->second, c->stream));
-    CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    if (!no_graphs) {
+        CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+        CUDA_TRY(cudaGraphLaunch(it->second, c->stream));
+        CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    }
     c->h_launch += k;
-    for (casimir_request *r : c->active) r->launches += k + 1;
+    int per_step = 0;
+    for (int gi = 0; gi < 6; ++gi)
+        if (c->groups[gi].ntiles > 0) per_step += gi < 2 ? 1 : 2;
+    for (casimir_request *r : c->active) r->launches += (int64_t)k * per_step + 1;
     return CASIMIR_OK;
 }
 
-// Publish a request's result.  The state store is the last access to *r: once
-// it is visible, casimir_force may release the request.
 static void finish_request(casimir_ctx *c, casimir_request *r, int status)
 {
     casimir_plan_t *P = r->plan;
@@ -609,8 +692,10 @@ void casimir_ctx_destroy(casimir_ctx_t *c)
     cudaStreamSynchronize(c->stream);
     for (casimir_request *r : c->active) dev_free(c, r->block);
     drop_graphs(c);
-    dev_free(c, c->d_sims);
-    dev_free(c, c->d_tiles);
+    for (auto &G : c->groups) {
+        dev_free(c, G.sims);
+        dev_free(c, G.tiles);
+    }
     cudaFree(c->d_launch);
     cudaEventDestroy(c->ev0);
     cudaEventDestroy(c->ev1);
@@ -640,7 +725,7 @@ int casimir_ctx_set_allocator(casimir_ctx_t *c, casimir_alloc_fn a, casimir_free
 {
     if (!c || (!a) != (!f)) return fail(CASIMIR_EINVAL, "allocator needs both callbacks");
     std::lock_guard<std::mutex> lk(c->mu);
-    if (!c->active.empty() || !c->queue.empty() || c->d_sims) return fail(CASIMIR_EBUSY, "set the allocator before the first request");
+    if (!c->active.empty() || !c->queue.empty() || c->groups[0].sims) return fail(CASIMIR_EBUSY, "set the allocator before the first request");
     c->alloc = a;
     c->freef = f;
     c->user = user;
@@ -695,7 +780,10 @@ int casimir_plan_get_info(const casimir_plan_t *P, casimir_plan_info *info)
     info->n_cells = P->cells;
     info->cell_updates = P->cells * (int64_t)P->data.prob.n_steps;
     info->device_bytes = P->table_bytes + P->request_bytes;
-    info->bytes_per_update = 6 * (int64_t)P->rsize + 1;
+    // algorithmic bytes per cell-update: every stored field read and written once, plus the material id
+    bool full = !P->sims.empty() && P->sims[0].full;
+    int cf = full && P->sims[0].cplx ? 2 : 1;
+    info->bytes_per_update = (full ? 12 * cf : 6) * (int64_t)P->rsize + 1;
     return CASIMIR_OK;
 }
 

@@ -1,0 +1,166 @@
+// Internal host-side structures shared by the executor translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <array>
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "casimir.h"
+#include "kernels.h"
+#include "plan.h"
+
+namespace cas {
+int fail(int code, const std::string &msg);
+double now_ms();
+size_t align256(size_t b);
+}  // namespace cas
+
+#define CUDA_TRY(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) return cas::fail(CASIMIR_ECUDA, std::string(#expr ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+using namespace cas;
+
+struct HostSim {
+    int geo;
+    int nx, ny, nz;
+    int second_u;
+    int full;              // six-component kernel
+    int cplx;              // complex fields (Bloch phase)
+    int magnetic;
+    double kzA, kzB;       // real-phase d/dz factors (two-dimensional k_z runs)
+    int64_t field_off;     // element offset of this sim's block inside the request's field block
+    int64_t psi_off;       // element offset of its CPML planes (full kernel, -1: none)
+    int64_t lor_off;       // element offset of its Lorentz planes (full kernel, -1: none)
+    int tile0, ntile;      // range in the plan's tile list (2D) or tile6 list (full)
+    int ent0, nent;        // range in the plan's entry list (bucketed by tile)
+    int src0, nsrc;        // range in the plan's source list
+};
+
+struct HostTile {
+    int sim, i0, j0, ent0, ne;
+};
+
+struct HostTile6 {
+    int sim, count;
+    int64_t cell0;
+    int ent0, ne;
+};
+
+struct DevPlan {           // device copies of a plan's static tables (kept while the plan lives)
+    uint8_t *mat = nullptr;
+    void *coef = nullptr;
+    double *gw = nullptr;
+    DevEnt *ents = nullptr;
+    DevSrc *src = nullptr;
+    DevEnt6 *ents6 = nullptr;
+    DevSrc6 *src6 = nullptr;
+    double *lor = nullptr;
+    void *pml = nullptr;
+    size_t bytes = 0;
+    void *block = nullptr;
+};
+
+struct casimir_ctx;
+
+struct casimir_plan {
+    casimir_ctx *ctx = nullptr;
+    PlanData data;
+    int fp64 = 0;
+    size_t rsize = 4;
+    std::vector<HostSim> sims;
+    std::vector<HostTile> tiles;
+    std::vector<DevEnt> ents;
+    std::vector<DevSrc> src;
+    std::vector<int64_t> mat_off;     // per geo, bytes
+    std::vector<int64_t> coef_off;    // per geo, elements
+    std::vector<uint8_t> mat_all;
+    std::vector<double> coef_all;
+    std::vector<HostTile6> tiles6;
+    std::vector<DevEnt6> ents6;
+    std::vector<DevSrc6> src6;
+    std::vector<double> lor_all;      // per geo [id][6]
+    std::vector<int64_t> lor_off;     // per geo, elements
+    std::vector<double> pml_all;      // per geo, per PML axis [half][b, c, 1/kappa][n_a]
+    std::vector<std::array<int64_t, 3>> pml_off;   // per geo and axis, elements (-1: no PML)
+    int64_t field_elems = 0;          // per request
+    int64_t cells = 0;
+    int64_t table_bytes = 0;
+    int64_t request_bytes = 0;
+    DevPlan dev;
+    std::atomic<int> inflight{0};
+};
+
+struct casimir_request {
+    casimir_plan_t *plan = nullptr;
+    uint64_t tag = 0;
+    std::atomic<int> state{0};   // 0 queued, 1 running, 2 done, 3 failed
+    std::atomic<int> status{0};
+    std::atomic<bool> cancel{false};
+    double F[3] = {0, 0, 0};
+    double err = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int64_t s0 = 0;
+    int64_t launches = 0;
+    void *block = nullptr;   // fields, acc, tail
+    double *acc = nullptr, *tail = nullptr;
+    double *h_acc = nullptr;  // pinned copy-back (acc then tail)
+    cudaEvent_t done_ev = nullptr;
+    bool copy_issued = false;
+    std::vector<double> per_sim;
+};
+
+struct casimir_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    casimir_alloc_fn alloc = nullptr;
+    casimir_free_fn freef = nullptr;
+    void *user = nullptr;
+    double watchdog_ms = 0;
+    int64_t *d_launch = nullptr;
+    int64_t h_launch = 1;            // index of the next launch
+    // active set
+    std::vector<casimir_request *> active;
+    // launch groups: [0, 1] the 2D kernel in FP32 / FP64, [2 + 2*fp64 + cplx] the six-component kernel
+    struct Group {
+        void *sims = nullptr, *tiles = nullptr;
+        size_t sims_cap = 0, tiles_cap = 0;
+        int ntiles = 0;
+    } groups[6];
+    int ntiles = 0;                   // over all groups
+    bool dirty = true;
+    std::map<int, cudaGraphExec_t> graphs;    // per chunk length, for the current active set
+    // statistics
+    double step_ms = 0;
+    int64_t step_launches = 0;
+    int64_t cell_updates = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // worker
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<casimir_request *> queue;
+    std::thread worker;
+    bool worker_on = false;
+    bool stop = false;
+    std::atomic<int> sync_busy{0};
+};
+
+
+int dev_alloc(casimir_ctx *c, size_t bytes, void **out);
+void make_sim2d(const casimir_plan_t *P, char *blk, double *acc, double *tail, int64_t s0, size_t s, DevSim2D *d);
+void make_sim6(const casimir_plan_t *P, char *blk, double *acc, double *tail, int64_t s0, size_t s, DevSim6 *d);
+int upload_plan(casimir_plan_t *P, cudaStream_t st);
+void dev_free(casimir_ctx *c, void *p);

@@ -5,7 +5,7 @@
 
 namespace cas {
 
-constexpr int TILE_X = 32;
+constexpr int TILE_X = 120;   // four warp strips of 30 interior columns
 constexpr int TILE_Y = 32;
 
 // One simulation of a TM-form 2D kernel (TM, or TE on the dual lattice).
@@ -30,7 +30,7 @@ struct DevSim2D {
 };
 
 struct DevEnt {
-    int loc;               // (ly * TILE_X + lx) within the tile, array in bits 16..
+    int loc;               // (ly * TILE_X + lx) within the tile in bits 0..15, array in bits 16..
     int pad;
     double w;              // measurement weight
 };
@@ -46,6 +46,56 @@ struct DevSrc {
     int64_t idx;           // element index inside the sim's buffer 0 (array * N + site)
     double v;
 };
+
+// One simulation of the six-component kernel (k_z, Bloch, 3D; CPML; Lorentz).
+struct DevSim6 {
+    void *fields;          // E_x..E_z, H_x..H_z planes of N elements (re, im pairs when complex)
+    void *psi;             // CPML auxiliary fields, 4 planes per PML axis over its two slabs
+    void *lor;             // Lorentz P then P_prev per E component (NULL: non-dispersive)
+    const uint8_t *mat;    // per-cell material id
+    const void *coef;      // [id][6]: 1/eps at E_x..E_z sites, 1/mu at H_x..H_z sites (0 masks)
+    const double *lorentz; // [id][3][2]: (delta_eps, omega0) per E component
+    const void *pml;       // CPML profiles: axis a at pml_off[a]: [half][b, c, 1/kappa][n_a]
+    const double *gw;
+    double *acc;
+    double *tail;
+    int64_t s0;
+    int64_t psi_off[3];    // element offset of axis a's psi planes
+    int64_t slab[3];       // cells of one psi plane of axis a
+    int64_t pml_off[3];
+    int n[3];
+    int pml_d[3];          // CPML thickness per axis (0: none)
+    int dims, magnetic, T, tail_from;
+    double a, bs;          // sigma group: decay and dt/(1 + sigma dt/2)
+    double dt, dt_full, sigma, inv_dx;
+    double kz;             // complex fields: d/dz = i kz (two-dimensional runs)
+    double kzA, kzB;       // real fields: d/dz = kzA on {Ex, Ey, Hz}, kzB on {Ez, Hx, Hy}
+    double bre[3], bim[3]; // Bloch factors exp(i k_a L_a)
+};
+
+struct DevEnt6 {
+    int off;               // cell offset from the tile's first cell
+    int arr;               // field component 0..5
+    double wre, wim;
+};
+
+struct DevTile6 {
+    int sim;
+    int count;             // cells in this tile (<= 256)
+    int64_t cell0;
+    int ne;
+    int pad;
+    const DevEnt6 *ents;
+};
+
+struct DevSrc6 {
+    int64_t idx_re, idx_im;   // element indices in the sim's field block (idx_im < 0: real fields)
+    double re, im;
+};
+
+void launch_full(int fp64, int cplx, const DevSim6 *sims, const DevTile6 *tiles, int ntiles,
+                 const int64_t *launch_base, int64_t launch_add, int phase, cudaStream_t st);
+void launch_inject6(int fp64, void *fields, const DevSrc6 *src, int nsrc, cudaStream_t st);
 
 void launch_step2d(int fp64, const DevSim2D *sims, const DevTile *tiles, int ntiles,
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st);

@@ -198,12 +198,10 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err)
             if (std::fabs(g->bloch_im[a]) > 0) cplxf = true;
         }
     }
-    if (p.dims == 2) {
-        g->kz = k[2];
-        if (k[2] != 0.0) cplxf = true;
-    }
+    if (p.dims == 2) g->kz = k[2];
+    // a complex Bloch phase needs complex fields; k_z alone keeps them real (see the kernel)
     g->complex_fields = cplxf;
-    if (cplxf && family != FAM_FULL) { *err = "k_z or a complex Bloch phase needs polarization FULL"; return CASIMIR_EINVAL; }
+    if ((cplxf || g->kz != 0.0) && family != FAM_FULL) { *err = "k_z or a complex Bloch phase needs polarization FULL"; return CASIMIR_EINVAL; }
 
     int64_t ncell = (int64_t)p.n[0] * p.n[1] * p.n[2];
     g->mat.assign(ncell, 0);
@@ -384,6 +382,18 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
         }
     }
 
+    if (twod_pol) {
+        for (auto &o : P->objects)
+            if (o.kind == CASIMIR_MAT_LORENTZ) { *err = "Lorentz media need polarization FULL"; return CASIMIR_EINVAL; }
+        for (int a = 0; a < p.dims; ++a)
+            if (p.bc[a] == CASIMIR_BC_PML) { *err = "PML boundaries need polarization FULL"; return CASIMIR_EINVAL; }
+    }
+    // with d/dz -> i k_z the leapfrog is stable only for (dt/2)^2 (dims (2/dx)^2 + k_z^2) < 1
+    if (p.dims == 2)
+        for (auto &k : P->kpoints) {
+            double lim = 0.25 * P->dt * P->dt * (2.0 * 4.0 / (P->dx * P->dx) + k.k[2] * k.k[2]);
+            if (lim >= 1.0) { *err = "k_z beyond the time-step stability limit"; return CASIMIR_EINVAL; }
+        }
     // families
     std::vector<int> fams;
     if (p.polarization == CASIMIR_POL_TM || p.polarization == CASIMIR_POL_TETM) fams.push_back(FAM_TM);

@@ -9,13 +9,20 @@
 //
 // Layout (TM form): u at (i, j), vx at (i, j+1/2), vy at (i+1/2, j) in the
 // kernel's own lattice; TE runs the same update on the lattice shifted by half a
-// cell (u = H_z, v = -E).  One CTA updates one TILE_X x TILE_Y tile of one
-// simulation for one full step:
-//   first group (no sigma):  v <- v -/+ hf c_v d(u)          (sims with sigma on u)
-//                            u <- u  +  hf c_u curl(v)       (sims with sigma on v)
-//   second group (sigma):    u <- a u + bf c_u curl(v')      /  v <- a v -/+ bf c_v d(u')
-// The first group is recomputed on a one-cell halo so that both half steps
-// need a single pass over HBM: the fields ping-pong between two buffers.
+// cell (u = H_z, v = -E).  One step of one simulation:
+//   sigma on u:  v  <- v -/+ hf c_v d(u)              then  u <- a u + bf c_u curl(v')
+//   sigma on v:  u  <- u  +  hf c_u curl(v)           then  v <- a v -/+ bf c_v d(u')
+// (hf is halved on step 1: the leapfrog starts with a half step.)
+//
+// Execution: a CTA owns a TILE_X x TILE_Y tile of one simulation.  Each warp
+// owns a strip of STRIP columns plus one halo column on each side (lane 0 and
+// lane STRIP+1) and marches down the tile's rows, keeping the stencil in
+// registers: x neighbours come from warp shuffles, y neighbours from the row
+// carried over from the previous iteration.  Rows are prefetched in batches of
+// ROWS so that each lane has several independent loads in flight.  Both half
+// steps therefore need one read and one write of every field: the fields
+// ping-pong between two buffers (step parity).  After the march the tile's
+// pixels are read back (the block's own writes) for the projection.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -24,118 +31,163 @@ namespace cas {
 
 namespace {
 
-template <typename R>
-__device__ __forceinline__ double block_sum(double v, double *red)
+constexpr int STRIP = 30;                 // interior columns per warp
+constexpr int WARPS = TILE_X / STRIP;     // warps per CTA
+constexpr int ROWS = 4;                   // prefetch depth
+static_assert(WARPS * STRIP == TILE_X, "tile width must be a multiple of the strip");
+
+__device__ __forceinline__ int wrap(int i, int n)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    return s;
+    i += i < 0 ? n : 0;
+    return i >= n ? i - n : i;
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ R shfl_dn(R v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+template <typename R>
+__device__ __forceinline__ R shfl_up(R v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+
+template <typename R>
+__global__ void __launch_bounds__(WARPS * 32)
 k_step2d(const DevSim2D *__restrict__ sims, const DevTile *__restrict__ tiles,
          const int64_t *__restrict__ launch_base, int64_t launch_add)
 {
-    constexpr int SX = TILE_X + 2, SY = TILE_Y + 2;
-    __shared__ R su[SY][SX], svx[SY][SX], svy[SY][SX];
-    __shared__ uint8_t sm[SY][SX];
-    __shared__ double red[8];
-
+    __shared__ double red[WARPS];
     const DevTile t = tiles[blockIdx.x];
     const DevSim2D &S = sims[t.sim];
     const int64_t n = *launch_base + launch_add - S.s0;
     if (n < 1 || n > S.T) return;
 
     const int nx = S.nx, ny = S.ny;
-    const int w = min(TILE_X, nx - t.i0), h = min(TILE_Y, ny - t.j0);
     const size_t N = (size_t)nx * ny;
-    const R *src = reinterpret_cast<const R *>(S.fields) + ((n - 1) & 1) * 3 * N;
-    R *dst = reinterpret_cast<R *>(S.fields) + (n & 1) * 3 * N;
-    const R *coef = reinterpret_cast<const R *>(S.coef);
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const R *__restrict__ su = reinterpret_cast<const R *>(S.fields) + ((n - 1) & 1) * 3 * N;
+    const R *__restrict__ svx = su + N;
+    const R *__restrict__ svy = su + 2 * N;
+    R *__restrict__ du = reinterpret_cast<R *>(S.fields) + (n & 1) * 3 * N;
+    R *__restrict__ dvx = du + N;
+    R *__restrict__ dvy = du + 2 * N;
+    const R *__restrict__ coef = reinterpret_cast<const R *>(S.coef);
+    const uint8_t *__restrict__ mat = S.mat;
 
-    // tile plus a one-cell halo, periodic wrap (walls are masked sites)
-    for (int ly = ty; ly < h + 2; ly += 8) {
-        int gj = t.j0 + ly - 1;
-        gj += gj < 0 ? ny : 0;
-        gj -= gj >= ny ? ny : 0;
-        for (int lx = tx; lx < w + 2; lx += 32) {
-            int gi = t.i0 + lx - 1;
-            gi += gi < 0 ? nx : 0;
-            gi -= gi >= nx ? nx : 0;
-            size_t g = (size_t)gj * nx + gi;
-            su[ly][lx] = src[g];
-            svx[ly][lx] = src[N + g];
-            svy[ly][lx] = src[2 * N + g];
-            sm[ly][lx] = S.mat[g];
-        }
-    }
-    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i0 = t.i0 + warp * STRIP;               // first interior column of this strip
+    const int w = min(STRIP, nx - i0);                // interior columns (may be <= 0)
+    const int h = min(TILE_Y, ny - t.j0);
+    const int col = wrap(i0 - 1 + lane, nx);          // this lane's column (lane 0: left halo)
+    const bool store = w > 0 && lane >= 1 && lane <= w;
 
     const R hf = (R)(n == 1 ? 0.5 * S.hf : S.hf);
     const R a = (R)S.a, bf = (R)S.bf;
-    if (S.second_u) {
-        // first group v on [0, w] x [0, h] (vx needs lx >= 1, vy needs ly >= 1)
-        for (int ly = ty; ly <= h; ly += 8)
-            for (int lx = tx; lx <= w; lx += 32) {
-                int m = sm[ly][lx];
-                R uc = su[ly][lx];
-                if (lx >= 1) svx[ly][lx] = svx[ly][lx] - hf * coef[3 * m + 1] * (su[ly + 1][lx] - uc);
-                if (ly >= 1) svy[ly][lx] = svy[ly][lx] + hf * coef[3 * m + 2] * (su[ly][lx + 1] - uc);
-            }
-        __syncthreads();
-        for (int ly = 1 + ty; ly <= h; ly += 8)
-            for (int lx = 1 + tx; lx <= w; lx += 32) {
-                int m = sm[ly][lx];
-                R c = (svy[ly][lx] - svy[ly][lx - 1]) - (svx[ly][lx] - svx[ly - 1][lx]);
-                su[ly][lx] = a * su[ly][lx] + bf * coef[3 * m] * c;
-            }
-    } else {
-        // first group u on [1, w+1] x [1, h+1]
-        for (int ly = 1 + ty; ly <= h + 1; ly += 8)
-            for (int lx = 1 + tx; lx <= w + 1; lx += 32) {
-                int m = sm[ly][lx];
-                R c = (svy[ly][lx] - svy[ly][lx - 1]) - (svx[ly][lx] - svx[ly - 1][lx]);
-                su[ly][lx] = su[ly][lx] + hf * coef[3 * m] * c;
-            }
-        __syncthreads();
-        for (int ly = 1 + ty; ly <= h; ly += 8)
-            for (int lx = 1 + tx; lx <= w; lx += 32) {
-                int m = sm[ly][lx];
-                R uc = su[ly][lx];
-                svx[ly][lx] = a * svx[ly][lx] - bf * coef[3 * m + 1] * (su[ly + 1][lx] - uc);
-                svy[ly][lx] = a * svy[ly][lx] + bf * coef[3 * m + 2] * (su[ly][lx + 1] - uc);
-            }
-    }
-    __syncthreads();
 
-    for (int ly = 1 + ty; ly <= h; ly += 8) {
-        size_t g = (size_t)(t.j0 + ly - 1) * nx + t.i0;
-        for (int lx = 1 + tx; lx <= w; lx += 32) {
-            dst[g + lx - 1] = su[ly][lx];
-            dst[N + g + lx - 1] = svx[ly][lx];
-            dst[2 * N + g + lx - 1] = svy[ly][lx];
+    if (w > 0) {
+        if (S.second_u) {
+            // carried state: u of the current row, new vx of the previous row
+            int jm = wrap(t.j0 - 1, ny);
+            size_t gm = (size_t)jm * nx + col, g0 = (size_t)t.j0 * nx + col;
+            R u_prev = su[gm];
+            R u_cur = su[g0];
+            int mm = mat[gm];
+            R vxp = svx[gm] - hf * coef[3 * mm + 1] * (u_cur - u_prev);
+            for (int jb = 0; jb < h; jb += ROWS) {
+                R un[ROWS], vx[ROWS], vy[ROWS];
+                int mt[ROWS];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    int j = t.j0 + jb + r;
+                    if (jb + r < h) {
+                        size_t g = (size_t)j * nx + col;
+                        un[r] = su[(size_t)wrap(j + 1, ny) * nx + col];
+                        vx[r] = svx[g];
+                        vy[r] = svy[g];
+                        mt[r] = mat[g];
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    if (jb + r >= h) break;
+                    int m = mt[r];
+                    R cu = coef[3 * m], cvx = coef[3 * m + 1], cvy = coef[3 * m + 2];
+                    R vxn = vx[r] - hf * cvx * (un[r] - u_cur);
+                    R u_right = shfl_dn(u_cur);
+                    R vyn = vy[r] + hf * cvy * (u_right - u_cur);
+                    R vy_left = shfl_up(vyn);
+                    R unew = a * u_cur + bf * cu * ((vyn - vy_left) - (vxn - vxp));
+                    if (store) {
+                        size_t g = (size_t)(t.j0 + jb + r) * nx + col;
+                        du[g] = unew;
+                        dvx[g] = vxn;
+                        dvy[g] = vyn;
+                    }
+                    vxp = vxn;
+                    u_cur = un[r];
+                }
+            }
+        } else {
+            // carried state: old fields and new u of the current row
+            int jm = wrap(t.j0 - 1, ny);
+            size_t gm = (size_t)jm * nx + col, g0 = (size_t)t.j0 * nx + col;
+            R vx_prev = svx[gm];
+            R u_c = su[g0], vx_c = svx[g0], vy_c = svy[g0];
+            int m_c = mat[g0];
+            R vyl = shfl_up(vy_c);
+            R up_c = u_c + hf * coef[3 * m_c] * ((vy_c - vyl) - (vx_c - vx_prev));
+            for (int jb = 0; jb < h; jb += ROWS) {
+                R un[ROWS], vx[ROWS], vy[ROWS];
+                int mt[ROWS];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    if (jb + r < h) {
+                        size_t g = (size_t)wrap(t.j0 + jb + r + 1, ny) * nx + col;
+                        un[r] = su[g];
+                        vx[r] = svx[g];
+                        vy[r] = svy[g];
+                        mt[r] = mat[g];
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    if (jb + r >= h) break;
+                    // new u of the next row
+                    R vyl_n = shfl_up(vy[r]);
+                    R up_n = un[r] + hf * coef[3 * mt[r]] * ((vy[r] - vyl_n) - (vx[r] - vx_c));
+                    // sigma half step of v on the current row
+                    R cvx = coef[3 * m_c + 1], cvy = coef[3 * m_c + 2];
+                    R up_right = shfl_dn(up_c);
+                    R vxn = a * vx_c - bf * cvx * (up_n - up_c);
+                    R vyn = a * vy_c + bf * cvy * (up_right - up_c);
+                    if (store) {
+                        size_t g = (size_t)(t.j0 + jb + r) * nx + col;
+                        du[g] = up_c;
+                        dvx[g] = vxn;
+                        dvy[g] = vyn;
+                    }
+                    up_c = up_n;
+                    vx_c = vx[r];
+                    vy_c = vy[r];
+                    m_c = mt[r];
+                }
+            }
         }
     }
 
     if (t.ne > 0) {
         // surface functional of this tile's pixels, accumulated as w_n * s(n)
+        __syncthreads();                              // the block's field writes are visible
         double part = 0.0;
         for (int e = threadIdx.x; e < t.ne; e += blockDim.x) {
             DevEnt en = t.ents[e];
             int loc = en.loc & 0xffff, arr = en.loc >> 16;
-            int ly = loc / TILE_X + 1, lx = loc % TILE_X + 1;
-            R v = arr == 0 ? su[ly][lx] : (arr == 1 ? svx[ly][lx] : svy[ly][lx]);
+            int ly = loc / TILE_X, lx = loc - ly * TILE_X;
+            size_t g = (size_t)(t.j0 + ly) * nx + t.i0 + lx;
+            R v = arr == 0 ? du[g] : (arr == 1 ? dvx[g] : dvy[g]);
             part += en.w * (double)v;
         }
-        double s = block_sum<R>(part, red);
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+        if (lane == 0) red[warp] = part;
+        __syncthreads();
         if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int q = 0; q < WARPS; ++q) s += red[q];
             double c = S.gw[n - 1] * s;
             atomicAdd(S.acc, c);
             if (n > S.tail_from) atomicAdd(S.tail, c);
@@ -162,9 +214,9 @@ void launch_step2d(int fp64, const DevSim2D *sims, const DevTile *tiles, int nti
 {
     if (ntiles <= 0) return;
     if (fp64)
-        k_step2d<double><<<ntiles, 256, 0, st>>>(sims, tiles, launch_base, launch_add);
+        k_step2d<double><<<ntiles, WARPS * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
     else
-        k_step2d<float><<<ntiles, 256, 0, st>>>(sims, tiles, launch_base, launch_add);
+        k_step2d<float><<<ntiles, WARPS * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
 }
 
 void launch_inject(int fp64, void *fields, const DevSrc *src, int nsrc, cudaStream_t st)

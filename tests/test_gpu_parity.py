@@ -162,3 +162,62 @@ def test_budget_rejects_oversized_plan(pk):
         c.plan(W.config2_piston(W.config2_heights()[7], n_steps=100))
     assert e.value.code == -2
     c.close()
+
+
+# ---- six-component kernel: k_z cross-sections, Bloch cells, 3D; CPML; Lorentz ----------
+
+def _waveguides_small(prec, kz_list=(0.0, 1.3, 4.0)):
+    p = W.config3_waveguides(0.5, resolution=8, n_cells=48, pml_units=0.75, n_harm=3, n_steps=300,
+                             k_points=[{"k": [0, 0, k], "weight": 0.3} for k in kz_list], precision=prec)
+    return p
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_kz_pml_lorentz(ctx, prec):
+    p = _waveguides_small(prec)
+    _check(ctx, p, ("wg", prec), prec == "fp64")
+
+
+def test_full_bloch_complex(ctx):
+    import math
+    p = W._base(2, (16, 24, 1), 8.0, 300)
+    p["bc"] = ["periodic", "pml", "pec"]
+    p["pml_cells"] = [0, 4, 0]
+    p["objects"] = [{"shape": "box", "lo": [0.5, 1.0, 0], "hi": [1.5, 1.5, 0], "kind": "dielectric", "eps": 4.0, "mu": 1.0},
+                    {"shape": "box", "lo": [0.0, 1.9, 0], "hi": [2.0, 2.0, 0], "kind": "lorentz",
+                     "eps_inf": 1.0, "delta_eps": 3.0, "omega0": 2.0}]
+    p["faces"] = [{"axis": 1, "sign": -1, "pos": 0.75, "lo": [0, 0.75, 0], "hi": [2.0, 0.75, 0]},
+                  {"axis": 1, "sign": 1, "pos": 1.75, "lo": [0, 1.75, 0], "hi": [2.0, 1.75, 0]}]
+    p["n_harm"] = 4
+    p["polarization"] = "full"
+    p["force_axis"] = 1
+    p["k_points"] = [{"k": [2 * math.pi * m / (3 * 2.0), 0, 0.7 * m], "weight": 1 / 3} for m in range(3)]
+    p["precision"] = "fp64"
+    _check(ctx, p, "bloch", True)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_3d_sphere_notch(ctx, prec):
+    p = W.config4_sphere_notch(0.4, seed=3, resolution=6, n_cells=24, pml_cells=4, n_harm=2, n_steps=120,
+                               precision=prec, substrate_top=1.0)
+    _check(ctx, p, ("3d", prec), prec == "fp64")
+
+
+def test_mixed_2d_and_full_requests_share_the_batch(ctx):
+    probs = [W.piston_small(n_steps=400, precision="fp32"), _waveguides_small("fp32", (0.5,)),
+             W.piston_small(h=0.8, n_steps=250, precision="fp64"), _waveguides_small("fp64", (2.0,))]
+    alone = [ctx.plan(p).run()[0] for p in probs]
+    plans = [ctx.plan(p) for p in probs]
+    tickets = [pl.submit(tag=i) for i, pl in enumerate(plans)]
+    for a, t in zip(alone, tickets):
+        F, err, st = t.force(-1)
+        assert np.allclose(F, a, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("which", ["2d", "full"])
+def test_plain_path_matches_batched(ctx, which):
+    p = W.piston_small(n_steps=300, precision="fp64") if which == "2d" else _waveguides_small("fp64", (0.0, 2.5))
+    Fb, pb, _ = ctx.plan(p).run(per_sim=True)
+    Fp, pp, st = ctx.plan(p).run(per_sim=True, plain=True)
+    assert np.allclose(pp, pb, rtol=1e-9, atol=1e-13 * np.sum(np.abs(pb)))
+    assert st["kernel_launches"] > p["n_steps"]
