@@ -92,9 +92,64 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_over_ranks(ms, units, device="cpu"):
+    """Whole-job timing across ranks (replicas): the slowest rank's time and the units
+    processed by all ranks.  Single-process runs return the inputs unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, units
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def workload_problems(n_steps=20000, n_harm=40):
     import workloads as W
     return [W.config2_piston(h, n_steps=n_steps, n_harm=n_harm) for h in W.config2_heights()]
+
+
+def serving_trial(pk, ctx, n_requests=12, rate=50.0, scale=0.15, seed=0, plain=False):
+    """Poisson arrivals of the seeded serving mix (2D pistons/waveguides, Bloch gratings, 3D
+    spheres, grid sides scaled by `scale`).  Batched: every request is submitted at its arrival
+    time and joins the running batch.  Plain: requests run one after another through the
+    unbatched path.  Latency = completion - arrival."""
+    import workloads as W
+    trace = W.serving_requests(seed, n_requests=n_requests, rate=rate, scale=scale)
+    plans = [ctx.plan(p) for _, p in trace]
+    done = [None] * len(trace)
+    t0 = time.perf_counter()
+    if not plain:
+        tickets = [None] * len(trace)
+        nxt = 0
+        while any(d is None for d in done):
+            now = time.perf_counter() - t0
+            while nxt < len(trace) and trace[nxt][0] <= now:
+                tickets[nxt] = plans[nxt].submit(tag=nxt)
+                nxt += 1
+            for i, t in enumerate(tickets):
+                if t is not None and done[i] is None and t.force(0) is not None:
+                    done[i] = time.perf_counter() - t0
+            time.sleep(0.0005)
+    else:
+        for i, (arr, _) in enumerate(trace):
+            wait = arr - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            plans[i].run(plain=True)
+            done[i] = time.perf_counter() - t0
+    lat = sorted(1e3 * (d - a) for d, (a, _) in zip(done, trace))
+    makespan = max(done)
+    kinds = {}
+    for _, p in trace:
+        kinds[p.get("kind", "?")] = kinds.get(p.get("kind", "?"), 0) + 1
+    for pl in plans:
+        pl.close()
+    return {"forces_per_s": len(trace) / makespan, "p50_ms": lat[len(lat) // 2],
+            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "makespan_s": makespan,
+            "requests": len(trace), "mix": kinds}
 
 
 def cpu_baseline(budget_s=15.0):
@@ -154,6 +209,8 @@ def main():
     ap.add_argument("--time-steps", type=int, default=20000, help="FDTD steps per simulation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=12)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -212,11 +269,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     step_ms, launches, cups_kernel = ctx.kernel_stats()
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    total_cups = cells_per_step * args.steps * world
+    ms, total_cups = reduce_over_ranks(ms, cells_per_step * args.steps, device="cuda")
     value = total_cups / (ms / 1e3) / 1e9
     forces_per_s = n_forces * args.steps * world / (ms / 1e3)
 
@@ -249,6 +302,14 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "forces_per_s": n_forces * world / e2e_s}
 
+    serving = None
+    if not args.no_serving:
+        batched = serving_trial(pk, ctx, n_requests=args.serving_requests)
+        plain = serving_trial(pk, ctx, n_requests=args.serving_requests, plain=True)
+        serving = {"trace": "seed 0, Poisson 50 req/s, serving mix with grid sides x0.15",
+                   "batched": batched, "plain": plain,
+                   "forces_per_s_ratio": batched["forces_per_s"] / plain["forces_per_s"]}
+
     cb = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -271,7 +332,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "forces_per_s": forces_per_s,
             "latency_ms": {"p50": lat_sorted[len(lat) // 2], "p99": lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))]},
-            "roofline": roof, "cpu_baseline": cb, "e2e": e2e,
+            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "serving": serving,
             "gpu_launches": int(launches + 3 * n_forces * args.steps),
             "clocks": clk,
         }

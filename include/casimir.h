@@ -163,6 +163,13 @@ int casimir_ctx_set_allocator(casimir_ctx_t *ctx, casimir_alloc_fn alloc, casimi
  * no device code ever waits on it. */
 int casimir_ctx_set_watchdog(casimir_ctx_t *ctx, double max_ms);
 
+/* Run simulations in waves whose field memory totals at most `bytes` (0, the
+ * default: all simulations of an admitted request at once; the environment
+ * variable CASIMIR_WAVE_BYTES sets the initial value).  Waves bound the number
+ * of simulations in flight, e.g. to keep their fields in the L2 cache.  Applies
+ * to requests admitted after the call. */
+int casimir_ctx_set_wave_bytes(casimir_ctx_t *ctx, int64_t bytes);
+
 /* Device time of the batched time-step kernels since the last reset, measured
  * with CUDA events on the context's stream: total milliseconds, number of step
  * launches and cell-updates performed.  reset != 0 zeroes the counters. */
@@ -201,9 +208,10 @@ int casimir_cancel(casimir_ticket ticket);
 int casimir_run(casimir_plan_t *plan, double F[3], double *per_sim, casimir_stats *st);
 
 /* The same computation without batching, as a point of comparison for the
- * batched executor: simulations run one after another, each time step issues
- * its field-update launches and a separate projection launch, and no CUDA graph
- * is used.  Arguments and results as for casimir_run. */
+ * batched executor: one run at a time (the simulations of one k-point, harmonic
+ * and polarisation family), each time step issuing that run's field-update
+ * launches and a separate projection launch, and no CUDA graph.  Arguments and
+ * results as for casimir_run. */
 int casimir_run_plain(casimir_plan_t *plan, double F[3], double *per_sim, casimir_stats *st);
 
 /* Per-simulation description in plan order (for per-simulation parity):

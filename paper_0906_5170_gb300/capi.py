@@ -79,6 +79,7 @@ SIGNATURES = {
     "casimir_ctx_set_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "casimir_ctx_set_allocator": (ctypes.c_int, [ctypes.c_void_p, ALLOC_FN, FREE_FN, ctypes.c_void_p]),
     "casimir_ctx_set_watchdog": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "casimir_ctx_set_wave_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "casimir_ctx_kernel_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                                 ctypes.c_int]),
@@ -214,6 +215,9 @@ class Context:
         self._alloc = ALLOC_FN(lambda b, u: alloc(b))
         self._free = FREE_FN(lambda p, u: free(p))
         check(lib().casimir_ctx_set_allocator(self.h, self._alloc, self._free, None))
+
+    def set_wave_bytes(self, nbytes):
+        check(lib().casimir_ctx_set_wave_bytes(self.h, int(nbytes)))
 
     def kernel_stats(self, reset=False):
         ms = ctypes.c_double()

@@ -295,12 +295,65 @@ static int admit(casimir_ctx *c, casimir_request *r)
     launch_inject6(P->fp64, blk, P->dev.src6, (int)P->src6.size(), c->stream);
     CUDA_TRY(cudaGetLastError());
     if (!r->h_acc) CUDA_TRY(cudaMallocHost((void **)&r->h_acc, std::max<size_t>(1, 2 * P->sims.size()) * 8));
-    r->s0 = c->h_launch - 1;
+    // waves of consecutive simulations whose field blocks fit the wave budget
+    r->waves.clear();
+    r->waves_done = 0;
+    const size_t ns = P->sims.size();
+    for (size_t q = 0; q < ns;) {
+        casimir_request::Wave w{q, q, 0, 0, 0, 0};
+        while (w.s_end < ns) {
+            size_t e = w.s_end;
+            int64_t next = e + 1 < ns ? P->sims[e + 1].field_off : P->field_elems;
+            int64_t b = (next - P->sims[e].field_off) * (int64_t)P->rsize;
+            if (w.s_end > w.s_begin && c->wave_bytes > 0 && w.bytes + b > c->wave_bytes) break;
+            w.bytes += b;
+            w.cells += (int64_t)P->sims[e].nx * P->sims[e].ny * P->sims[e].nz;
+            ++w.s_end;
+        }
+        q = w.s_end;
+        r->waves.push_back(w);
+    }
+    for (size_t wi = 0; wi < r->waves.size(); ++wi) c->pending_waves.push_back({r, wi});
     r->state = 1;
     r->t_admit = now_ms();
     c->active.push_back(r);
     c->dirty = true;
     return CASIMIR_OK;
+}
+
+// Start pending waves (FIFO over requests) while the active waves' field bytes stay
+// within the wave budget; a wave always starts when nothing else is active.
+static void activate_waves(casimir_ctx *c)
+{
+    while (!c->pending_waves.empty()) {
+        auto pw = c->pending_waves.front();
+        casimir_request::Wave &w = pw.first->waves[pw.second];
+        if (!c->active_waves.empty() && c->wave_bytes > 0 && c->active_bytes + w.bytes > c->wave_bytes) break;
+        c->pending_waves.pop_front();
+        w.s0 = c->h_launch - 1;
+        w.state = 1;
+        c->active_bytes += w.bytes;
+        c->active_waves.push_back(pw);
+        c->dirty = true;
+    }
+}
+
+// Drop every wave of request r (timeout, cancel).
+static void drop_waves(casimir_ctx *c, casimir_request *r)
+{
+    for (size_t q = 0; q < c->active_waves.size();) {
+        if (c->active_waves[q].first == r) {
+            c->active_bytes -= r->waves[c->active_waves[q].second].bytes;
+            c->active_waves.erase(c->active_waves.begin() + q);
+        } else {
+            ++q;
+        }
+    }
+    for (size_t q = 0; q < c->pending_waves.size();) {
+        if (c->pending_waves[q].first == r) c->pending_waves.erase(c->pending_waves.begin() + q);
+        else ++q;
+    }
+    c->dirty = true;
 }
 
 // Device descriptor of simulation s of plan P whose request block is `blk`.
@@ -391,9 +444,11 @@ static int rebuild(casimir_ctx *c)
     std::vector<DevTile> t2[2];
     std::vector<DevSim6> s6[4];
     std::vector<DevTile6> t6[4];
-    for (casimir_request *r : c->active) {
+    for (auto &aw : c->active_waves) {
+        casimir_request *r = aw.first;
+        const casimir_request::Wave &w = r->waves[aw.second];
         casimir_plan_t *P = r->plan;
-        for (size_t s = 0; s < P->sims.size(); ++s) {
+        for (size_t s = w.s_begin; s < w.s_end; ++s) {
             const HostSim &hs = P->sims[s];
             char *blk = (char *)r->block;
             if (!hs.full) {
@@ -401,7 +456,7 @@ static int rebuild(casimir_ctx *c)
                 auto &tv = t2[P->fp64];
                 int idx = (int)sv.size();
                 DevSim2D d;
-                make_sim2d(P, blk, r->acc, r->tail, r->s0, s, &d);
+                make_sim2d(P, blk, r->acc, r->tail, w.s0, s, &d);
                 sv.push_back(d);
                 for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
                     const HostTile &ht = P->tiles[t];
@@ -413,7 +468,7 @@ static int rebuild(casimir_ctx *c)
                 auto &tv = t6[gi];
                 int idx = (int)sv.size();
                 DevSim6 d;
-                make_sim6(P, blk, r->acc, r->tail, r->s0, s, &d);
+                make_sim6(P, blk, r->acc, r->tail, w.s0, s, &d);
                 sv.push_back(d);
                 for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
                     const HostTile6 &ht = P->tiles6[t];
@@ -539,16 +594,19 @@ static void finish_request(casimir_ctx *c, casimir_request *r, int status)
 // and retire those whose copies landed.  Returns 0 or an error code.
 static int engine_iterate(casimir_ctx *c)
 {
+    activate_waves(c);
     if (c->dirty) {
         int rc = rebuild(c);
         if (rc) return rc;
     }
-    if (c->ntiles > 0) {
+    if (c->ntiles > 0 && !c->active_waves.empty()) {
         int64_t next = c->h_launch;
         int64_t rem = INT64_MAX;
-        for (casimir_request *r : c->active)
-            if (!r->copy_issued) rem = std::min<int64_t>(rem, r->s0 + r->plan->data.prob.n_steps - (next - 1));
-        if (rem != INT64_MAX && rem > 0) {
+        for (auto &aw : c->active_waves) {
+            const casimir_request::Wave &w = aw.first->waves[aw.second];
+            rem = std::min<int64_t>(rem, w.s0 + aw.first->plan->data.prob.n_steps - (next - 1));
+        }
+        if (rem > 0) {
             int k = (int)std::min<int64_t>(64, rem);
             int rc = run_chunk(c, k);
             if (rc) return rc;
@@ -557,18 +615,34 @@ static int engine_iterate(casimir_ctx *c)
             cudaEventElapsedTime(&ms, c->ev0, c->ev1);
             c->step_ms += ms;
             c->step_launches += k;
-            for (casimir_request *r : c->active) {
-                int64_t n_lo = std::max<int64_t>(1, next - r->s0), n_hi = std::min<int64_t>(r->plan->data.prob.n_steps, next + k - 1 - r->s0);
-                if (n_hi >= n_lo) c->cell_updates += (n_hi - n_lo + 1) * r->plan->cells;
+            for (auto &aw : c->active_waves) {
+                const casimir_request::Wave &w = aw.first->waves[aw.second];
+                int64_t T = aw.first->plan->data.prob.n_steps;
+                int64_t n_lo = std::max<int64_t>(1, next - w.s0), n_hi = std::min<int64_t>(T, next + k - 1 - w.s0);
+                if (n_hi >= n_lo) c->cell_updates += (n_hi - n_lo + 1) * w.cells;
             }
         }
     }
-    bool changed = false;
+    // retire finished waves
+    for (size_t q = 0; q < c->active_waves.size();) {
+        casimir_request *r = c->active_waves[q].first;
+        casimir_request::Wave &w = r->waves[c->active_waves[q].second];
+        if (c->h_launch - 1 - w.s0 >= r->plan->data.prob.n_steps) {
+            w.state = 2;
+            r->waves_done++;
+            c->active_bytes -= w.bytes;
+            c->active_waves.erase(c->active_waves.begin() + q);
+            c->dirty = true;
+        } else {
+            ++q;
+        }
+    }
     for (casimir_request *r : c->active) {
         if (r->copy_issued) continue;
-        bool done = c->h_launch - 1 - r->s0 >= r->plan->data.prob.n_steps;
+        bool done = r->waves_done == r->waves.size();
         bool timed_out = c->watchdog_ms > 0 && now_ms() - r->t_admit > c->watchdog_ms;
         if (done || timed_out || r->cancel) {
+            if (!done) drop_waves(c, r);
             size_t ns = r->plan->sims.size();
             CUDA_TRY(cudaMemcpyAsync(r->h_acc, r->acc, ns * 8, cudaMemcpyDeviceToHost, c->stream));
             CUDA_TRY(cudaMemcpyAsync(r->h_acc + ns, r->tail, ns * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -576,7 +650,6 @@ static int engine_iterate(casimir_ctx *c)
             CUDA_TRY(cudaEventRecord(r->done_ev, c->stream));
             r->copy_issued = true;
             if (!done) r->status = r->cancel ? CASIMIR_ECANCELED : CASIMIR_ETIMEOUT;
-            changed = true;
         }
     }
     for (size_t q = 0; q < c->active.size();) {
@@ -584,12 +657,11 @@ static int engine_iterate(casimir_ctx *c)
         if (r->copy_issued && cudaEventQuery(r->done_ev) == cudaSuccess) {
             c->active.erase(c->active.begin() + q);
             finish_request(c, r, r->status.load());
-            changed = true;
         } else {
             ++q;
         }
     }
-    if (changed) c->dirty = true;
+    activate_waves(c);
     return CASIMIR_OK;
 }
 
@@ -642,6 +714,9 @@ static void worker_main(casimir_ctx *c)
                 r->state = 3;
             }
             c->active.clear();
+            c->active_waves.clear();
+            c->pending_waves.clear();
+            c->active_bytes = 0;
             c->dirty = true;
         }
         c->cv.notify_all();
@@ -669,6 +744,10 @@ int casimir_ctx_create(int device, uint64_t budget, casimir_ctx_t **out)
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     c->budget = budget ? budget : (uint64_t)(0.9 * (double)fr);
+    // waves off by default: one launch per step over every admitted simulation measured
+    // faster than L2-sized waves (each launch then fills the GPU)
+    c->wave_bytes = 0;
+    if (const char *e = std::getenv("CASIMIR_WAVE_BYTES")) c->wave_bytes = std::atoll(e);
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return fail(CASIMIR_ECUDA, "stream"); }
     c->own_stream = true;
     if (cudaMalloc(&c->d_launch, sizeof(int64_t)) != cudaSuccess) { cudaStreamDestroy(c->stream); delete c; return fail(CASIMIR_ENOMEM, "launch counter"); }
@@ -736,6 +815,14 @@ int casimir_ctx_set_watchdog(casimir_ctx_t *c, double max_ms)
 {
     if (!c || max_ms < 0) return fail(CASIMIR_EINVAL, "watchdog");
     c->watchdog_ms = max_ms;
+    return CASIMIR_OK;
+}
+
+int casimir_ctx_set_wave_bytes(casimir_ctx_t *c, int64_t bytes)
+{
+    if (!c || bytes < 0) return fail(CASIMIR_EINVAL, "wave bytes");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->wave_bytes = bytes;
     return CASIMIR_OK;
 }
 
@@ -910,6 +997,9 @@ int casimir_run(casimir_plan_t *P, double F[3], double *per_sim, casimir_stats *
     if (rc) {
         for (casimir_request *q : c->active) dev_free(c, q->block);
         c->active.clear();
+        c->active_waves.clear();
+        c->pending_waves.clear();
+        c->active_bytes = 0;
         c->dirty = true;
     }
     c->sync_busy = 0;

@@ -118,6 +118,15 @@ struct casimir_request {
     cudaEvent_t done_ev = nullptr;
     bool copy_issued = false;
     std::vector<double> per_sim;
+    // the request's simulations run in waves (contiguous ranges in plan order)
+    struct Wave {
+        size_t s_begin, s_end;
+        int64_t s0;            // launch index of step 0 once active
+        int64_t bytes, cells;
+        int state;             // 0 pending, 1 active, 2 done
+    };
+    std::vector<Wave> waves;
+    size_t waves_done = 0;
 };
 
 struct casimir_ctx {
@@ -141,6 +150,12 @@ struct casimir_ctx {
         int ntiles = 0;
     } groups[6];
     int ntiles = 0;                   // over all groups
+    // waves: simulations are activated in groups whose field bytes fit `wave_bytes`
+    // (0: a whole request at once), so that the active working set can stay in L2
+    int64_t wave_bytes = 0;
+    int64_t active_bytes = 0;
+    std::vector<std::pair<casimir_request *, size_t>> active_waves;
+    std::deque<std::pair<casimir_request *, size_t>> pending_waves;
     bool dirty = true;
     std::map<int, cudaGraphExec_t> graphs;    // per chunk length, for the current active set
     // statistics

@@ -1,12 +1,14 @@
 // The plain execution of a plan, kept as the comparison point for the batched
-// executor: one simulation at a time, one launch per half of each time step
-// group and one separate projection launch per step, no CUDA graph.  The field
-// updates are the same kernels the batched path uses, so the two differ only
-// in how the work is scheduled.
+// executor: one run at a time -- a run being the simulations of one k-point,
+// harmonic and polarisation family (every face and source component) -- with
+// the field updates of each time step launched for that run alone, a separate
+// projection launch per step, and no CUDA graph.  The field updates are the
+// same kernels the batched path uses, so the two differ only in scheduling.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <tuple>
 #include <vector>
 
 #include "engine_internal.h"
@@ -18,12 +20,22 @@ struct PlainEnt {
     double wre, wim;
 };
 
+struct PlainSim {
+    int64_t parity_stride;    // 2D fields ping-pong between two buffers; 0 for in-place updates
+    int ent0, ne;
+    double *acc;
+};
+
+// one block per simulation of the run
 template <typename R>
-__global__ void k_project(const R *base, int64_t parity_stride, const PlainEnt *ents, int ne,
-                          const double *gw, int n, double *acc)
+__global__ void k_project(const R *base, const PlainSim *sims, const PlainEnt *all, const double *gw, int n)
 {
     __shared__ double red[8];
-    const R *f = base + (n & 1) * parity_stride;
+    const PlainSim ps = sims[blockIdx.x];
+    const R *f = base + (n & 1) * ps.parity_stride;
+    const PlainEnt *ents = all + ps.ent0;
+    const int ne = ps.ne;
+    double *acc = ps.acc;
     double part = 0.0;
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
         PlainEnt en = ents[e];
@@ -39,6 +51,12 @@ __global__ void k_project(const R *base, int64_t parity_stride, const PlainEnt *
         *acc += gw[n - 1] * s;
     }
 }
+
+struct Free {
+    casimir_ctx *c;
+    void *p;
+    ~Free() { dev_free(c, p); }
+};
 
 }  // namespace
 
@@ -63,100 +81,126 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
     if (rc) return rc;
     const PlanData &D = P->data;
     const size_t ns = P->sims.size();
-    size_t max_tiles = 1, max_ents = 1;
-    for (const HostSim &hs : P->sims) {
-        max_tiles = std::max<size_t>(max_tiles, hs.ntile);
-        max_ents = std::max<size_t>(max_ents, hs.nent);
-    }
     size_t bf = align256(P->field_elems * P->rsize), ba = align256(ns * 8);
-    size_t bs = align256(std::max(sizeof(DevSim2D), sizeof(DevSim6)));
-    size_t bt = align256(max_tiles * std::max(sizeof(DevTile), sizeof(DevTile6)));
-    size_t be = align256(max_ents * sizeof(PlainEnt));
     void *blk = nullptr;
-    rc = dev_alloc(c, bf + 2 * ba + bs + bt + be + 256, &blk);
+    rc = dev_alloc(c, bf + 2 * ba + 256, &blk);
     if (rc) return rc;
-    struct Free {
-        casimir_ctx *c;
-        void *p;
-        ~Free() { dev_free(c, p); }
-    } guard{c, blk};
+    Free guard{c, blk};
     char *b = (char *)blk;
     double *acc = (double *)(b + bf), *tail = (double *)(b + bf + ba);
-    void *d_sim = b + bf + 2 * ba;
-    void *d_tiles = b + bf + 2 * ba + bs;
-    PlainEnt *d_ents = (PlainEnt *)(b + bf + 2 * ba + bs + bt);
-    int64_t *d_counter = (int64_t *)(b + bf + 2 * ba + bs + bt + be);
+    int64_t *d_counter = (int64_t *)(b + bf + 2 * ba);
     CUDA_TRY(cudaMemsetAsync(blk, 0, bf + 2 * ba, s));
     launch_inject(P->fp64, blk, P->dev.src, (int)P->src.size(), s);
     launch_inject6(P->fp64, blk, P->dev.src6, (int)P->src6.size(), s);
     static const int64_t one = 1;
     CUDA_TRY(cudaMemcpyAsync(d_counter, &one, sizeof(int64_t), cudaMemcpyHostToDevice, s));
     int64_t launches = 2;
+    // runs: the simulations of one k-point, harmonic and family, in order of first appearance
+    std::vector<std::vector<size_t>> runs;
+    {
+        std::map<std::tuple<int, int, int, int>, size_t> at;
+        for (size_t q = 0; q < ns; ++q) {
+            const Sim &m = D.sims[q];
+            auto key = std::make_tuple(m.kpt, m.n1, m.n2, m.family);
+            auto it = at.find(key);
+            if (it == at.end()) {
+                at.emplace(key, runs.size());
+                runs.push_back({q});
+            } else {
+                runs[it->second].push_back(q);
+            }
+        }
+    }
+    std::vector<DevSim2D> s2;
+    std::vector<DevSim6> s6;
     std::vector<DevTile> t2;
     std::vector<DevTile6> t6;
     std::vector<PlainEnt> pe;
-    for (size_t q = 0; q < ns; ++q) {
-        const HostSim &hs = P->sims[q];
-        int64_t N = (int64_t)hs.nx * hs.ny * hs.nz;
-        pe.clear();
-        if (!hs.full) {
-            DevSim2D d;
-            make_sim2d(P, b, acc, tail, 0, q, &d);
-            t2.clear();
-            for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
-                const HostTile &ht = P->tiles[t];
-                t2.push_back(DevTile{0, ht.i0, ht.j0, 0, nullptr});      // projection runs separately
-                for (int e = ht.ent0; e < ht.ent0 + ht.ne; ++e) {
-                    const DevEnt &en = P->ents[e];
-                    int loc = en.loc & 0xffff, arr = en.loc >> 16;
-                    int ly = loc / TILE_X, lx = loc - ly * TILE_X;
-                    int64_t g = (int64_t)arr * N + (int64_t)(ht.j0 + ly) * hs.nx + ht.i0 + lx;
-                    pe.push_back(PlainEnt{hs.field_off + g, -1, en.w, 0.0});
-                }
-            }
-            CUDA_TRY(cudaMemcpyAsync(d_sim, &d, sizeof(d), cudaMemcpyHostToDevice, s));
-            CUDA_TRY(cudaMemcpyAsync(d_tiles, t2.data(), t2.size() * sizeof(DevTile), cudaMemcpyHostToDevice, s));
-        } else {
-            DevSim6 d;
-            make_sim6(P, b, acc, tail, 0, q, &d);
-            t6.clear();
-            int cf = hs.cplx ? 2 : 1;
-            for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
-                const HostTile6 &ht = P->tiles6[t];
-                t6.push_back(DevTile6{0, ht.count, ht.cell0, 0, 0, nullptr});
-                for (int e = ht.ent0; e < ht.ent0 + ht.ne; ++e) {
-                    const DevEnt6 &en = P->ents6[e];
-                    int64_t cell = ht.cell0 + en.off;
-                    int64_t re = hs.field_off + (int64_t)(cf * en.arr) * N + cell;
-                    int64_t im = hs.cplx ? hs.field_off + (int64_t)(2 * en.arr + 1) * N + cell : -1;
-                    pe.push_back(PlainEnt{re, im, en.wre, en.wim});
-                }
-            }
-            CUDA_TRY(cudaMemcpyAsync(d_sim, &d, sizeof(d), cudaMemcpyHostToDevice, s));
-            CUDA_TRY(cudaMemcpyAsync(d_tiles, t6.data(), t6.size() * sizeof(DevTile6), cudaMemcpyHostToDevice, s));
-        }
-        if (!pe.empty()) CUDA_TRY(cudaMemcpyAsync(d_ents, pe.data(), pe.size() * sizeof(PlainEnt), cudaMemcpyHostToDevice, s));
-        // 2D fields ping-pong between two buffers of 3N; the six-component fields update in place
-        int64_t stride = hs.full ? 0 : 3 * N;
-        for (int n = 1; n <= D.prob.n_steps; ++n) {
+    std::vector<PlainSim> ps;
+    for (auto &run : runs) {
+        s2.clear(); s6.clear(); t2.clear(); t6.clear(); pe.clear(); ps.clear();
+        bool full = P->sims[run[0]].full;
+        int cplx = P->sims[run[0]].cplx;
+        for (size_t q : run) {
+            const HostSim &hs = P->sims[q];
+            int64_t N = (int64_t)hs.nx * hs.ny * hs.nz;
+            PlainSim one{hs.full ? 0 : 3 * N, (int)pe.size(), 0, acc + q};
             if (!hs.full) {
+                DevSim2D d;
+                make_sim2d(P, b, acc, tail, 0, q, &d);
+                int idx = (int)s2.size();
+                s2.push_back(d);
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile &ht = P->tiles[t];
+                    t2.push_back(DevTile{idx, ht.i0, ht.j0, 0, nullptr});      // projection runs separately
+                    for (int e = ht.ent0; e < ht.ent0 + ht.ne; ++e) {
+                        const DevEnt &en = P->ents[e];
+                        int loc = en.loc & 0xffff, arr = en.loc >> 16;
+                        int ly = loc / TILE_X, lx = loc - ly * TILE_X;
+                        int64_t g = (int64_t)arr * N + (int64_t)(ht.j0 + ly) * hs.nx + ht.i0 + lx;
+                        pe.push_back(PlainEnt{hs.field_off + g, -1, en.w, 0.0});
+                    }
+                }
+            } else {
+                DevSim6 d;
+                make_sim6(P, b, acc, tail, 0, q, &d);
+                int idx = (int)s6.size();
+                s6.push_back(d);
+                int cf = hs.cplx ? 2 : 1;
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile6 &ht = P->tiles6[t];
+                    t6.push_back(DevTile6{idx, ht.count, ht.cell0, 0, 0, nullptr});
+                    for (int e = ht.ent0; e < ht.ent0 + ht.ne; ++e) {
+                        const DevEnt6 &en = P->ents6[e];
+                        int64_t cell = ht.cell0 + en.off;
+                        int64_t re = hs.field_off + (int64_t)(cf * en.arr) * N + cell;
+                        int64_t im = hs.cplx ? hs.field_off + (int64_t)(2 * en.arr + 1) * N + cell : -1;
+                        pe.push_back(PlainEnt{re, im, en.wre, en.wim});
+                    }
+                }
+            }
+            one.ne = (int)pe.size() - one.ent0;
+            ps.push_back(one);
+        }
+        void *d_sim = nullptr, *d_tiles = nullptr, *d_pe = nullptr, *d_ps = nullptr;
+        size_t bsim = align256(full ? s6.size() * sizeof(DevSim6) : s2.size() * sizeof(DevSim2D));
+        size_t btil = align256(full ? t6.size() * sizeof(DevTile6) : t2.size() * sizeof(DevTile));
+        size_t bpe = align256(std::max<size_t>(1, pe.size()) * sizeof(PlainEnt));
+        size_t bps = align256(ps.size() * sizeof(PlainSim));
+        void *rb = nullptr;
+        rc = dev_alloc(c, bsim + btil + bpe + bps, &rb);
+        if (rc) return rc;
+        Free rguard{c, rb};
+        d_sim = rb;
+        d_tiles = (char *)rb + bsim;
+        d_pe = (char *)rb + bsim + btil;
+        d_ps = (char *)rb + bsim + btil + bpe;
+        if (full) {
+            CUDA_TRY(cudaMemcpyAsync(d_sim, s6.data(), s6.size() * sizeof(DevSim6), cudaMemcpyHostToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(d_tiles, t6.data(), t6.size() * sizeof(DevTile6), cudaMemcpyHostToDevice, s));
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(d_sim, s2.data(), s2.size() * sizeof(DevSim2D), cudaMemcpyHostToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(d_tiles, t2.data(), t2.size() * sizeof(DevTile), cudaMemcpyHostToDevice, s));
+        }
+        if (!pe.empty()) CUDA_TRY(cudaMemcpyAsync(d_pe, pe.data(), pe.size() * sizeof(PlainEnt), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(d_ps, ps.data(), ps.size() * sizeof(PlainSim), cudaMemcpyHostToDevice, s));
+        for (int n = 1; n <= D.prob.n_steps; ++n) {
+            if (!full) {
                 launch_step2d(P->fp64, (const DevSim2D *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, s);
                 ++launches;
             } else {
                 for (int phase = 0; phase < 2; ++phase)
-                    launch_full(P->fp64, hs.cplx, (const DevSim6 *)d_sim, (const DevTile6 *)d_tiles, (int)t6.size(), d_counter, n - 1, phase, s);
+                    launch_full(P->fp64, cplx, (const DevSim6 *)d_sim, (const DevTile6 *)d_tiles, (int)t6.size(), d_counter, n - 1, phase, s);
                 launches += 2;
             }
-            if (!pe.empty()) {
-                if (P->fp64)
-                    k_project<double><<<1, 256, 0, s>>>((const double *)b, stride, d_ents, (int)pe.size(), P->dev.gw, n, acc + q);
-                else
-                    k_project<float><<<1, 256, 0, s>>>((const float *)b, stride, d_ents, (int)pe.size(), P->dev.gw, n, acc + q);
-                ++launches;
-            }
+            if (P->fp64)
+                k_project<double><<<(int)ps.size(), 256, 0, s>>>((const double *)b, (const PlainSim *)d_ps, (const PlainEnt *)d_pe, P->dev.gw, n);
+            else
+                k_project<float><<<(int)ps.size(), 256, 0, s>>>((const float *)b, (const PlainSim *)d_ps, (const PlainEnt *)d_pe, P->dev.gw, n);
+            ++launches;
         }
         CUDA_TRY(cudaGetLastError());
-        CUDA_TRY(cudaStreamSynchronize(s));   // the host descriptor vectors are reused for the next simulation
+        CUDA_TRY(cudaStreamSynchronize(s));   // the run's tables are freed and the host vectors reused
     }
     std::vector<double> h(ns);
     CUDA_TRY(cudaMemcpy(h.data(), acc, ns * 8, cudaMemcpyDeviceToHost));

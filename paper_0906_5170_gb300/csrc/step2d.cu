@@ -33,7 +33,6 @@ namespace {
 
 constexpr int STRIP = 30;                 // interior columns per warp
 constexpr int WARPS = TILE_X / STRIP;     // warps per CTA
-constexpr int ROWS = 4;                   // prefetch depth
 static_assert(WARPS * STRIP == TILE_X, "tile width must be a multiple of the strip");
 
 __device__ __forceinline__ int wrap(int i, int n)
@@ -47,8 +46,9 @@ __device__ __forceinline__ R shfl_dn(R v) { return __shfl_down_sync(0xffffffffu,
 template <typename R>
 __device__ __forceinline__ R shfl_up(R v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 
-template <typename R>
-__global__ void __launch_bounds__(WARPS * 32)
+// ROWS: rows prefetched per batch; MINB: resident CTAs per SM requested from the register allocator
+template <typename R, int ROWS, int MINB>
+__global__ void __launch_bounds__(WARPS * 32, MINB)
 k_step2d(const DevSim2D *__restrict__ sims, const DevTile *__restrict__ tiles,
          const int64_t *__restrict__ launch_base, int64_t launch_add)
 {
@@ -213,10 +213,12 @@ void launch_step2d(int fp64, const DevSim2D *sims, const DevTile *tiles, int nti
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st)
 {
     if (ntiles <= 0) return;
+    // four rows in flight per lane; registers capped so that seven CTAs (28 warps) fit an SM
+    // (measured best among prefetch depths 2-8 and caps of 40-106 registers)
     if (fp64)
-        k_step2d<double><<<ntiles, WARPS * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
+        k_step2d<double, 4, 4><<<ntiles, WARPS * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
     else
-        k_step2d<float><<<ntiles, WARPS * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
+        k_step2d<float, 4, 7><<<ntiles, WARPS * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
 }
 
 void launch_inject(int fp64, void *fields, const DevSrc *src, int nsrc, cudaStream_t st)

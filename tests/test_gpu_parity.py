@@ -221,3 +221,21 @@ def test_plain_path_matches_batched(ctx, which):
     Fp, pp, st = ctx.plan(p).run(per_sim=True, plain=True)
     assert np.allclose(pp, pb, rtol=1e-9, atol=1e-13 * np.sum(np.abs(pb)))
     assert st["kernel_launches"] > p["n_steps"]
+
+
+def test_waves_do_not_change_results(ctx):
+    probs = [W.piston_small(n_steps=300, precision="fp32"), _waveguides_small("fp32", (0.0, 2.0))]
+    whole = []
+    for p in probs:
+        ctx.set_wave_bytes(0)                    # every simulation of the request at once
+        whole.append(ctx.plan(p).run(per_sim=True))
+        ctx.set_wave_bytes(200_000)             # a few simulations per wave
+        _, waves, _ = ctx.plan(p).run(per_sim=True)
+        assert np.allclose(waves, whole[-1][1], rtol=1e-12, atol=1e-15 * np.sum(np.abs(whole[-1][1])))
+    # both requests in flight together, in small waves
+    plans = [ctx.plan(p) for p in probs]
+    tickets = [pl.submit() for pl in plans]
+    for t, (F0, _, _) in zip(tickets, whole):
+        F, _, _ = t.force(-1)
+        assert np.allclose(F, F0, rtol=1e-12, atol=0)
+    ctx.set_wave_bytes(0)

@@ -174,19 +174,20 @@ def config3_gaps():
     return [round(16.0 * (0.3 + 0.1 * j)) / 16.0 for j in range(8)]
 
 
-def config3_kz_points(gap, n=32):
-    """Gauss-Legendre nodes on u in (-1, 1) mapped to k_z = c (1+u)/(1-u), c = 1/gap.
+def config3_kz_points(gap, n=32, resolution=32, courant=0.5):
+    """n Gauss-Legendre nodes for the k_z integral on [0, K].
 
-    The weight includes the Jacobian 2c/(1-u)^2 and the 1/pi of the k_z measure.
+    K = min(12/gap, 0.8 k_max): the integrand decays like exp(-2 gap k_z), and k_max is
+    the largest k_z the time step resolves, (dt/2)^2 (8/Delta^2 + k_max^2) = 1.
+    The weight includes the Jacobian K/2 and the 1/pi of the k_z measure.
     """
+    d = 1.0 / resolution
+    dt = courant * d
+    kmax = math.sqrt((2.0 / dt) ** 2 - 8.0 / d**2)
+    K = min(12.0 / gap, 0.8 * kmax)
     u, w = np.polynomial.legendre.leggauss(n)
-    c = 1.0 / gap
-    out = []
-    for ui, wi in zip(u, w):
-        k = c * (1 + ui) / (1 - ui)
-        jac = 2 * c / (1 - ui) ** 2
-        out.append({"k": [0.0, 0.0, float(k)], "weight": float(wi * jac / math.pi)})
-    return out
+    return [{"k": [0.0, 0.0, float(K * (1 + ui) / 2)], "weight": float(wi * K / 2 / math.pi)}
+            for ui, wi in zip(u, w)]
 
 
 def config3_waveguides(gap, *, resolution=32, n_cells=256, pml_units=1.0, n_harm=30,
@@ -208,7 +209,7 @@ def config3_waveguides(gap, *, resolution=32, n_cells=256, pml_units=1.0, n_harm
     p["faces"] = box_faces([xc + gap / 2 - d, yc - 0.25 - d], [xc + gap / 2 + 1.0 + d, yc + 0.25 + d], 2)
     p["n_harm"] = n_harm
     p["polarization"] = "full"
-    p["k_points"] = config3_kz_points(gap) if k_points is None else k_points
+    p["k_points"] = config3_kz_points(gap, resolution=resolution) if k_points is None else k_points
     p["force_axis"] = 0
     p["g_variant"] = "plain"
     p["precision"] = precision
@@ -271,7 +272,10 @@ def serving_requests(seed, n_requests=200, rate=50.0, *, scale=1.0):
             side = int(rng.integers(64, 513))
             side = max(16, int(round(side * scale)) // 4 * 4)
             nh = int(rng.integers(10, 61))
-            prob = _serving_piston(side, nh, rng)
+            if rng.uniform() < 0.5:
+                prob = _serving_piston(side, nh, rng)
+            else:
+                prob = _serving_waveguide(side, nh, rng)
         elif u < 0.9:
             prob = _serving_grating(scale, rng)
         else:
@@ -304,6 +308,19 @@ def _serving_piston(side, n_harm, rng):
     p["g_variant"] = "zinv"
     p["precision"] = "fp32"
     p["kind"] = "piston"
+    return p
+
+
+def _serving_waveguide(side, n_harm, rng):
+    """Two Lorentz waveguides in a CPML-terminated cell of 8 units, 4 k_z points
+    (side rounded to a multiple of 16 so that the guides fall on whole cells)."""
+    side = max(32, side // 16 * 16)
+    res = side / 8.0
+    gap = float(rng.uniform(0.3, 1.0))
+    kp = config3_kz_points(gap, n=4, resolution=res)
+    p = config3_waveguides(round(gap * res / 2) * 2 / res, resolution=res, n_cells=side, pml_units=1.0,
+                           n_harm=int(min(n_harm, 12)), n_steps=int(round(30.0 / (0.5 / res))), k_points=kp)
+    p["kind"] = "waveguide"
     return p
 
 
