@@ -152,6 +152,40 @@ def serving_trial(pk, ctx, n_requests=12, rate=50.0, scale=0.15, seed=0, plain=F
             "requests": len(trace), "mix": kinds}
 
 
+def measure_configs(pk, ctx, peak):
+    """The other configurations, each timed once after a warm-up run (device-resident
+    tables): Gcell-updates/s of the step kernels and the fraction of the HBM roofline on
+    algorithmic bytes.  Bounded subsets where the full configuration would take minutes."""
+    import workloads as W
+    out = {}
+    kp = W.config3_kz_points(0.5)
+    cases = {
+        "plates_2d_tm_fp64_full": ([W.config1_plates()], "full configuration (24 sims, 60x40, 4000 steps, FP64)"),
+        "waveguides_kz_cpml_lorentz": ([W.config3_waveguides(0.5, k_points=[kp[i] for i in (0, 8, 16, 24)])],
+                                       "gap 0.5, 4 of 32 k_z points, 30 harmonics, 256x256, 3840 steps"),
+        "sphere_notch_3d": ([W.config4_sphere_notch(0.55, seed=1, n_harm=1)],
+                            "height 0.55, 1 harmonic per face (20 sims), 160^3, 3200 steps"),
+    }
+    for name, (probs, desc) in cases.items():
+        plans = [ctx.plan(p) for p in probs]
+        for pl in plans:
+            pl.run()
+        ctx.kernel_stats(reset=True)
+        t0 = time.perf_counter()
+        for pl in plans:
+            pl.run()
+        wall = time.perf_counter() - t0
+        ms, nl, cu = ctx.kernel_stats()
+        b = plans[0].info()["bytes_per_update"]
+        gcu = cu / (ms / 1e3) / 1e9
+        out[name] = {"workload": desc, "gcell_updates_per_s": gcu, "bytes_per_cell_update": b,
+                     "hbm_frac": gcu * b / peak, "forces_per_s": len(plans) / wall,
+                     "kernel_ms": ms, "launches": nl}
+        for pl in plans:
+            pl.close()
+    return out
+
+
 def cpu_baseline(budget_s=15.0):
     """The FP64 oracle on a bounded sample of the workload: simulations of the
     h = 0.5 geometry for a shortened number of steps, one per host core."""
@@ -211,6 +245,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=12)
+    ap.add_argument("--no-configs", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -295,7 +330,7 @@ def main():
         e2e_s = time.perf_counter() - t0
         for pl in fresh:
             i = pl.info()
-            h2d += i["device_bytes"]
+            h2d += i["upload_bytes"]          # the plan's tables; fields are zeroed and seeded on the device
             d2h += 2 * 8 * i["n_sims"]
             pl.close()
         e2e = {"value": cells_per_step * world / e2e_s / 1e9, "unit": "Gcell-updates/s",
@@ -309,6 +344,10 @@ def main():
         serving = {"trace": "seed 0, Poisson 50 req/s, serving mix with grid sides x0.15",
                    "batched": batched, "plain": plain,
                    "forces_per_s_ratio": batched["forces_per_s"] / plain["forces_per_s"]}
+
+    others = None
+    if not args.no_configs:
+        others = measure_configs(pk, ctx, peaks()[0])
 
     cb = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -332,7 +371,7 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "forces_per_s": forces_per_s,
             "latency_ms": {"p50": lat_sorted[len(lat) // 2], "p99": lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))]},
-            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "serving": serving,
+            "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "serving": serving, "other_configs": others,
             "gpu_launches": int(launches + 3 * n_forces * args.steps),
             "clocks": clk,
         }

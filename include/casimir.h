@@ -131,6 +131,7 @@ typedef struct {
     int64_t cell_updates;      /* n_cells * n_steps */
     int64_t device_bytes;      /* device memory the plan needs while running */
     int64_t bytes_per_update;  /* algorithmic bytes per cell-update of the dominant kernel */
+    int64_t upload_bytes;      /* host-to-device bytes copied when the plan is first admitted */
 } casimir_plan_info;
 
 typedef struct {

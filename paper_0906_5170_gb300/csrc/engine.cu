@@ -871,6 +871,7 @@ int casimir_plan_get_info(const casimir_plan_t *P, casimir_plan_info *info)
     bool full = !P->sims.empty() && P->sims[0].full;
     int cf = full && P->sims[0].cplx ? 2 : 1;
     info->bytes_per_update = (full ? 12 * cf : 6) * (int64_t)P->rsize + 1;
+    info->upload_bytes = P->table_bytes;
     return CASIMIR_OK;
 }
 

@@ -137,9 +137,11 @@ k_full(const DevSim6 *__restrict__ sims, const DevTile6 *__restrict__ tiles,
     const size_t m = t.cell0 + threadIdx.x;
     if (m < N && threadIdx.x < t.count) {
         int c3[3];
-        c3[0] = (int)(m % S.n[0]);
-        c3[1] = (int)((m / S.n[0]) % S.n[1]);
-        c3[2] = (int)(m / ((size_t)S.n[0] * S.n[1]));
+        const unsigned mm = (unsigned)m, nx = (unsigned)S.n[0], ny = (unsigned)S.n[1];
+        const unsigned row = mm / nx;
+        c3[0] = (int)(mm - row * nx);
+        c3[1] = (int)(row % ny);
+        c3[2] = (int)(row / ny);
         const int id = S.mat[m];
         const R *coef = reinterpret_cast<const R *>(S.coef) + 6 * id;
         if (updE) {
