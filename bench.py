@@ -313,7 +313,8 @@ def main():
     achieved = cups_kernel * b_alg / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm if achieved else None, "traffic": None,
-            "kernel": "k_step2d<float>", "bytes_per_cell_update": b_alg,
+            "kernel": ("k_step2d_t2<float> (two steps per launch)" if os.environ.get("CASIMIR_STEP2D_K", "2") == "2"
+                       else "k_step2d<float>"), "bytes_per_cell_update": b_alg,
             "avg_launch_ms": step_ms / max(1, launches), "peak_source": peak_kind}
 
     e2e = None

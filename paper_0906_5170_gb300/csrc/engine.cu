@@ -148,6 +148,34 @@ static int prepare_plan(casimir_plan_t *P)
             hs.src0 = (int)P->src.size();
             for (const Entry &e : sm.src) P->src.push_back(DevSrc{hs.field_off + e.arr * N + e.idx, e.re});
             hs.nsrc = (int)P->src.size() - hs.src0;
+            // two-step tiles: TILE_X2 wide, entries sorted by row with per-row offsets
+            {
+                int tx2 = (hs.nx + TILE_X2 - 1) / TILE_X2;
+                std::vector<std::vector<std::pair<int, DevEnt>>> b2(tx2 * ty);
+                for (const Entry &e : sm.meas) {
+                    int i = (int)(e.idx % hs.nx), j = (int)(e.idx / hs.nx);
+                    int ti = i / TILE_X2, tj = j / TILE_Y;
+                    int ly = j - tj * TILE_Y, lx = i - ti * TILE_X2;
+                    b2[tj * tx2 + ti].push_back({ly * TILE_X2 + lx, DevEnt{(ly * TILE_X2 + lx) | (e.arr << 16), 0, e.re}});
+                }
+                hs.tile2_0 = (int)P->tiles2.size();
+                for (int tj = 0; tj < ty; ++tj)
+                    for (int ti = 0; ti < tx2; ++ti) {
+                        auto &b = b2[tj * tx2 + ti];
+                        std::stable_sort(b.begin(), b.end(), [](const std::pair<int, DevEnt> &x, const std::pair<int, DevEnt> &y) {
+                            return x.first < y.first;
+                        });
+                        HostTile2 ht{(int)s, ti * TILE_X2, tj * TILE_Y, (int)P->ents2.size(), (int)b.size(), (int)P->rowptr2.size()};
+                        int k = 0;
+                        for (int ly = 0; ly <= TILE_Y; ++ly) {
+                            while (k < (int)b.size() && b[k].first / TILE_X2 < ly) ++k;
+                            P->rowptr2.push_back(ly == TILE_Y ? (int)b.size() : k);
+                        }
+                        for (auto &pe : b) P->ents2.push_back(pe.second);
+                        P->tiles2.push_back(ht);
+                    }
+                hs.ntile2 = (int)P->tiles2.size() - hs.tile2_0;
+            }
         } else {
             hs.cplx = g.complex_fields ? 1 : 0;
             int cf = hs.cplx ? 2 : 1;
@@ -169,19 +197,19 @@ static int prepare_plan(casimir_plan_t *P)
                 off += 6 * cf * N;
             }
             off = (off + 63) & ~(int64_t)63;
-            int ntile = (int)((N + 255) / 256);
+            int ntile = (int)((N + TILE6 - 1) / TILE6);
             hs.tile0 = (int)P->tiles6.size();
             hs.ntile = ntile;
             std::vector<std::vector<DevEnt6>> bucket(ntile);
             for (const Entry &e : sm.meas) {
                 if (!hs.cplx && g.n[2] == 1 && D.prob.dims == 2 && inA(e.arr) != inA(sarr)) continue;   // contributes i * real: no real part
-                int tl = (int)(e.idx / 256);
-                bucket[tl].push_back(DevEnt6{(int)(e.idx - (int64_t)tl * 256), e.arr, e.re, e.im});
+                int tl = (int)(e.idx / TILE6);
+                bucket[tl].push_back(DevEnt6{(int)(e.idx - (int64_t)tl * TILE6), e.arr, e.re, e.im});
             }
             hs.ent0 = (int)P->ents6.size();
             for (int tl = 0; tl < ntile; ++tl) {
                 auto &b = bucket[tl];
-                HostTile6 ht{(int)s, (int)std::min<int64_t>(256, N - (int64_t)tl * 256), (int64_t)tl * 256,
+                HostTile6 ht{(int)s, (int)std::min<int64_t>(TILE6, N - (int64_t)tl * TILE6), (int64_t)tl * TILE6,
                              (int)P->ents6.size(), (int)b.size()};
                 P->ents6.insert(P->ents6.end(), b.begin(), b.end());
                 P->tiles6.push_back(ht);
@@ -199,13 +227,24 @@ static int prepare_plan(casimir_plan_t *P)
         P->sims.push_back(hs);
     }
     P->field_elems = off;
-    P->table_bytes = (int64_t)(align256(P->mat_all.size()) + align256(P->coef_all.size() * P->rsize) +
+    {
+        static const int k_env = [] {
+            const char *e = std::getenv("CASIMIR_STEP2D_K");
+            return e ? std::atoi(e) : 2;
+        }();
+        bool all2d = !P->sims.empty() && !P->sims[0].full;
+        P->k2d = (all2d && k_env == 2) ? 2 : 1;
+        P->launches = P->k2d == 2 ? (D.prob.n_steps + 1) / 2 : D.prob.n_steps;
+    }
+    P->table_bytes = (int64_t)(align256(P->ents2.size() * sizeof(DevEnt)) + align256(P->rowptr2.size() * sizeof(int)) +
+                               align256(P->mat_all.size()) + align256(P->coef_all.size() * P->rsize) +
                                align256(D.gw.size() * 8) + align256(P->ents.size() * sizeof(DevEnt)) +
                                align256(P->src.size() * sizeof(DevSrc)) + align256(P->ents6.size() * sizeof(DevEnt6)) +
                                align256(P->src6.size() * sizeof(DevSrc6)) + align256(P->lor_all.size() * 8) +
                                align256(P->pml_all.size() * P->rsize));
     P->request_bytes = (int64_t)(align256(P->field_elems * P->rsize) + 2 * align256(P->sims.size() * 8) +
                                  P->tiles.size() * sizeof(DevTile) + P->tiles6.size() * sizeof(DevTile6) +
+                                 P->tiles2.size() * sizeof(DevTile2) +
                                  P->sims.size() * std::max(sizeof(DevSim2D), sizeof(DevSim6)));
     return CASIMIR_OK;
 }
@@ -231,11 +270,12 @@ int upload_plan(casimir_plan_t *P, cudaStream_t st)
 {
     if (P->dev.block) return CASIMIR_OK;
     casimir_ctx *c = P->ctx;
-    size_t sz[9] = {align256(P->mat_all.size()), align256(P->coef_all.size() * P->rsize),
-                    align256(P->data.gw.size() * 8), align256(P->ents.size() * sizeof(DevEnt)),
-                    align256(P->src.size() * sizeof(DevSrc)), align256(P->ents6.size() * sizeof(DevEnt6)),
-                    align256(P->src6.size() * sizeof(DevSrc6)), align256(P->lor_all.size() * 8),
-                    align256(P->pml_all.size() * P->rsize)};
+    size_t sz[11] = {align256(P->mat_all.size()), align256(P->coef_all.size() * P->rsize),
+                     align256(P->data.gw.size() * 8), align256(P->ents.size() * sizeof(DevEnt)),
+                     align256(P->src.size() * sizeof(DevSrc)), align256(P->ents6.size() * sizeof(DevEnt6)),
+                     align256(P->src6.size() * sizeof(DevSrc6)), align256(P->lor_all.size() * 8),
+                     align256(P->pml_all.size() * P->rsize), align256(P->ents2.size() * sizeof(DevEnt)),
+                     align256(P->rowptr2.size() * sizeof(int))};
     size_t total = 0;
     for (size_t q : sz) total += q;
     void *blk;
@@ -252,7 +292,9 @@ int upload_plan(casimir_plan_t *P, cudaStream_t st)
     P->dev.ents6 = (DevEnt6 *)p; p += sz[5];
     P->dev.src6 = (DevSrc6 *)p; p += sz[6];
     P->dev.lor = (double *)p; p += sz[7];
-    P->dev.pml = p;
+    P->dev.pml = p; p += sz[8];
+    P->dev.ents2 = (DevEnt *)p; p += sz[9];
+    P->dev.rowptr2 = (int *)p;
     if ((rc = put_table(P->mat_all, P->dev.mat, st))) return rc;
     if ((rc = put_real(P->coef_all, P->dev.coef, P->fp64, st))) return rc;
     if ((rc = put_table(P->data.gw, P->dev.gw, st))) return rc;
@@ -262,6 +304,8 @@ int upload_plan(casimir_plan_t *P, cudaStream_t st)
     if ((rc = put_table(P->src6, P->dev.src6, st))) return rc;
     if ((rc = put_table(P->lor_all, P->dev.lor, st))) return rc;
     if ((rc = put_real(P->pml_all, P->dev.pml, P->fp64, st))) return rc;
+    if ((rc = put_table(P->ents2, P->dev.ents2, st))) return rc;
+    if ((rc = put_table(P->rowptr2, P->dev.rowptr2, st))) return rc;
     c->used += total;
     return CASIMIR_OK;
 }
@@ -442,8 +486,9 @@ static int rebuild(casimir_ctx *c)
 {
     std::vector<DevSim2D> s2[2];
     std::vector<DevTile> t2[2];
-    std::vector<DevSim6> s6[4];
-    std::vector<DevTile6> t6[4];
+    std::vector<DevTile2> tt[2];
+    std::vector<DevSim6> s6[8];
+    std::vector<DevTile6> t6[8];
     for (auto &aw : c->active_waves) {
         casimir_request *r = aw.first;
         const casimir_request::Wave &w = r->waves[aw.second];
@@ -458,12 +503,19 @@ static int rebuild(casimir_ctx *c)
                 DevSim2D d;
                 make_sim2d(P, blk, r->acc, r->tail, w.s0, s, &d);
                 sv.push_back(d);
-                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
-                    const HostTile &ht = P->tiles[t];
-                    tv.push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.ents + ht.ent0});
+                if (P->k2d == 2) {
+                    for (int t = hs.tile2_0; t < hs.tile2_0 + hs.ntile2; ++t) {
+                        const HostTile2 &ht = P->tiles2[t];
+                        tt[P->fp64].push_back(DevTile2{idx, ht.i0, ht.j0, ht.ne, P->dev.ents2 + ht.ent0, P->dev.rowptr2 + ht.rp0});
+                    }
+                } else {
+                    for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                        const HostTile &ht = P->tiles[t];
+                        tv.push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.ents + ht.ent0});
+                    }
                 }
             } else {
-                int gi = 2 * P->fp64 + hs.cplx;
+                int gi = 4 * P->fp64 + 2 * hs.cplx + (P->data.prob.dims == 3 ? 1 : 0);
                 auto &sv = s6[gi];
                 auto &tv = t6[gi];
                 int idx = (int)sv.size();
@@ -478,12 +530,13 @@ static int rebuild(casimir_ctx *c)
         }
     }
     c->ntiles = 0;
-    for (int gi = 0; gi < 6; ++gi) {
+    for (int gi = 0; gi < 12; ++gi) {
         auto &G = c->groups[gi];
         size_t ns, nt, ss, ts;
         const void *sp, *tp;
         if (gi < 2) { ns = s2[gi].size(); nt = t2[gi].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile); sp = s2[gi].data(); tp = t2[gi].data(); }
-        else { ns = s6[gi - 2].size(); nt = t6[gi - 2].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile6); sp = s6[gi - 2].data(); tp = t6[gi - 2].data(); }
+        else if (gi < 10) { ns = s6[gi - 2].size(); nt = t6[gi - 2].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile6); sp = s6[gi - 2].data(); tp = t6[gi - 2].data(); }
+        else { ns = 0; nt = tt[gi - 10].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile2); sp = nullptr; tp = tt[gi - 10].data(); }
         int rc = grow(c, &G.sims, &G.sims_cap, ns * ss);
         if (rc) return rc;
         rc = grow(c, &G.tiles, &G.tiles_cap, nt * ts);
@@ -493,6 +546,9 @@ static int rebuild(casimir_ctx *c)
         G.ntiles = (int)nt;
         c->ntiles += (int)nt;
     }
+    // the two-step tiles index the 2D simulation tables of groups 0 / 1
+    c->groups[10].ntiles = (int)tt[0].size();
+    c->groups[11].ntiles = (int)tt[1].size();
     CUDA_TRY(cudaStreamSynchronize(c->stream));   // host vectors die here
     drop_graphs(c);
     c->dirty = false;
@@ -502,12 +558,15 @@ static int rebuild(casimir_ctx *c)
 static void launch_steps(casimir_ctx *c, int k)
 {
     for (int j = 0; j < k; ++j) {
-        for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < 2; ++p) {
             launch_step2d(p, (const DevSim2D *)c->groups[p].sims, (const DevTile *)c->groups[p].tiles,
                           c->groups[p].ntiles, c->d_launch, j, c->stream);
+            launch_step2d_t2(p, (const DevSim2D *)c->groups[p].sims, (const DevTile2 *)c->groups[10 + p].tiles,
+                             c->groups[10 + p].ntiles, c->d_launch, j, c->stream);
+        }
         for (int phase = 0; phase < 2; ++phase)
-            for (int gi = 2; gi < 6; ++gi)
-                launch_full((gi - 2) >> 1, (gi - 2) & 1, (const DevSim6 *)c->groups[gi].sims,
+            for (int gi = 2; gi < 10; ++gi)
+                launch_full(((gi - 2) >> 2) & 1, ((gi - 2) >> 1) & 1, ((gi - 2) & 1) ? 3 : 2, (const DevSim6 *)c->groups[gi].sims,
                             (const DevTile6 *)c->groups[gi].tiles, c->groups[gi].ntiles, c->d_launch, j, phase,
                             c->stream);
     }
@@ -531,12 +590,15 @@ static int run_chunk(casimir_ctx *c, int k)
         cudaGraph_t g;
         CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         for (int j = 0; j < k; ++j) {
-            for (int p = 0; p < 2; ++p)
+            for (int p = 0; p < 2; ++p) {
                 launch_step2d(p, (const DevSim2D *)c->groups[p].sims, (const DevTile *)c->groups[p].tiles,
                               c->groups[p].ntiles, c->d_launch, j, c->stream);
+                launch_step2d_t2(p, (const DevSim2D *)c->groups[p].sims, (const DevTile2 *)c->groups[10 + p].tiles,
+                                 c->groups[10 + p].ntiles, c->d_launch, j, c->stream);
+            }
             for (int phase = 0; phase < 2; ++phase)
-                for (int gi = 2; gi < 6; ++gi)
-                    launch_full((gi - 2) >> 1, (gi - 2) & 1, (const DevSim6 *)c->groups[gi].sims,
+                for (int gi = 2; gi < 10; ++gi)
+                    launch_full(((gi - 2) >> 2) & 1, ((gi - 2) >> 1) & 1, ((gi - 2) & 1) ? 3 : 2, (const DevSim6 *)c->groups[gi].sims,
                                 (const DevTile6 *)c->groups[gi].tiles, c->groups[gi].ntiles, c->d_launch, j, phase,
                                 c->stream);
         }
@@ -556,8 +618,8 @@ static int run_chunk(casimir_ctx *c, int k)
     }
     c->h_launch += k;
     int per_step = 0;
-    for (int gi = 0; gi < 6; ++gi)
-        if (c->groups[gi].ntiles > 0) per_step += gi < 2 ? 1 : 2;
+    for (int gi = 0; gi < 12; ++gi)
+        if (c->groups[gi].ntiles > 0) per_step += (gi >= 2 && gi < 10) ? 2 : 1;
     for (casimir_request *r : c->active) r->launches += (int64_t)k * per_step + 1;
     return CASIMIR_OK;
 }
@@ -604,7 +666,7 @@ static int engine_iterate(casimir_ctx *c)
         int64_t rem = INT64_MAX;
         for (auto &aw : c->active_waves) {
             const casimir_request::Wave &w = aw.first->waves[aw.second];
-            rem = std::min<int64_t>(rem, w.s0 + aw.first->plan->data.prob.n_steps - (next - 1));
+            rem = std::min<int64_t>(rem, w.s0 + aw.first->plan->launches - (next - 1));
         }
         if (rem > 0) {
             int k = (int)std::min<int64_t>(64, rem);
@@ -617,9 +679,11 @@ static int engine_iterate(casimir_ctx *c)
             c->step_launches += k;
             for (auto &aw : c->active_waves) {
                 const casimir_request::Wave &w = aw.first->waves[aw.second];
-                int64_t T = aw.first->plan->data.prob.n_steps;
-                int64_t n_lo = std::max<int64_t>(1, next - w.s0), n_hi = std::min<int64_t>(T, next + k - 1 - w.s0);
-                if (n_hi >= n_lo) c->cell_updates += (n_hi - n_lo + 1) * w.cells;
+                const casimir_plan_t *P = aw.first->plan;
+                int64_t T = P->data.prob.n_steps, K = P->k2d;
+                // steps covered by launches next .. next+k-1 of this wave
+                int64_t l_lo = std::max<int64_t>(1, next - w.s0), l_hi = std::min<int64_t>(P->launches, next + k - 1 - w.s0);
+                if (l_hi >= l_lo) c->cell_updates += (std::min<int64_t>(T, K * l_hi) - K * (l_lo - 1)) * w.cells;
             }
         }
     }
@@ -627,7 +691,7 @@ static int engine_iterate(casimir_ctx *c)
     for (size_t q = 0; q < c->active_waves.size();) {
         casimir_request *r = c->active_waves[q].first;
         casimir_request::Wave &w = r->waves[c->active_waves[q].second];
-        if (c->h_launch - 1 - w.s0 >= r->plan->data.prob.n_steps) {
+        if (c->h_launch - 1 - w.s0 >= r->plan->launches) {
             w.state = 2;
             r->waves_done++;
             c->active_bytes -= w.bytes;

@@ -43,12 +43,17 @@ struct HostSim {
     int64_t psi_off;       // element offset of its CPML planes (full kernel, -1: none)
     int64_t lor_off;       // element offset of its Lorentz planes (full kernel, -1: none)
     int tile0, ntile;      // range in the plan's tile list (2D) or tile6 list (full)
+    int tile2_0, ntile2;   // range in the plan's two-step tile list (2D)
     int ent0, nent;        // range in the plan's entry list (bucketed by tile)
     int src0, nsrc;        // range in the plan's source list
 };
 
 struct HostTile {
     int sim, i0, j0, ent0, ne;
+};
+
+struct HostTile2 {
+    int sim, i0, j0, ent0, ne, rp0;
 };
 
 struct HostTile6 {
@@ -65,6 +70,8 @@ struct DevPlan {           // device copies of a plan's static tables (kept whil
     DevSrc *src = nullptr;
     DevEnt6 *ents6 = nullptr;
     DevSrc6 *src6 = nullptr;
+    DevEnt *ents2 = nullptr;
+    int *rowptr2 = nullptr;
     double *lor = nullptr;
     void *pml = nullptr;
     size_t bytes = 0;
@@ -86,6 +93,11 @@ struct casimir_plan {
     std::vector<int64_t> coef_off;    // per geo, elements
     std::vector<uint8_t> mat_all;
     std::vector<double> coef_all;
+    std::vector<HostTile2> tiles2;    // two-step kernel tiles (TILE_X2 wide), entries sorted by row
+    std::vector<DevEnt> ents2;
+    std::vector<int> rowptr2;
+    int64_t launches = 0;             // launches a request needs (ceil(T/2) for the two-step kernel)
+    int k2d = 1;                      // time steps per launch of the 2D kernel
     std::vector<HostTile6> tiles6;
     std::vector<DevEnt6> ents6;
     std::vector<DevSrc6> src6;
@@ -143,12 +155,13 @@ struct casimir_ctx {
     int64_t h_launch = 1;            // index of the next launch
     // active set
     std::vector<casimir_request *> active;
-    // launch groups: [0, 1] the 2D kernel in FP32 / FP64, [2 + 2*fp64 + cplx] the six-component kernel
+    // launch groups: [0, 1] the 2D kernel in FP32 / FP64; [2 + 4*fp64 + 2*cplx + (dims == 3)]
+    // the six-component kernel; [10, 11] the two-step 2D kernel in FP32 / FP64
     struct Group {
         void *sims = nullptr, *tiles = nullptr;
         size_t sims_cap = 0, tiles_cap = 0;
         int ntiles = 0;
-    } groups[6];
+    } groups[12];
     int ntiles = 0;                   // over all groups
     // waves: simulations are activated in groups whose field bytes fit `wave_bytes`
     // (0: a whole request at once), so that the active working set can stay in L2

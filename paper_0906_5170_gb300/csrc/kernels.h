@@ -79,9 +79,11 @@ struct DevEnt6 {
     double wre, wim;
 };
 
+constexpr int TILE6 = 2048;   // cells per CTA of the six-component kernel (8 per thread)
+
 struct DevTile6 {
     int sim;
-    int count;             // cells in this tile (<= 256)
+    int count;             // cells in this tile (<= TILE6)
     int64_t cell0;
     int ne;
     int pad;
@@ -93,9 +95,25 @@ struct DevSrc6 {
     double re, im;
 };
 
-void launch_full(int fp64, int cplx, const DevSim6 *sims, const DevTile6 *tiles, int ntiles,
+void launch_full(int fp64, int cplx, int dims, const DevSim6 *sims, const DevTile6 *tiles, int ntiles,
                  const int64_t *launch_base, int64_t launch_add, int phase, cudaStream_t st);
 void launch_inject6(int fp64, void *fields, const DevSrc6 *src, int nsrc, cudaStream_t st);
+
+// Two-step tiles of the 2D kernel: four warp strips of 28 interior columns; the
+// tile's pixel entries sorted by row, with rowptr[ly] .. rowptr[ly+1] per row.
+constexpr int TILE_X2 = 112;
+struct DevTile2 {
+    int sim;
+    int i0, j0;
+    int ne;
+    const DevEnt *ents;    // loc = ly * TILE_X2 + lx
+    const int *rowptr;     // TILE_Y + 1 offsets into ents
+};
+
+// Two leapfrog steps per launch: launch number L (from the simulation's start) advances
+// steps 2L-1 and 2L (only 2L-1 when 2L > T), reading buffer (L-1)&1 and writing L&1.
+void launch_step2d_t2(int fp64, const DevSim2D *sims, const DevTile2 *tiles, int ntiles,
+                      const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 
 void launch_step2d(int fp64, const DevSim2D *sims, const DevTile *tiles, int ntiles,
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st);

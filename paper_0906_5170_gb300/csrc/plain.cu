@@ -190,7 +190,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                 ++launches;
             } else {
                 for (int phase = 0; phase < 2; ++phase)
-                    launch_full(P->fp64, cplx, (const DevSim6 *)d_sim, (const DevTile6 *)d_tiles, (int)t6.size(), d_counter, n - 1, phase, s);
+                    launch_full(P->fp64, cplx, D.prob.dims, (const DevSim6 *)d_sim, (const DevTile6 *)d_tiles, (int)t6.size(), d_counter, n - 1, phase, s);
                 launches += 2;
             }
             if (P->fp64)

@@ -78,27 +78,6 @@ __device__ __forceinline__ size_t slab_index(const DevSim6 &S, int a, const int 
 }
 
 template <typename R, bool CPLX>
-__device__ __forceinline__ V<R, CPLX> deriv(const DevSim6 &S, const Fields<R, CPLX> &F, int comp, int a,
-                                            const int c[3], size_t m, bool forward)
-{
-    using Vt = V<R, CPLX>;
-    Vt here = F.get(comp, m);
-    if (a == 2 && S.dims == 2) {
-        if constexpr (CPLX) return here.ikz((R)S.kz);
-        else return here.ikz((comp == 0 || comp == 1 || comp == 5) ? (R)S.kzA : (R)S.kzB);
-    }
-    size_t stride = a == 0 ? 1 : (a == 1 ? (size_t)S.n[0] : (size_t)S.n[0] * S.n[1]);
-    if (forward) {
-        if (c[a] + 1 < S.n[a]) return (F.get(comp, m + stride) - here).scale((R)S.inv_dx);
-        Vt o = F.get(comp, m - (size_t)(S.n[a] - 1) * stride).rot((R)S.bre[a], (R)S.bim[a]);
-        return (o - here).scale((R)S.inv_dx);
-    }
-    if (c[a] > 0) return (here - F.get(comp, m - stride)).scale((R)S.inv_dx);
-    Vt o = F.get(comp, m + (size_t)(S.n[a] - 1) * stride).rot((R)S.bre[a], -(R)S.bim[a]);
-    return (here - o).scale((R)S.inv_dx);
-}
-
-template <typename R, bool CPLX>
 __device__ __forceinline__ V<R, CPLX> stretch(const DevSim6 &S, V<R, CPLX> d, int a, int half, int pos,
                                               int psi_plane, const int c[3])
 {
@@ -118,86 +97,149 @@ __device__ __forceinline__ V<R, CPLX> stretch(const DevSim6 &S, V<R, CPLX> d, in
     return d.scale(ik) + p;
 }
 
-template <typename R, bool CPLX>
+// Neighbour of cell (c) along axis a in direction dir (+1 forward, -1 backward): flat index,
+// and whether the step wraps around (then the Bloch factor applies).
+struct Nb {
+    int64_t m;
+    bool wrap;
+};
+
+template <int D>
+__device__ __forceinline__ Nb nbr(const DevSim6 &S, const int c[3], int64_t m, int a, int dir)
+{
+    int64_t stride = a == 0 ? 1 : (a == 1 ? (int64_t)S.n[0] : (int64_t)S.n[0] * S.n[1]);
+    if (dir > 0) {
+        if (c[a] + 1 < S.n[a]) return Nb{m + stride, false};
+        return Nb{m - (int64_t)(S.n[a] - 1) * stride, true};
+    }
+    if (c[a] > 0) return Nb{m - stride, false};
+    return Nb{m + (int64_t)(S.n[a] - 1) * stride, true};
+}
+
+// d_a F at this cell: forward (H update) or backward (E update) difference, i k_z in 2D along z.
+template <typename R, bool CPLX, int D>
+__device__ __forceinline__ V<R, CPLX> dif(const DevSim6 &S, const Fields<R, CPLX> &F, int comp, int a,
+                                          const int c[3], int64_t m, V<R, CPLX> here, bool forward)
+{
+    if (D == 2 && a == 2) {
+        if constexpr (CPLX) return here.ikz((R)S.kz);
+        else return here.ikz((comp == 0 || comp == 1 || comp == 5) ? (R)S.kzA : (R)S.kzB);
+    }
+    Nb q = nbr<D>(S, c, m, a, forward ? 1 : -1);
+    V<R, CPLX> o = F.get(comp, q.m);
+    if (q.wrap) o = o.rot((R)S.bre[a], forward ? (R)S.bim[a] : -(R)S.bim[a]);
+    return (forward ? (o - here) : (here - o)).scale((R)S.inv_dx);
+}
+
+template <typename R, bool CPLX, int D>
 __global__ void __launch_bounds__(256)
 k_full(const DevSim6 *__restrict__ sims, const DevTile6 *__restrict__ tiles,
        const int64_t *__restrict__ launch_base, int64_t launch_add, int phase)
 {
     using Vt = V<R, CPLX>;
     __shared__ double red[8];
+    __shared__ DevSim6 sS;
     const DevTile6 t = tiles[blockIdx.x];
-    const DevSim6 &S = sims[t.sim];
+    {
+        // one copy of the simulation's descriptor per CTA
+        const int *src = reinterpret_cast<const int *>(sims + t.sim);
+        int *dst = reinterpret_cast<int *>(&sS);
+        for (int q = threadIdx.x; q < (int)(sizeof(DevSim6) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+    }
+    __syncthreads();
+    const DevSim6 &S = sS;
     const int64_t n = *launch_base + launch_add - S.s0;
     if (n < 1 || n > S.T) return;
-    const size_t N = (size_t)S.n[0] * S.n[1] * S.n[2];
-    Fields<R, CPLX> F{reinterpret_cast<R *>(S.fields), N};
+    const int64_t N = (int64_t)S.n[0] * S.n[1] * S.n[2];
+    Fields<R, CPLX> F{reinterpret_cast<R *>(S.fields), (size_t)N};
     const bool updE = (phase == 0) == (S.magnetic != 0);
     const R a = phase == 0 ? (R)1 : (R)S.a;
     const R b = phase == 0 ? (R)(n == 1 ? 0.5 * S.dt : S.dt) : (R)S.bs;
-    const size_t m = t.cell0 + threadIdx.x;
-    if (m < N && threadIdx.x < t.count) {
+#pragma unroll 2
+    for (int r = 0; r < TILE6 / 256; ++r) {
+    const int64_t m = t.cell0 + r * 256 + threadIdx.x;
+    if (r * 256 + (int)threadIdx.x < t.count) {
         int c3[3];
         const unsigned mm = (unsigned)m, nx = (unsigned)S.n[0], ny = (unsigned)S.n[1];
         const unsigned row = mm / nx;
         c3[0] = (int)(mm - row * nx);
         c3[1] = (int)(row % ny);
         c3[2] = (int)(row / ny);
+        bool inpml = false;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax)
+            if (S.pml_d[ax] > 0 && (c3[ax] < S.pml_d[ax] || c3[ax] >= S.n[ax] - S.pml_d[ax])) inpml = true;
         const int id = S.mat[m];
         const R *coef = reinterpret_cast<const R *>(S.coef) + 6 * id;
         if (updE) {
+            Vt h[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) h[q] = F.get(3 + q, m);
+            Vt curl[3];
+#pragma unroll
             for (int cpt = 0; cpt < 3; ++cpt) {
-                int a1 = (cpt + 1) % 3, a2 = (cpt + 2) % 3;
+                const int a1 = (cpt + 1) % 3, a2 = (cpt + 2) % 3;
                 // (curl H)_c = d_{a1} H_{a2} - d_{a2} H_{a1}, backward differences, integer-site profiles
-                Vt t1 = stretch<R, CPLX>(S, deriv<R, CPLX>(S, F, 3 + a2, a1, c3, m, false), a1, 0, c3[a1], (cpt == (a1 + 1) % 3) ? 0 : 1, c3);
-                Vt t2 = stretch<R, CPLX>(S, deriv<R, CPLX>(S, F, 3 + a1, a2, c3, m, false), a2, 0, c3[a2], (cpt == (a2 + 1) % 3) ? 0 : 1, c3);
-                Vt curl = t1 - t2;
+                Vt t1 = dif<R, CPLX, D>(S, F, 3 + a2, a1, c3, m, h[a2], false);
+                Vt t2 = dif<R, CPLX, D>(S, F, 3 + a1, a2, c3, m, h[a1], false);
+                if (inpml) {
+                    t1 = stretch<R, CPLX>(S, t1, a1, 0, c3[a1], (cpt == (a1 + 1) % 3) ? 0 : 1, c3);
+                    t2 = stretch<R, CPLX>(S, t2, a2, 0, c3[a2], (cpt == (a2 + 1) % 3) ? 0 : 1, c3);
+                }
+                curl[cpt] = t1 - t2;
+            }
+#pragma unroll
+            for (int cpt = 0; cpt < 3; ++cpt) {
                 R ce = coef[cpt];
                 Vt e = F.get(cpt, m);
                 Vt enew;
-                if (S.lor) {
-                    const double *lt = S.lorentz + 6 * id + 2 * cpt;
-                    R de = (R)lt[0];
-                    if (de != (R)0) {
-                        R w2 = (R)(lt[1] * lt[1]);
-                        R dt = (R)S.dt_full, sg = (R)S.sigma;
-                        Fields<R, CPLX> P{reinterpret_cast<R *>(S.lor), N};
-                        Vt p = P.get(cpt, m), pm = P.get(3 + cpt, m);
-                        Vt pn;
-                        if (S.magnetic == 0 && n == 1)
-                            pn = (p.scale((R)2 - w2 * dt * dt) + e.scale(de * w2 * dt * dt)).scale((R)0.5);
-                        else
-                            pn = (p.scale((R)2 - w2 * dt * dt) - pm.scale((R)1 - (R)0.5 * sg * dt) +
-                                  e.scale(de * w2 * dt * dt)).scale((R)1 / ((R)1 + (R)0.5 * sg * dt));
-                        P.put(3 + cpt, m, p);
-                        P.put(cpt, m, pn);
-                        enew = e.scale(a) + (p.scale(a) - pn + curl.scale(b)).scale(ce);
-                    } else {
-                        enew = e.scale(a) + curl.scale(b * ce);
-                    }
+                R de = S.lor ? (R)S.lorentz[6 * id + 2 * cpt] : (R)0;
+                if (de != (R)0) {
+                    R w2 = (R)(S.lorentz[6 * id + 2 * cpt + 1] * S.lorentz[6 * id + 2 * cpt + 1]);
+                    R dt = (R)S.dt_full, sg = (R)S.sigma;
+                    Fields<R, CPLX> P{reinterpret_cast<R *>(S.lor), (size_t)N};
+                    Vt p = P.get(cpt, m), pm = P.get(3 + cpt, m);
+                    Vt pn;
+                    if (S.magnetic == 0 && n == 1)
+                        pn = (p.scale((R)2 - w2 * dt * dt) + e.scale(de * w2 * dt * dt)).scale((R)0.5);
+                    else
+                        pn = (p.scale((R)2 - w2 * dt * dt) - pm.scale((R)1 - (R)0.5 * sg * dt) +
+                              e.scale(de * w2 * dt * dt)).scale((R)1 / ((R)1 + (R)0.5 * sg * dt));
+                    P.put(3 + cpt, m, p);
+                    P.put(cpt, m, pn);
+                    enew = e.scale(a) + (p.scale(a) - pn + curl[cpt].scale(b)).scale(ce);
                 } else {
-                    enew = e.scale(a) + curl.scale(b * ce);
+                    enew = e.scale(a) + curl[cpt].scale(b * ce);
                 }
                 F.put(cpt, m, enew);
             }
         } else {
+            Vt e[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) e[q] = F.get(q, m);
+#pragma unroll
             for (int cpt = 0; cpt < 3; ++cpt) {
-                int a1 = (cpt + 1) % 3, a2 = (cpt + 2) % 3;
+                const int a1 = (cpt + 1) % 3, a2 = (cpt + 2) % 3;
                 // (curl E)_c = d_{a1} E_{a2} - d_{a2} E_{a1}, forward differences, half-site profiles
-                Vt t1 = stretch<R, CPLX>(S, deriv<R, CPLX>(S, F, a2, a1, c3, m, true), a1, 1, c3[a1], 2 + ((cpt == (a1 + 1) % 3) ? 0 : 1), c3);
-                Vt t2 = stretch<R, CPLX>(S, deriv<R, CPLX>(S, F, a1, a2, c3, m, true), a2, 1, c3[a2], 2 + ((cpt == (a2 + 1) % 3) ? 0 : 1), c3);
+                Vt t1 = dif<R, CPLX, D>(S, F, a2, a1, c3, m, e[a2], true);
+                Vt t2 = dif<R, CPLX, D>(S, F, a1, a2, c3, m, e[a1], true);
+                if (inpml) {
+                    t1 = stretch<R, CPLX>(S, t1, a1, 1, c3[a1], 2 + ((cpt == (a1 + 1) % 3) ? 0 : 1), c3);
+                    t2 = stretch<R, CPLX>(S, t2, a2, 1, c3[a2], 2 + ((cpt == (a2 + 1) % 3) ? 0 : 1), c3);
+                }
                 Vt curl = t1 - t2;
-                R ch = coef[3 + cpt];
                 Vt hv = F.get(3 + cpt, m);
-                F.put(3 + cpt, m, hv.scale(a) - curl.scale(b * ch));
+                F.put(3 + cpt, m, hv.scale(a) - curl.scale(b * coef[3 + cpt]));
             }
         }
+    }
     }
     if (phase == 1 && t.ne > 0) {
         __syncthreads();
         double part = 0.0;
         for (int e = threadIdx.x; e < t.ne; e += blockDim.x) {
             DevEnt6 en = t.ents[e];
-            size_t g = t.cell0 + en.off;
+            int64_t g = t.cell0 + en.off;
             Vt v = F.get(en.arr, g);
             if constexpr (CPLX) part += en.wre * (double)v.x - en.wim * (double)v.y;
             else part += en.wre * (double)v.x;
@@ -228,17 +270,19 @@ __global__ void k_inject6(R *fields, const DevSrc6 *src, int nsrc)
 
 }  // namespace
 
-void launch_full(int fp64, int cplx, const DevSim6 *sims, const DevTile6 *tiles, int ntiles,
+void launch_full(int fp64, int cplx, int dims, const DevSim6 *sims, const DevTile6 *tiles, int ntiles,
                  const int64_t *launch_base, int64_t launch_add, int phase, cudaStream_t st)
 {
     if (ntiles <= 0) return;
+#define CAS_FULL(R, C, D) k_full<R, C, D><<<ntiles, 256, 0, st>>>(sims, tiles, launch_base, launch_add, phase)
     if (fp64) {
-        if (cplx) k_full<double, true><<<ntiles, 256, 0, st>>>(sims, tiles, launch_base, launch_add, phase);
-        else k_full<double, false><<<ntiles, 256, 0, st>>>(sims, tiles, launch_base, launch_add, phase);
+        if (cplx) { if (dims == 2) CAS_FULL(double, true, 2); else CAS_FULL(double, true, 3); }
+        else { if (dims == 2) CAS_FULL(double, false, 2); else CAS_FULL(double, false, 3); }
     } else {
-        if (cplx) k_full<float, true><<<ntiles, 256, 0, st>>>(sims, tiles, launch_base, launch_add, phase);
-        else k_full<float, false><<<ntiles, 256, 0, st>>>(sims, tiles, launch_base, launch_add, phase);
+        if (cplx) { if (dims == 2) CAS_FULL(float, true, 2); else CAS_FULL(float, true, 3); }
+        else { if (dims == 2) CAS_FULL(float, false, 2); else CAS_FULL(float, false, 3); }
     }
+#undef CAS_FULL
 }
 
 void launch_inject6(int fp64, void *fields, const DevSrc6 *src, int nsrc, cudaStream_t st)
