@@ -209,6 +209,38 @@ def cpu_baseline(budget_s=15.0):
             "sample": f"{len(sims)} sims of the h=0.5 geometry (400x80) x {T} steps, FP64, {dt:.2f} s"}, dt
 
 
+def profile_case_problems(case, steps):
+    """Mid-size single cases for kernel profiling (fields above L2, a few GB at most)."""
+    import workloads as W
+    if case == "piston":       # one sweep geometry, 16 harmonics: 256 FP32 simulations, 17 M cells
+        return [W.config2_piston(W.config2_heights()[3], n_harm=16, n_steps=steps)]
+    if case == "waveguides":   # 256 x 256 CPML cell, Lorentz guides, 2 k_z x 6 harmonics: 192 simulations
+        kp = W.config3_kz_points(0.5)
+        return [W.config3_waveguides(0.5, n_harm=6, n_steps=steps, k_points=[kp[3], kp[12]])]
+    if case == "sphere3d":     # 160^3 CPML cell, 1 harmonic per face: 20 simulations
+        return [W.config4_sphere_notch(0.55, seed=1, n_harm=1, n_steps=steps)]
+    raise ValueError(case)
+
+
+def run_profile_case(args):
+    """One synchronous run of a profiling case; prints one JSON line with its kernel timing."""
+    from paper_0906_5170_gb300 import build as pkbuild
+    pkbuild.build()
+    import paper_0906_5170_gb300 as pk
+    ctx = pk.Context(0)
+    out = []
+    for p in profile_case_problems(args.profile_case, args.time_steps):
+        plan = ctx.plan(p)
+        info = plan.info()
+        F, _, st = plan.run()
+        ms, nl, cu = ctx.kernel_stats(reset=True)
+        out.append({"case": args.profile_case, "info": info, "kernel_ms": ms, "launches": nl,
+                    "gcell_updates_per_s": cu / (ms / 1e3) / 1e9,
+                    "gb_per_s_algorithmic": info["bytes_per_update"] * cu / (ms / 1e3) / 1e9})
+    print(json.dumps(out))
+    ctx.close()
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -246,9 +278,13 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=12)
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--profile-case", choices=["piston", "waveguides", "sphere3d"], default=None,
+                    help="run one mid-size case for kernel profiling instead of the benchmark")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args)
 
     import numpy as np
     import torch
