@@ -186,35 +186,73 @@ static int prepare_plan(casimir_plan_t *P)
             double sgn = inA(sarr) ? 1.0 : -1.0;
             hs.kzA = sgn * g.kz;
             hs.kzB = -sgn * g.kz;
-            off += 6 * cf * N;
-            if (g.has_pml[0] || g.has_pml[1] || g.has_pml[2]) {
+            // two-dimensional runs march both half steps in one launch over ping-pong buffers
+            static const bool march_env = [] {
+                const char *e = std::getenv("CASIMIR_MARCH6");
+                return !(e && std::atoi(e) == 0);
+            }();
+            hs.march = (D.prob.dims == 2 && g.n[2] == 1 && march_env) ? 1 : 0;
+            const int nbuf = hs.march ? 2 : 1;
+            hs.fhalf = 6 * cf * N;
+            off += nbuf * hs.fhalf;
+            hs.psi_half = 0;
+            for (int a = 0; a < 3; ++a)
+                if (g.has_pml[a]) hs.psi_half += 4 * cf * (N / g.n[a]) * 2 * D.prob.pml_cells[a];
+            if (hs.psi_half > 0) {
                 hs.psi_off = off;
-                for (int a = 0; a < 3; ++a)
-                    if (g.has_pml[a]) off += 4 * cf * (N / g.n[a]) * 2 * D.prob.pml_cells[a];
+                off += nbuf * hs.psi_half;
             }
+            hs.lor_half = g.has_lorentz ? 6 * cf * N : 0;
             if (g.has_lorentz) {
                 hs.lor_off = off;
-                off += 6 * cf * N;
+                off += nbuf * hs.lor_half;
             }
             off = (off + 63) & ~(int64_t)63;
-            int ntile = (int)((N + TILE6 - 1) / TILE6);
-            hs.tile0 = (int)P->tiles6.size();
-            hs.ntile = ntile;
-            std::vector<std::vector<DevEnt6>> bucket(ntile);
-            for (const Entry &e : sm.meas) {
-                if (!hs.cplx && g.n[2] == 1 && D.prob.dims == 2 && inA(e.arr) != inA(sarr)) continue;   // contributes i * real: no real part
-                int tl = (int)(e.idx / TILE6);
-                bucket[tl].push_back(DevEnt6{(int)(e.idx - (int64_t)tl * TILE6), e.arr, e.re, e.im});
+            if (hs.march) {
+                // TILE_X x TILE_Y tiles; entries carry the component in bits 16..18 and, for the
+                // imaginary weight of complex fields, bit 19
+                int tx = (hs.nx + TILE_X - 1) / TILE_X, ty = (hs.ny + TILE_Y - 1) / TILE_Y;
+                std::vector<std::vector<DevEnt>> bucket((size_t)tx * ty);
+                for (const Entry &e : sm.meas) {
+                    if (!hs.cplx && inA(e.arr) != inA(sarr)) continue;   // contributes i * real: no real part
+                    int i = (int)(e.idx % hs.nx), j = (int)(e.idx / hs.nx);
+                    int ti = i / TILE_X, tj = j / TILE_Y;
+                    int loc = (j - tj * TILE_Y) * TILE_X + (i - ti * TILE_X);
+                    auto &b = bucket[(size_t)tj * tx + ti];
+                    if (e.re != 0.0 || !hs.cplx) b.push_back(DevEnt{loc | (e.arr << 16), 0, e.re});
+                    if (hs.cplx && e.im != 0.0) b.push_back(DevEnt{loc | ((e.arr | 8) << 16), 0, e.im});
+                }
+                hs.tile0 = (int)P->tilesM.size();
+                hs.ntile = tx * ty;
+                hs.ent0 = (int)P->entsM.size();
+                for (int tj = 0; tj < ty; ++tj)
+                    for (int ti = 0; ti < tx; ++ti) {
+                        auto &b = bucket[(size_t)tj * tx + ti];
+                        P->tilesM.push_back(HostTile{(int)s, ti * TILE_X, tj * TILE_Y, (int)P->entsM.size(), (int)b.size()});
+                        P->entsM.insert(P->entsM.end(), b.begin(), b.end());
+                    }
+                hs.nent = (int)P->entsM.size() - hs.ent0;
             }
-            hs.ent0 = (int)P->ents6.size();
-            for (int tl = 0; tl < ntile; ++tl) {
-                auto &b = bucket[tl];
-                HostTile6 ht{(int)s, (int)std::min<int64_t>(TILE6, N - (int64_t)tl * TILE6), (int64_t)tl * TILE6,
-                             (int)P->ents6.size(), (int)b.size()};
-                P->ents6.insert(P->ents6.end(), b.begin(), b.end());
-                P->tiles6.push_back(ht);
+            if (!hs.march) {
+                int ntile = (int)((N + TILE6 - 1) / TILE6);
+                hs.tile0 = (int)P->tiles6.size();
+                hs.ntile = ntile;
+                std::vector<std::vector<DevEnt6>> bucket(ntile);
+                for (const Entry &e : sm.meas) {
+                    if (!hs.cplx && g.n[2] == 1 && D.prob.dims == 2 && inA(e.arr) != inA(sarr)) continue;   // contributes i * real: no real part
+                    int tl = (int)(e.idx / TILE6);
+                    bucket[tl].push_back(DevEnt6{(int)(e.idx - (int64_t)tl * TILE6), e.arr, e.re, e.im});
+                }
+                hs.ent0 = (int)P->ents6.size();
+                for (int tl = 0; tl < ntile; ++tl) {
+                    auto &b = bucket[tl];
+                    HostTile6 ht{(int)s, (int)std::min<int64_t>(TILE6, N - (int64_t)tl * TILE6), (int64_t)tl * TILE6,
+                                 (int)P->ents6.size(), (int)b.size()};
+                    P->ents6.insert(P->ents6.end(), b.begin(), b.end());
+                    P->tiles6.push_back(ht);
+                }
+                hs.nent = (int)P->ents6.size() - hs.ent0;
             }
-            hs.nent = (int)P->ents6.size() - hs.ent0;
             hs.src0 = (int)P->src6.size();
             for (const Entry &e : sm.src) {
                 if (hs.cplx)
@@ -241,10 +279,10 @@ static int prepare_plan(casimir_plan_t *P)
                                align256(D.gw.size() * 8) + align256(P->ents.size() * sizeof(DevEnt)) +
                                align256(P->src.size() * sizeof(DevSrc)) + align256(P->ents6.size() * sizeof(DevEnt6)) +
                                align256(P->src6.size() * sizeof(DevSrc6)) + align256(P->lor_all.size() * 8) +
-                               align256(P->pml_all.size() * P->rsize));
+                               align256(P->pml_all.size() * P->rsize) + align256(P->entsM.size() * sizeof(DevEnt)));
     P->request_bytes = (int64_t)(align256(P->field_elems * P->rsize) + 2 * align256(P->sims.size() * 8) +
                                  P->tiles.size() * sizeof(DevTile) + P->tiles6.size() * sizeof(DevTile6) +
-                                 P->tiles2.size() * sizeof(DevTile2) +
+                                 P->tiles2.size() * sizeof(DevTile2) + P->tilesM.size() * sizeof(DevTile) +
                                  P->sims.size() * std::max(sizeof(DevSim2D), sizeof(DevSim6)));
     return CASIMIR_OK;
 }
@@ -270,12 +308,12 @@ int upload_plan(casimir_plan_t *P, cudaStream_t st)
 {
     if (P->dev.block) return CASIMIR_OK;
     casimir_ctx *c = P->ctx;
-    size_t sz[11] = {align256(P->mat_all.size()), align256(P->coef_all.size() * P->rsize),
+    size_t sz[12] = {align256(P->mat_all.size()), align256(P->coef_all.size() * P->rsize),
                      align256(P->data.gw.size() * 8), align256(P->ents.size() * sizeof(DevEnt)),
                      align256(P->src.size() * sizeof(DevSrc)), align256(P->ents6.size() * sizeof(DevEnt6)),
                      align256(P->src6.size() * sizeof(DevSrc6)), align256(P->lor_all.size() * 8),
                      align256(P->pml_all.size() * P->rsize), align256(P->ents2.size() * sizeof(DevEnt)),
-                     align256(P->rowptr2.size() * sizeof(int))};
+                     align256(P->rowptr2.size() * sizeof(int)), align256(P->entsM.size() * sizeof(DevEnt))};
     size_t total = 0;
     for (size_t q : sz) total += q;
     void *blk;
@@ -294,7 +332,8 @@ int upload_plan(casimir_plan_t *P, cudaStream_t st)
     P->dev.lor = (double *)p; p += sz[7];
     P->dev.pml = p; p += sz[8];
     P->dev.ents2 = (DevEnt *)p; p += sz[9];
-    P->dev.rowptr2 = (int *)p;
+    P->dev.rowptr2 = (int *)p; p += sz[10];
+    P->dev.entsM = (DevEnt *)p;
     if ((rc = put_table(P->mat_all, P->dev.mat, st))) return rc;
     if ((rc = put_real(P->coef_all, P->dev.coef, P->fp64, st))) return rc;
     if ((rc = put_table(P->data.gw, P->dev.gw, st))) return rc;
@@ -306,6 +345,7 @@ int upload_plan(casimir_plan_t *P, cudaStream_t st)
     if ((rc = put_real(P->pml_all, P->dev.pml, P->fp64, st))) return rc;
     if ((rc = put_table(P->ents2, P->dev.ents2, st))) return rc;
     if ((rc = put_table(P->rowptr2, P->dev.rowptr2, st))) return rc;
+    if ((rc = put_table(P->entsM, P->dev.entsM, st))) return rc;
     c->used += total;
     return CASIMIR_OK;
 }
@@ -468,6 +508,9 @@ void make_sim6(const casimir_plan_t *P, char *blk, double *acc, double *tail, in
     d->kz = g.kz;
     d->kzA = hs.kzA;
     d->kzB = hs.kzB;
+    d->fhalf = hs.march ? hs.fhalf : 0;
+    d->psi_half = hs.march ? hs.psi_half : 0;
+    d->lor_half = hs.march ? hs.lor_half : 0;
 }
 
 static int grow(casimir_ctx *c, void **p, size_t *cap, size_t need)
@@ -489,6 +532,8 @@ static int rebuild(casimir_ctx *c)
     std::vector<DevTile2> tt[2];
     std::vector<DevSim6> s6[8];
     std::vector<DevTile6> t6[8];
+    std::vector<DevSim6> sm6[4];
+    std::vector<DevTile> tm6[4];
     for (auto &aw : c->active_waves) {
         casimir_request *r = aw.first;
         const casimir_request::Wave &w = r->waves[aw.second];
@@ -514,6 +559,16 @@ static int rebuild(casimir_ctx *c)
                         tv.push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.ents + ht.ent0});
                     }
                 }
+            } else if (hs.march) {
+                int gi = 2 * P->fp64 + hs.cplx;
+                int idx = (int)sm6[gi].size();
+                DevSim6 d;
+                make_sim6(P, blk, r->acc, r->tail, w.s0, s, &d);
+                sm6[gi].push_back(d);
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile &ht = P->tilesM[t];
+                    tm6[gi].push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.entsM + ht.ent0});
+                }
             } else {
                 int gi = 4 * P->fp64 + 2 * hs.cplx + (P->data.prob.dims == 3 ? 1 : 0);
                 auto &sv = s6[gi];
@@ -530,13 +585,14 @@ static int rebuild(casimir_ctx *c)
         }
     }
     c->ntiles = 0;
-    for (int gi = 0; gi < 12; ++gi) {
+    for (int gi = 0; gi < 16; ++gi) {
         auto &G = c->groups[gi];
         size_t ns, nt, ss, ts;
         const void *sp, *tp;
         if (gi < 2) { ns = s2[gi].size(); nt = t2[gi].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile); sp = s2[gi].data(); tp = t2[gi].data(); }
         else if (gi < 10) { ns = s6[gi - 2].size(); nt = t6[gi - 2].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile6); sp = s6[gi - 2].data(); tp = t6[gi - 2].data(); }
-        else { ns = 0; nt = tt[gi - 10].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile2); sp = nullptr; tp = tt[gi - 10].data(); }
+        else if (gi < 12) { ns = 0; nt = tt[gi - 10].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile2); sp = nullptr; tp = tt[gi - 10].data(); }
+        else { ns = sm6[gi - 12].size(); nt = tm6[gi - 12].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sm6[gi - 12].data(); tp = tm6[gi - 12].data(); }
         int rc = grow(c, &G.sims, &G.sims_cap, ns * ss);
         if (rc) return rc;
         rc = grow(c, &G.tiles, &G.tiles_cap, nt * ts);
@@ -569,6 +625,9 @@ static void launch_steps(casimir_ctx *c, int k)
                 launch_full(((gi - 2) >> 2) & 1, ((gi - 2) >> 1) & 1, ((gi - 2) & 1) ? 3 : 2, (const DevSim6 *)c->groups[gi].sims,
                             (const DevTile6 *)c->groups[gi].tiles, c->groups[gi].ntiles, c->d_launch, j, phase,
                             c->stream);
+        for (int gi = 12; gi < 16; ++gi)
+            launch_march6(((gi - 12) >> 1) & 1, (gi - 12) & 1, (const DevSim6 *)c->groups[gi].sims,
+                          (const DevTile *)c->groups[gi].tiles, c->groups[gi].ntiles, c->d_launch, j, c->stream);
     }
     launch_bump(c->d_launch, k, c->stream);
 }
@@ -589,20 +648,7 @@ static int run_chunk(casimir_ctx *c, int k)
     if (!no_graphs && it == c->graphs.end()) {
         cudaGraph_t g;
         CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        for (int j = 0; j < k; ++j) {
-            for (int p = 0; p < 2; ++p) {
-                launch_step2d(p, (const DevSim2D *)c->groups[p].sims, (const DevTile *)c->groups[p].tiles,
-                              c->groups[p].ntiles, c->d_launch, j, c->stream);
-                launch_step2d_t2(p, (const DevSim2D *)c->groups[p].sims, (const DevTile2 *)c->groups[10 + p].tiles,
-                                 c->groups[10 + p].ntiles, c->d_launch, j, c->stream);
-            }
-            for (int phase = 0; phase < 2; ++phase)
-                for (int gi = 2; gi < 10; ++gi)
-                    launch_full(((gi - 2) >> 2) & 1, ((gi - 2) >> 1) & 1, ((gi - 2) & 1) ? 3 : 2, (const DevSim6 *)c->groups[gi].sims,
-                                (const DevTile6 *)c->groups[gi].tiles, c->groups[gi].ntiles, c->d_launch, j, phase,
-                                c->stream);
-        }
-        launch_bump(c->d_launch, k, c->stream);
+        launch_steps(c, k);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (e != cudaSuccess) return fail(CASIMIR_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
         cudaGraphExec_t ex;
@@ -618,7 +664,7 @@ static int run_chunk(casimir_ctx *c, int k)
     }
     c->h_launch += k;
     int per_step = 0;
-    for (int gi = 0; gi < 12; ++gi)
+    for (int gi = 0; gi < 16; ++gi)
         if (c->groups[gi].ntiles > 0) per_step += (gi >= 2 && gi < 10) ? 2 : 1;
     for (casimir_request *r : c->active) r->launches += (int64_t)k * per_step + 1;
     return CASIMIR_OK;

@@ -35,14 +35,16 @@ struct HostSim {
     int geo;
     int nx, ny, nz;
     int second_u;
-    int full;              // six-component kernel
+    int full;              // six-component fields
+    int march;             // two-dimensional six-component run on the march kernel (ping-pong buffers)
     int cplx;              // complex fields (Bloch phase)
     int magnetic;
     double kzA, kzB;       // real-phase d/dz factors (two-dimensional k_z runs)
     int64_t field_off;     // element offset of this sim's block inside the request's field block
     int64_t psi_off;       // element offset of its CPML planes (full kernel, -1: none)
     int64_t lor_off;       // element offset of its Lorentz planes (full kernel, -1: none)
-    int tile0, ntile;      // range in the plan's tile list (2D) or tile6 list (full)
+    int64_t fhalf, psi_half, lor_half;   // march runs: elements of one buffer of fields, psi, Lorentz planes
+    int tile0, ntile;      // range in the plan's tile list (2D and march runs) or tile6 list (full)
     int tile2_0, ntile2;   // range in the plan's two-step tile list (2D)
     int ent0, nent;        // range in the plan's entry list (bucketed by tile)
     int src0, nsrc;        // range in the plan's source list
@@ -69,6 +71,7 @@ struct DevPlan {           // device copies of a plan's static tables (kept whil
     DevEnt *ents = nullptr;
     DevSrc *src = nullptr;
     DevEnt6 *ents6 = nullptr;
+    DevEnt *entsM = nullptr;
     DevSrc6 *src6 = nullptr;
     DevEnt *ents2 = nullptr;
     int *rowptr2 = nullptr;
@@ -99,6 +102,8 @@ struct casimir_plan {
     int64_t launches = 0;             // launches a request needs (ceil(T/2) for the two-step kernel)
     int k2d = 1;                      // time steps per launch of the 2D kernel
     std::vector<HostTile6> tiles6;
+    std::vector<HostTile> tilesM;     // march kernel tiles (TILE_X x TILE_Y) with their entries
+    std::vector<DevEnt> entsM;
     std::vector<DevEnt6> ents6;
     std::vector<DevSrc6> src6;
     std::vector<double> lor_all;      // per geo [id][6]
@@ -156,12 +161,13 @@ struct casimir_ctx {
     // active set
     std::vector<casimir_request *> active;
     // launch groups: [0, 1] the 2D kernel in FP32 / FP64; [2 + 4*fp64 + 2*cplx + (dims == 3)]
-    // the six-component kernel; [10, 11] the two-step 2D kernel in FP32 / FP64
+    // the six-component kernel; [10, 11] the two-step 2D kernel in FP32 / FP64;
+    // [12 + 2*fp64 + cplx] the six-component march kernel of two-dimensional runs
     struct Group {
         void *sims = nullptr, *tiles = nullptr;
         size_t sims_cap = 0, tiles_cap = 0;
         int ntiles = 0;
-    } groups[12];
+    } groups[16];
     int ntiles = 0;                   // over all groups
     // waves: simulations are activated in groups whose field bytes fit `wave_bytes`
     // (0: a whole request at once), so that the active working set can stay in L2

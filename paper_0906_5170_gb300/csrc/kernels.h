@@ -71,6 +71,9 @@ struct DevSim6 {
     double kz;             // complex fields: d/dz = i kz (two-dimensional runs)
     double kzA, kzB;       // real fields: d/dz = kzA on {Ex, Ey, Hz}, kzB on {Ez, Hx, Hy}
     double bre[3], bim[3]; // Bloch factors exp(i k_a L_a)
+    // march kernel (two-dimensional runs): elements from buffer 0 to buffer 1 of the
+    // ping-pong fields, psi and Lorentz planes (step n reads buffer (n-1)&1, writes n&1)
+    int64_t fhalf, psi_half, lor_half;
 };
 
 struct DevEnt6 {
@@ -97,6 +100,12 @@ struct DevSrc6 {
 
 void launch_full(int fp64, int cplx, int dims, const DevSim6 *sims, const DevTile6 *tiles, int ntiles,
                  const int64_t *launch_base, int64_t launch_add, int phase, cudaStream_t st);
+
+// Six-component march over TILE_X x TILE_Y tiles of two-dimensional runs, one full step per
+// launch (both half steps), ping-pong buffers.  Tile entries: DevEnt with the field component
+// in bits 16..18 of loc and bit 19 set for the weight of the imaginary part (complex fields).
+void launch_march6(int fp64, int cplx, const DevSim6 *sims, const DevTile *tiles, int ntiles,
+                   const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 void launch_inject6(int fp64, void *fields, const DevSrc6 *src, int nsrc, cudaStream_t st);
 
 // Two-step tiles of the 2D kernel: four warp strips of 28 interior columns; the

@@ -120,11 +120,12 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
     for (auto &run : runs) {
         s2.clear(); s6.clear(); t2.clear(); t6.clear(); pe.clear(); ps.clear();
         bool full = P->sims[run[0]].full;
+        bool march = P->sims[run[0]].march;
         int cplx = P->sims[run[0]].cplx;
         for (size_t q : run) {
             const HostSim &hs = P->sims[q];
             int64_t N = (int64_t)hs.nx * hs.ny * hs.nz;
-            PlainSim one{hs.full ? 0 : 3 * N, (int)pe.size(), 0, acc + q};
+            PlainSim one{hs.full ? (hs.march ? hs.fhalf : 0) : 3 * N, (int)pe.size(), 0, acc + q};
             if (!hs.full) {
                 DevSim2D d;
                 make_sim2d(P, b, acc, tail, 0, q, &d);
@@ -139,6 +140,23 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                         int ly = loc / TILE_X, lx = loc - ly * TILE_X;
                         int64_t g = (int64_t)arr * N + (int64_t)(ht.j0 + ly) * hs.nx + ht.i0 + lx;
                         pe.push_back(PlainEnt{hs.field_off + g, -1, en.w, 0.0});
+                    }
+                }
+            } else if (hs.march) {
+                DevSim6 d;
+                make_sim6(P, b, acc, tail, 0, q, &d);
+                int idx = (int)s6.size();
+                s6.push_back(d);
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile &ht = P->tilesM[t];
+                    t2.push_back(DevTile{idx, ht.i0, ht.j0, 0, nullptr});      // projection runs separately
+                    for (int e = ht.ent0; e < ht.ent0 + ht.ne; ++e) {
+                        const DevEnt &en = P->entsM[e];
+                        int loc = en.loc & 0xffff, arr = (en.loc >> 16) & 7, im = (en.loc >> 19) & 1;
+                        int ly = loc / TILE_X, lx = loc - ly * TILE_X;
+                        int64_t plane = hs.cplx ? 2 * arr + im : arr;
+                        int64_t g = plane * N + (int64_t)(ht.j0 + ly) * hs.nx + ht.i0 + lx;
+                        pe.push_back(PlainEnt{hs.field_off + g, -1, im ? -en.w : en.w, 0.0});
                     }
                 }
             } else {
@@ -164,7 +182,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
         }
         void *d_sim = nullptr, *d_tiles = nullptr, *d_pe = nullptr, *d_ps = nullptr;
         size_t bsim = align256(full ? s6.size() * sizeof(DevSim6) : s2.size() * sizeof(DevSim2D));
-        size_t btil = align256(full ? t6.size() * sizeof(DevTile6) : t2.size() * sizeof(DevTile));
+        size_t btil = align256(full && !march ? t6.size() * sizeof(DevTile6) : t2.size() * sizeof(DevTile));
         size_t bpe = align256(std::max<size_t>(1, pe.size()) * sizeof(PlainEnt));
         size_t bps = align256(ps.size() * sizeof(PlainSim));
         void *rb = nullptr;
@@ -177,7 +195,10 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
         d_ps = (char *)rb + bsim + btil + bpe;
         if (full) {
             CUDA_TRY(cudaMemcpyAsync(d_sim, s6.data(), s6.size() * sizeof(DevSim6), cudaMemcpyHostToDevice, s));
-            CUDA_TRY(cudaMemcpyAsync(d_tiles, t6.data(), t6.size() * sizeof(DevTile6), cudaMemcpyHostToDevice, s));
+            if (march)
+                CUDA_TRY(cudaMemcpyAsync(d_tiles, t2.data(), t2.size() * sizeof(DevTile), cudaMemcpyHostToDevice, s));
+            else
+                CUDA_TRY(cudaMemcpyAsync(d_tiles, t6.data(), t6.size() * sizeof(DevTile6), cudaMemcpyHostToDevice, s));
         } else {
             CUDA_TRY(cudaMemcpyAsync(d_sim, s2.data(), s2.size() * sizeof(DevSim2D), cudaMemcpyHostToDevice, s));
             CUDA_TRY(cudaMemcpyAsync(d_tiles, t2.data(), t2.size() * sizeof(DevTile), cudaMemcpyHostToDevice, s));
@@ -187,6 +208,9 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
         for (int n = 1; n <= D.prob.n_steps; ++n) {
             if (!full) {
                 launch_step2d(P->fp64, (const DevSim2D *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, s);
+                ++launches;
+            } else if (march) {
+                launch_march6(P->fp64, cplx, (const DevSim6 *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, s);
                 ++launches;
             } else {
                 for (int phase = 0; phase < 2; ++phase)

@@ -35,9 +35,12 @@ constexpr int STRIP = 30;                 // interior columns per warp
 constexpr int WARPS = TILE_X / STRIP;     // warps per CTA
 static_assert(WARPS * STRIP == TILE_X, "tile width must be a multiple of the strip");
 
+// i in [-2n, 3n): rows up to two before and after the range, for any n >= 1
 __device__ __forceinline__ int wrap(int i, int n)
 {
     i += i < 0 ? n : 0;
+    i += i < 0 ? n : 0;
+    i -= i >= n ? n : 0;
     return i >= n ? i - n : i;
 }
 
@@ -73,7 +76,7 @@ k_step2d(const DevSim2D *__restrict__ sims, const DevTile *__restrict__ tiles,
     const int i0 = t.i0 + warp * STRIP;               // first interior column of this strip
     const int w = min(STRIP, nx - i0);                // interior columns (may be <= 0)
     const int h = min(TILE_Y, ny - t.j0);
-    const int col = wrap(i0 - 1 + lane, nx);          // this lane's column (lane 0: left halo)
+    const int col = ((i0 - 1 + lane) % nx + nx) % nx;  // this lane's column (lane 0: left halo), any nx >= 1
     const bool store = w > 0 && lane >= 1 && lane <= w;
 
     const R hf = (R)(n == 1 ? 0.5 * S.hf : S.hf);

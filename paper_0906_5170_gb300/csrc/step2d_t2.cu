@@ -27,9 +27,12 @@ constexpr int STRIP2 = 28;
 constexpr int WARPS2 = TILE_X2 / STRIP2;
 static_assert(WARPS2 * STRIP2 == TILE_X2, "tile width must be a multiple of the strip");
 
+// i in [-2n, 3n): rows up to two before and after the range, for any n >= 1
 __device__ __forceinline__ int wrap2(int i, int n)
 {
     i += i < 0 ? n : 0;
+    i += i < 0 ? n : 0;
+    i -= i >= n ? n : 0;
     return i >= n ? i - n : i;
 }
 
@@ -96,7 +99,7 @@ k_step2d_t2(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
     const int i0 = t.i0 + strip_lo;
     const int w = min(STRIP2, nx - i0);
     const int h = min(TILE_Y, ny - t.j0);
-    const int col = wrap2(i0 - 2 + lane, nx);
+    const int col = ((i0 - 2 + lane) % nx + nx) % nx;   // any nx >= 1
     const bool store = w > 0 && lane >= 2 && lane < w + 2;
 
     const R hfA = (R)(nA == 1 ? 0.5 * S.hf : S.hf);

@@ -239,3 +239,57 @@ def test_waves_do_not_change_results(ctx):
         F, _, _ = t.force(-1)
         assert np.allclose(F, F0, rtol=1e-12, atol=0)
     ctx.set_wave_bytes(0)
+
+
+# ---- degenerate grids: narrower than a warp strip, a single row ---------------------------
+
+def _tiny_2d(nx, ny, pol):
+    res = 10.0
+    p = W._base(2, (nx, ny, 1), res, 240)
+    Lx, Ly = nx / res, ny / res
+    if ny >= 8:      # periodic x, a PEC plate across the cell, an open line below it
+        p["bc"] = ["periodic", "pec", "pec"]
+        p["objects"] = [{"shape": "box", "lo": [0.0, 2.5, 0], "hi": [Lx, 2.5, 0], "kind": "pec"},
+                        {"shape": "box", "lo": [0.0, 0.5, 0], "hi": [Lx, 1.0, 0], "kind": "dielectric", "eps": 2.5, "mu": 1.0}]
+        p["faces"] = [{"axis": 1, "sign": -1, "pos": 1.9, "lo": [0.0, 1.9, 0], "hi": [Lx, 1.9, 0]}]
+        p["force_axis"] = 1
+    else:            # periodic y (one or two rows), a dielectric slab across x, a line normal to x
+        p["bc"] = ["pec", "periodic", "pec"]
+        p["objects"] = [{"shape": "box", "lo": [0.6 * Lx, 0.0, 0], "hi": [0.8 * Lx, Ly, 0], "kind": "dielectric", "eps": 3.0, "mu": 1.0}]
+        x = round(0.3 * nx) / res
+        p["faces"] = [{"axis": 0, "sign": 1, "pos": x, "lo": [x, 0.0, 0], "hi": [x, Ly, 0]}]
+        p["force_axis"] = 0
+    p["n_harm"] = min(3, max(1, (nx if p["force_axis"] == 1 else ny)))
+    p["polarization"] = pol
+    return p
+
+
+@pytest.mark.parametrize("nx,ny", [(7, 40), (40, 1), (3, 2)])
+def test_tiny_grids_2d(ctx, nx, ny):
+    # the two-step kernel (batched path) and the one-step kernel (plain path) on grids
+    # narrower than a warp strip or only one or two rows high
+    p = _tiny_2d(nx, ny, "TE+TM")
+    _check(ctx, p, ("tiny2d", nx, ny), True)
+    Fb, pb, _ = ctx.plan(p).run(per_sim=True)
+    Fp, pp, _ = ctx.plan(p).run(per_sim=True, plain=True)
+    assert np.allclose(pp, pb, rtol=1e-9, atol=1e-13 * np.sum(np.abs(pb)))
+
+
+@pytest.mark.parametrize("nx,ny,kind", [(7, 40, "kz"), (40, 1, "bloch"), (3, 2, "kz"), (6, 33, "bloch")])
+def test_tiny_grids_six_component(ctx, nx, ny, kind):
+    import math
+    p = _tiny_2d(nx, ny, "full")
+    if kind == "kz":          # real fields, d/dz -> k_z
+        p["k_points"] = [{"k": [0.0, 0.0, kz], "weight": 0.5} for kz in (0.0, 1.7)]
+    else:                     # complex fields: Bloch phase along the periodic axis, and k_z
+        ax = 0 if p["bc"][0] == "periodic" else 1
+        L = p["n"][ax] / p["resolution"]
+        p["k_points"] = []
+        for m in range(2):
+            k = [0.0, 0.0, 0.9]
+            k[ax] = 2 * math.pi * (m + 0.5) / (2 * L)
+            p["k_points"].append({"k": k, "weight": 0.5})
+    _check(ctx, p, ("tiny6", nx, ny, kind), True)
+    Fb, pb, _ = ctx.plan(p).run(per_sim=True)
+    Fp, pp, _ = ctx.plan(p).run(per_sim=True, plain=True)
+    assert np.allclose(pp, pb, rtol=1e-9, atol=1e-13 * np.sum(np.abs(pb)))
