@@ -95,6 +95,21 @@ static int prepare_plan(casimir_plan_t *P)
         while (P->coef_all.size() % 32) P->coef_all.push_back(0.0);
         P->lor_off.push_back((int64_t)P->lor_all.size());
         if (g.family == FAM_FULL) P->lor_all.insert(P->lor_all.end(), g.lorentz.begin(), g.lorentz.end());
+        // march-kernel form of the Lorentz recurrence: P' = (cp P - cpm P_prev + ce E) cd
+        P->lorc_off.push_back((int64_t)P->lorc_all.size());
+        if (g.family == FAM_FULL && g.has_lorentz) {
+            const double dt = D.dt, sg = D.prob.sigma;
+            for (size_t id = 0; id < g.lorentz.size() / 6; ++id)
+                for (int q = 0; q < 3; ++q) {
+                    const double de = g.lorentz[id * 6 + 2 * q], w0 = g.lorentz[id * 6 + 2 * q + 1];
+                    const double w2dt2 = w0 * w0 * dt * dt;
+                    P->lorc_all.push_back(2.0 - w2dt2);
+                    P->lorc_all.push_back(1.0 - 0.5 * sg * dt);
+                    P->lorc_all.push_back(de * w2dt2);
+                    P->lorc_all.push_back(1.0 / (1.0 + 0.5 * sg * dt));
+                }
+            while (P->lorc_all.size() % 32) P->lorc_all.push_back(0.0);
+        }
         std::array<int64_t, 3> po{-1, -1, -1};
         for (int a = 0; a < 3; ++a)
             if (g.has_pml[a]) {
@@ -209,15 +224,16 @@ static int prepare_plan(casimir_plan_t *P)
             }
             off = (off + 63) & ~(int64_t)63;
             if (hs.march) {
-                // TILE_X x TILE_Y tiles; entries carry the component in bits 16..18 and, for the
-                // imaginary weight of complex fields, bit 19
-                int tx = (hs.nx + TILE_X - 1) / TILE_X, ty = (hs.ny + TILE_Y - 1) / TILE_Y;
+                // one strip tile (MARCH_W x MARCH_H) per warp, row bands outer; entries carry the
+                // component in bits 16..18 and, for the imaginary weight of complex fields, bit 19
+                hs.variant = (hs.psi_half > 0 ? 1 : 0) + (g.has_lorentz ? 2 : 0);
+                int tx = (hs.nx + MARCH_W - 1) / MARCH_W, ty = (hs.ny + MARCH_H - 1) / MARCH_H;
                 std::vector<std::vector<DevEnt>> bucket((size_t)tx * ty);
                 for (const Entry &e : sm.meas) {
                     if (!hs.cplx && inA(e.arr) != inA(sarr)) continue;   // contributes i * real: no real part
                     int i = (int)(e.idx % hs.nx), j = (int)(e.idx / hs.nx);
-                    int ti = i / TILE_X, tj = j / TILE_Y;
-                    int loc = (j - tj * TILE_Y) * TILE_X + (i - ti * TILE_X);
+                    int ti = i / MARCH_W, tj = j / MARCH_H;
+                    int loc = (j - tj * MARCH_H) * MARCH_W + (i - ti * MARCH_W);
                     auto &b = bucket[(size_t)tj * tx + ti];
                     if (e.re != 0.0 || !hs.cplx) b.push_back(DevEnt{loc | (e.arr << 16), 0, e.re});
                     if (hs.cplx && e.im != 0.0) b.push_back(DevEnt{loc | ((e.arr | 8) << 16), 0, e.im});
@@ -228,7 +244,7 @@ static int prepare_plan(casimir_plan_t *P)
                 for (int tj = 0; tj < ty; ++tj)
                     for (int ti = 0; ti < tx; ++ti) {
                         auto &b = bucket[(size_t)tj * tx + ti];
-                        P->tilesM.push_back(HostTile{(int)s, ti * TILE_X, tj * TILE_Y, (int)P->entsM.size(), (int)b.size()});
+                        P->tilesM.push_back(HostTile{(int)s, ti * MARCH_W, tj * MARCH_H, (int)P->entsM.size(), (int)b.size()});
                         P->entsM.insert(P->entsM.end(), b.begin(), b.end());
                     }
                 hs.nent = (int)P->entsM.size() - hs.ent0;
@@ -279,7 +295,8 @@ static int prepare_plan(casimir_plan_t *P)
                                align256(D.gw.size() * 8) + align256(P->ents.size() * sizeof(DevEnt)) +
                                align256(P->src.size() * sizeof(DevSrc)) + align256(P->ents6.size() * sizeof(DevEnt6)) +
                                align256(P->src6.size() * sizeof(DevSrc6)) + align256(P->lor_all.size() * 8) +
-                               align256(P->pml_all.size() * P->rsize) + align256(P->entsM.size() * sizeof(DevEnt)));
+                               align256(P->pml_all.size() * P->rsize) + align256(P->entsM.size() * sizeof(DevEnt)) +
+                               align256(P->lorc_all.size() * P->rsize));
     P->request_bytes = (int64_t)(align256(P->field_elems * P->rsize) + 2 * align256(P->sims.size() * 8) +
                                  P->tiles.size() * sizeof(DevTile) + P->tiles6.size() * sizeof(DevTile6) +
                                  P->tiles2.size() * sizeof(DevTile2) + P->tilesM.size() * sizeof(DevTile) +
@@ -308,12 +325,13 @@ int upload_plan(casimir_plan_t *P, cudaStream_t st)
 {
     if (P->dev.block) return CASIMIR_OK;
     casimir_ctx *c = P->ctx;
-    size_t sz[12] = {align256(P->mat_all.size()), align256(P->coef_all.size() * P->rsize),
+    size_t sz[13] = {align256(P->mat_all.size()), align256(P->coef_all.size() * P->rsize),
                      align256(P->data.gw.size() * 8), align256(P->ents.size() * sizeof(DevEnt)),
                      align256(P->src.size() * sizeof(DevSrc)), align256(P->ents6.size() * sizeof(DevEnt6)),
                      align256(P->src6.size() * sizeof(DevSrc6)), align256(P->lor_all.size() * 8),
                      align256(P->pml_all.size() * P->rsize), align256(P->ents2.size() * sizeof(DevEnt)),
-                     align256(P->rowptr2.size() * sizeof(int)), align256(P->entsM.size() * sizeof(DevEnt))};
+                     align256(P->rowptr2.size() * sizeof(int)), align256(P->entsM.size() * sizeof(DevEnt)),
+                     align256(P->lorc_all.size() * P->rsize)};
     size_t total = 0;
     for (size_t q : sz) total += q;
     void *blk;
@@ -333,7 +351,8 @@ int upload_plan(casimir_plan_t *P, cudaStream_t st)
     P->dev.pml = p; p += sz[8];
     P->dev.ents2 = (DevEnt *)p; p += sz[9];
     P->dev.rowptr2 = (int *)p; p += sz[10];
-    P->dev.entsM = (DevEnt *)p;
+    P->dev.entsM = (DevEnt *)p; p += sz[11];
+    P->dev.lorc = p;
     if ((rc = put_table(P->mat_all, P->dev.mat, st))) return rc;
     if ((rc = put_real(P->coef_all, P->dev.coef, P->fp64, st))) return rc;
     if ((rc = put_table(P->data.gw, P->dev.gw, st))) return rc;
@@ -346,6 +365,7 @@ int upload_plan(casimir_plan_t *P, cudaStream_t st)
     if ((rc = put_table(P->ents2, P->dev.ents2, st))) return rc;
     if ((rc = put_table(P->rowptr2, P->dev.rowptr2, st))) return rc;
     if ((rc = put_table(P->entsM, P->dev.entsM, st))) return rc;
+    if ((rc = put_real(P->lorc_all, P->dev.lorc, P->fp64, st))) return rc;
     c->used += total;
     return CASIMIR_OK;
 }
@@ -477,6 +497,7 @@ void make_sim6(const casimir_plan_t *P, char *blk, double *acc, double *tail, in
     d->mat = P->dev.mat + P->mat_off[hs.geo];
     d->coef = (char *)P->dev.coef + P->coef_off[hs.geo] * P->rsize;
     d->lorentz = P->dev.lor + P->lor_off[hs.geo];
+    d->lorc = (char *)P->dev.lorc + P->lorc_off[hs.geo] * P->rsize;
     d->pml = P->dev.pml;
     d->gw = P->dev.gw;
     d->acc = acc + s;
@@ -532,8 +553,8 @@ static int rebuild(casimir_ctx *c)
     std::vector<DevTile2> tt[2];
     std::vector<DevSim6> s6[8];
     std::vector<DevTile6> t6[8];
-    std::vector<DevSim6> sm6[4];
-    std::vector<DevTile> tm6[4];
+    std::vector<DevSim6> sm6[16];
+    std::vector<DevTile> tm6[16];
     for (auto &aw : c->active_waves) {
         casimir_request *r = aw.first;
         const casimir_request::Wave &w = r->waves[aw.second];
@@ -560,7 +581,7 @@ static int rebuild(casimir_ctx *c)
                     }
                 }
             } else if (hs.march) {
-                int gi = 2 * P->fp64 + hs.cplx;
+                int gi = 4 * (2 * P->fp64 + hs.cplx) + hs.variant;
                 int idx = (int)sm6[gi].size();
                 DevSim6 d;
                 make_sim6(P, blk, r->acc, r->tail, w.s0, s, &d);
@@ -585,7 +606,7 @@ static int rebuild(casimir_ctx *c)
         }
     }
     c->ntiles = 0;
-    for (int gi = 0; gi < 16; ++gi) {
+    for (int gi = 0; gi < 28; ++gi) {
         auto &G = c->groups[gi];
         size_t ns, nt, ss, ts;
         const void *sp, *tp;
@@ -625,8 +646,8 @@ static void launch_steps(casimir_ctx *c, int k)
                 launch_full(((gi - 2) >> 2) & 1, ((gi - 2) >> 1) & 1, ((gi - 2) & 1) ? 3 : 2, (const DevSim6 *)c->groups[gi].sims,
                             (const DevTile6 *)c->groups[gi].tiles, c->groups[gi].ntiles, c->d_launch, j, phase,
                             c->stream);
-        for (int gi = 12; gi < 16; ++gi)
-            launch_march6(((gi - 12) >> 1) & 1, (gi - 12) & 1, (const DevSim6 *)c->groups[gi].sims,
+        for (int gi = 12; gi < 28; ++gi)
+            launch_march6(((gi - 12) >> 3) & 1, ((gi - 12) >> 2) & 1, (gi - 12) & 3, (const DevSim6 *)c->groups[gi].sims,
                           (const DevTile *)c->groups[gi].tiles, c->groups[gi].ntiles, c->d_launch, j, c->stream);
     }
     launch_bump(c->d_launch, k, c->stream);
@@ -664,7 +685,7 @@ static int run_chunk(casimir_ctx *c, int k)
     }
     c->h_launch += k;
     int per_step = 0;
-    for (int gi = 0; gi < 16; ++gi)
+    for (int gi = 0; gi < 28; ++gi)
         if (c->groups[gi].ntiles > 0) per_step += (gi >= 2 && gi < 10) ? 2 : 1;
     for (casimir_request *r : c->active) r->launches += (int64_t)k * per_step + 1;
     return CASIMIR_OK;

@@ -37,6 +37,7 @@ struct HostSim {
     int second_u;
     int full;              // six-component fields
     int march;             // two-dimensional six-component run on the march kernel (ping-pong buffers)
+    int variant;           // march kernel variant: 1 = CPML, + 2 = Lorentz
     int cplx;              // complex fields (Bloch phase)
     int magnetic;
     double kzA, kzB;       // real-phase d/dz factors (two-dimensional k_z runs)
@@ -76,6 +77,7 @@ struct DevPlan {           // device copies of a plan's static tables (kept whil
     DevEnt *ents2 = nullptr;
     int *rowptr2 = nullptr;
     double *lor = nullptr;
+    void *lorc = nullptr;
     void *pml = nullptr;
     size_t bytes = 0;
     void *block = nullptr;
@@ -102,12 +104,14 @@ struct casimir_plan {
     int64_t launches = 0;             // launches a request needs (ceil(T/2) for the two-step kernel)
     int k2d = 1;                      // time steps per launch of the 2D kernel
     std::vector<HostTile6> tiles6;
-    std::vector<HostTile> tilesM;     // march kernel tiles (TILE_X x TILE_Y) with their entries
+    std::vector<HostTile> tilesM;     // march kernel strip tiles (MARCH_W x MARCH_H) with their entries
     std::vector<DevEnt> entsM;
     std::vector<DevEnt6> ents6;
     std::vector<DevSrc6> src6;
     std::vector<double> lor_all;      // per geo [id][6]
     std::vector<int64_t> lor_off;     // per geo, elements
+    std::vector<double> lorc_all;     // per geo [id][3][4] march-kernel Lorentz coefficients
+    std::vector<int64_t> lorc_off;    // per geo, elements
     std::vector<double> pml_all;      // per geo, per PML axis [half][b, c, 1/kappa][n_a]
     std::vector<std::array<int64_t, 3>> pml_off;   // per geo and axis, elements (-1: no PML)
     int64_t field_elems = 0;          // per request
@@ -162,12 +166,12 @@ struct casimir_ctx {
     std::vector<casimir_request *> active;
     // launch groups: [0, 1] the 2D kernel in FP32 / FP64; [2 + 4*fp64 + 2*cplx + (dims == 3)]
     // the six-component kernel; [10, 11] the two-step 2D kernel in FP32 / FP64;
-    // [12 + 2*fp64 + cplx] the six-component march kernel of two-dimensional runs
+    // [12 + 4 * (2*fp64 + cplx) + variant] the six-component march kernel of two-dimensional runs
     struct Group {
         void *sims = nullptr, *tiles = nullptr;
         size_t sims_cap = 0, tiles_cap = 0;
         int ntiles = 0;
-    } groups[16];
+    } groups[28];
     int ntiles = 0;                   // over all groups
     // waves: simulations are activated in groups whose field bytes fit `wave_bytes`
     // (0: a whole request at once), so that the active working set can stay in L2

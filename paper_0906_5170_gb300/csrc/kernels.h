@@ -55,6 +55,8 @@ struct DevSim6 {
     const uint8_t *mat;    // per-cell material id
     const void *coef;      // [id][6]: 1/eps at E_x..E_z sites, 1/mu at H_x..H_z sites (0 masks)
     const double *lorentz; // [id][3][2]: (delta_eps, omega0) per E component
+    const void *lorc;      // [id][3][4] in the run's precision: cp = 2 - w0^2 dt^2, cpm = 1 - sigma dt/2,
+                           // ce = delta_eps w0^2 dt^2, cd = 1/(1 + sigma dt/2) (march kernel)
     const void *pml;       // CPML profiles: axis a at pml_off[a]: [half][b, c, 1/kappa][n_a]
     const double *gw;
     double *acc;
@@ -101,10 +103,14 @@ struct DevSrc6 {
 void launch_full(int fp64, int cplx, int dims, const DevSim6 *sims, const DevTile6 *tiles, int ntiles,
                  const int64_t *launch_base, int64_t launch_add, int phase, cudaStream_t st);
 
-// Six-component march over TILE_X x TILE_Y tiles of two-dimensional runs, one full step per
-// launch (both half steps), ping-pong buffers.  Tile entries: DevEnt with the field component
-// in bits 16..18 of loc and bit 19 set for the weight of the imaginary part (complex fields).
-void launch_march6(int fp64, int cplx, const DevSim6 *sims, const DevTile *tiles, int ntiles,
+// Six-component march of two-dimensional runs: one warp per strip tile of MARCH_W columns and
+// MARCH_H rows, one full step per launch (both half steps), ping-pong buffers.  Tile entries:
+// DevEnt with loc = ly * MARCH_W + lx in bits 0..15, the field component in bits 16..18 and
+// bit 19 set for the weight of the imaginary part (complex fields).  variant: 1 = CPML planes
+// present, + 2 = Lorentz planes present.
+constexpr int MARCH_W = 30;
+constexpr int MARCH_H = 32;
+void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles,
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 void launch_inject6(int fp64, void *fields, const DevSrc6 *src, int nsrc, cudaStream_t st);
 

@@ -153,7 +153,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                     for (int e = ht.ent0; e < ht.ent0 + ht.ne; ++e) {
                         const DevEnt &en = P->entsM[e];
                         int loc = en.loc & 0xffff, arr = (en.loc >> 16) & 7, im = (en.loc >> 19) & 1;
-                        int ly = loc / TILE_X, lx = loc - ly * TILE_X;
+                        int ly = loc / MARCH_W, lx = loc - ly * MARCH_W;
                         int64_t plane = hs.cplx ? 2 * arr + im : arr;
                         int64_t g = plane * N + (int64_t)(ht.j0 + ly) * hs.nx + ht.i0 + lx;
                         pe.push_back(PlainEnt{hs.field_off + g, -1, im ? -en.w : en.w, 0.0});
@@ -210,7 +210,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                 launch_step2d(P->fp64, (const DevSim2D *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, s);
                 ++launches;
             } else if (march) {
-                launch_march6(P->fp64, cplx, (const DevSim6 *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, s);
+                launch_march6(P->fp64, cplx, P->sims[run[0]].variant, (const DevSim6 *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, s);
                 ++launches;
             } else {
                 for (int phase = 0; phase < 2; ++phase)

@@ -3,18 +3,20 @@
 //
 // The update is the one of step6.cu (CPML of Sec. III B, Lorentz ADE of Eq. (9)
 // continued onto the contour, surface functional weighted by w_n = 2 dt
-// Im g(-n dt), Eq. (1)), organised like the TM-form kernel of step2d.cu: a CTA
-// owns a TILE_X x TILE_Y tile of one simulation, each warp a strip of 30
-// columns plus one halo lane per side, marching down the rows with x
-// neighbours exchanged by shuffles and y neighbours carried in registers.
-// Electric sources update H first (E of rows j and j+1 give H of row j), then
-// E; magnetic sources update E one row ahead, then H.  Fields, CPML psi and
-// Lorentz P ping-pong between two buffers by step parity, so that halo lanes
-// recompute a neighbour's first half step from values nobody overwrites.
+// Im g(-n dt), Eq. (1)), organised as a row march: every warp owns a strip of
+// MARCH_W columns and MARCH_H rows of one simulation (lane 0 and lane w + 1
+// are halo columns), walks down the rows with x neighbours exchanged by
+// shuffles and y neighbours carried in registers, and loads the next row's
+// inputs while it computes the current one.  Electric sources update H first
+// (E of rows j and j+1 give H of row j), then E; magnetic sources update E one
+// row ahead, then H.  Fields, CPML psi and Lorentz P ping-pong between two
+// buffers by step parity, so that halo lanes recompute a neighbour's first
+// half step from values nobody overwrites.
 //
 // Storage within one buffer is that of step6.cu: E_x..H_z planes of nx*ny
 // elements (real and imaginary planes when complex), psi planes per PML axis
-// over its two slabs, Lorentz P then P_prev per E component.
+// over its two slabs (planes 0, 1 for the E update, 2, 3 for the H update),
+// Lorentz P then P_prev per E component.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -23,9 +25,7 @@ namespace cas {
 
 namespace {
 
-constexpr int STRIP6 = 30;
-constexpr int WARPS6 = TILE_X / STRIP6;
-static_assert(WARPS6 * STRIP6 == TILE_X, "tile width must be a multiple of the strip");
+constexpr int WARPS6 = 4;   // warps (strips) per CTA
 
 template <typename R, bool CPLX>
 struct Z;
@@ -58,253 +58,355 @@ struct Z<R, true> {
 };
 
 template <typename R, bool CPLX>
-__device__ __forceinline__ Z<R, CPLX> ld(const R *p, int plane, size_t N, size_t g)
+__device__ __forceinline__ Z<R, CPLX> ld(const R *__restrict__ p, int plane, size_t N, size_t g)
 {
     if constexpr (CPLX) return Z<R, CPLX>(p[(size_t)(2 * plane) * N + g], p[(size_t)(2 * plane + 1) * N + g]);
     else return Z<R, CPLX>(p[(size_t)plane * N + g]);
 }
 
 template <typename R, bool CPLX>
-__device__ __forceinline__ void st(R *p, int plane, size_t N, size_t g, Z<R, CPLX> v)
+__device__ __forceinline__ void st(R *__restrict__ p, int plane, size_t N, size_t g, Z<R, CPLX> v)
 {
     if constexpr (CPLX) { p[(size_t)(2 * plane) * N + g] = v.x; p[(size_t)(2 * plane + 1) * N + g] = v.y; }
     else p[(size_t)plane * N + g] = v.x;
 }
 
-// One CPML-stretched difference: psi' = b psi + c d (written by the owner of the cell),
-// returned value d / kappa + psi'.  prof holds b, c, 1/kappa, n entries each.
+// The inputs of one row step, loaded one row ahead.  Electric sources (row j):
+// f = E(j+1), q = H(j), m, P(j), psi(j) of all four planes.  Magnetic sources:
+// f = H(j+1), q = E(j+1) (old), m of row j+1, P(j+1), psi planes 0, 1 of row j+1
+// and 2, 3 of row j.
 template <typename R, bool CPLX>
-__device__ __forceinline__ Z<R, CPLX> cpml(Z<R, CPLX> d, const R *prof, int n, int pos, const R *pin, R *pout,
-                                           int plane, size_t P, size_t gi, bool write)
-{
-    const R b = prof[pos], c = prof[n + pos], ik = prof[2 * n + pos];
-    const Z<R, CPLX> p = ld<R, CPLX>(pin, plane, P, gi) * b + d * c;
-    if (write) st<R, CPLX>(pout, plane, P, gi, p);
-    return d * ik + p;
-}
+struct RowIn {
+    Z<R, CPLX> f[3], q[3];
+    int m;
+    Z<R, CPLX> p[3], pm[3];
+    Z<R, CPLX> px[4], py[4];
+};
 
-template <typename R, bool CPLX>
-__global__ void __launch_bounds__(WARPS6 * 32)
-k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles,
+template <typename R, bool CPLX, bool PML, bool LOR, int MINB>
+__global__ void __launch_bounds__(WARPS6 * 32, MINB)
+k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, int ntiles,
          const int64_t *__restrict__ launch_base, int64_t launch_add)
 {
     using V = Z<R, CPLX>;
-    __shared__ double red[WARPS6];
-    const DevTile t = tiles[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ti = blockIdx.x * WARPS6 + warp;
+    if (ti >= ntiles) return;
+    const DevTile t = tiles[ti];
     const DevSim6 &S = sims[t.sim];
     const int64_t n = *launch_base + launch_add - S.s0;
     if (n < 1 || n > S.T) return;
     const int nx = S.n[0], ny = S.n[1];
     const size_t N = (size_t)nx * ny;
     const int pin_par = (int)((n - 1) & 1), pout_par = (int)(n & 1);
-    const R *fin = reinterpret_cast<const R *>(S.fields) + (size_t)pin_par * S.fhalf;
-    R *fout = reinterpret_cast<R *>(S.fields) + (size_t)pout_par * S.fhalf;
-    const R *coef = reinterpret_cast<const R *>(S.coef);
-    const int dX = S.pml_d[0], dY = S.pml_d[1];
-    const size_t PX = (size_t)S.slab[0], PY = (size_t)S.slab[1];
-    const R *psi_in = S.psi ? reinterpret_cast<const R *>(S.psi) + (size_t)pin_par * S.psi_half : nullptr;
-    R *psi_out = S.psi ? reinterpret_cast<R *>(S.psi) + (size_t)pout_par * S.psi_half : nullptr;
-    const R *pxin = dX ? psi_in + S.psi_off[0] : nullptr;
-    R *pxout = dX ? psi_out + S.psi_off[0] : nullptr;
-    const R *pyin = dY ? psi_in + S.psi_off[1] : nullptr;
-    R *pyout = dY ? psi_out + S.psi_off[1] : nullptr;
-    const R *profx = dX ? reinterpret_cast<const R *>(S.pml) + S.pml_off[0] : nullptr;   // [half][b, c, 1/kappa][nx]
-    const R *profy = dY ? reinterpret_cast<const R *>(S.pml) + S.pml_off[1] : nullptr;
-    const R *lin = S.lor ? reinterpret_cast<const R *>(S.lor) + (size_t)pin_par * S.lor_half : nullptr;
-    R *lout = S.lor ? reinterpret_cast<R *>(S.lor) + (size_t)pout_par * S.lor_half : nullptr;
+    const R *__restrict__ fin = reinterpret_cast<const R *>(S.fields) + (size_t)pin_par * S.fhalf;
+    R *__restrict__ fout = reinterpret_cast<R *>(S.fields) + (size_t)pout_par * S.fhalf;
+    const R *__restrict__ coef = reinterpret_cast<const R *>(S.coef);
+    const uint8_t *__restrict__ mat = S.mat;
+    const int dX = PML ? S.pml_d[0] : 0, dY = PML ? S.pml_d[1] : 0;
+    const size_t PX = PML ? (size_t)S.slab[0] : 0, PY = PML ? (size_t)S.slab[1] : 0;
+    const R *__restrict__ pxin = nullptr, *__restrict__ pyin = nullptr, *__restrict__ profy = nullptr;
+    R *__restrict__ pxout = nullptr, *__restrict__ pyout = nullptr;
+    if constexpr (PML) {
+        const R *psi_in = reinterpret_cast<const R *>(S.psi) + (size_t)pin_par * S.psi_half;
+        R *psi_out = reinterpret_cast<R *>(S.psi) + (size_t)pout_par * S.psi_half;
+        pxin = psi_in + S.psi_off[0];
+        pxout = psi_out + S.psi_off[0];
+        pyin = psi_in + S.psi_off[1];
+        pyout = psi_out + S.psi_off[1];
+        profy = reinterpret_cast<const R *>(S.pml) + S.pml_off[1];   // [half][b, c, 1/kappa][ny]
+    }
+    const R *__restrict__ lin = nullptr, *__restrict__ lc = nullptr;
+    R *__restrict__ lout = nullptr;
+    if constexpr (LOR) {
+        lin = reinterpret_cast<const R *>(S.lor) + (size_t)pin_par * S.lor_half;
+        lout = reinterpret_cast<R *>(S.lor) + (size_t)pout_par * S.lor_half;
+        lc = reinterpret_cast<const R *>(S.lorc);                    // [id][3][cp, cpm, ce, cd]
+    }
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i0 = t.i0 + warp * STRIP6;
-    const int w = min(STRIP6, nx - i0);
-    const int h = min(TILE_Y, ny - t.j0);
+    const int i0 = t.i0;
+    const int w = min(MARCH_W, nx - i0);
+    const int h = min(MARCH_H, ny - t.j0);
     const int col = ((i0 - 1 + lane) % nx + nx) % nx;     // lane 0: left halo, lane w + 1: right halo
-    const bool own = w > 0 && lane >= 1 && lane <= w;
+    const bool own = lane >= 1 && lane <= w;
     const bool wrapR = col == nx - 1;                     // the right neighbour lies across the x wrap
     const bool wrapL = col == 0;                          // the left neighbour lies across the x wrap
-    const bool inx = dX > 0 && (col < dX || col >= nx - dX);
+    const bool inx = PML && dX > 0 && (col < dX || col >= nx - dX);
     const int sx = col < dX ? col : col - (nx - 2 * dX);
+    // x profiles of this column: [b, c, 1/kappa] for the E update (integer sites) and the H update
+    R xe[3] = {0, 0, 1}, xh[3] = {0, 0, 1};
+    if (inx) {
+        const R *pr = reinterpret_cast<const R *>(S.pml) + S.pml_off[0];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            xe[k] = pr[k * nx + col];
+            xh[k] = pr[(3 + k) * nx + col];
+        }
+    }
     const R bxr = (R)S.bre[0], bxi = (R)S.bim[0], byr = (R)S.bre[1], byi = (R)S.bim[1];
     const R idx = (R)S.inv_dx;
     const R kA = (R)S.kzA, kB = (R)S.kzB, kc = (R)S.kz;
     const R a = (R)S.a, bs = (R)S.bs;
     const R hfirst = (R)(n == 1 ? 0.5 * S.dt : S.dt);
-    const R dtl = (R)S.dt_full, sg = (R)S.sigma;
+    const bool electric = S.magnetic == 0;
+    const bool first_e = electric && n == 1;              // Lorentz start of electric sources
+    auto rowp = [&](int j) { return j < 0 ? j + ny : (j >= ny ? j - ny : j); };
+    auto iny = [&](int j) { return PML && dY > 0 && (j < dY || j >= ny - dY); };
+    auto gxi = [&](int j) { return (size_t)j * (2 * dX) + sx; };
+    auto gyi = [&](int j) { return (size_t)(j < dY ? j : j - (ny - 2 * dY)) * nx + col; };
 
     // d/dz of a field of the set {Ex, Ey, Hz} (A) or {Ez, Hx, Hy} (B)
     auto dzA = [&](V f) -> V { if constexpr (CPLX) return f.ik(kc); else return f * kA; };
     auto dzB = [&](V f) -> V { if constexpr (CPLX) return f.ik(kc); else return f * kB; };
     auto right = [&](V f) -> V { V r = f.dn(); return wrapR ? r.ph(bxr, bxi) : r; };
     auto left = [&](V f) -> V { V l = f.up(); return wrapL ? l.ph(bxr, -bxi) : l; };
-    auto rowp = [&](int j) { return j < 0 ? j + ny : (j >= ny ? j - ny : j); };
+    // CPML-stretched difference: psi' = b psi + c d; d / kappa + psi'
+    auto str = [&](V d, const R *pr, V psi, V &pn) -> V { pn = psi * pr[0] + d * pr[1]; return d * pr[2] + pn; };
 
-    // H at row j from E at rows j and j+1 (forward differences, half-site profiles)
-    auto updH = [&](int j, int m, V ex, V ey, V ez, V exn, V ezn, V hx, V hy, V hz, R aa, R bb, bool wr,
-                    V &hxo, V &hyo, V &hzo) {
-        if (j + 1 >= ny) { exn = exn.ph(byr, byi); ezn = ezn.ph(byr, byi); }
-        V dyEz = (ezn - ez) * idx, dyEx = (exn - ex) * idx;
-        V dxEz = (right(ez) - ez) * idx, dxEy = (right(ey) - ey) * idx;
-        if (inx) {
-            const size_t gi = (size_t)j * (2 * dX) + sx;
-            dxEz = cpml<R, CPLX>(dxEz, profx + 3 * nx, nx, col, pxin, pxout, 2, PX, gi, wr);   // H_y
-            dxEy = cpml<R, CPLX>(dxEy, profx + 3 * nx, nx, col, pxin, pxout, 3, PX, gi, wr);   // H_z
-        }
-        if (dY > 0 && (j < dY || j >= ny - dY)) {
-            const size_t gi = (size_t)(j < dY ? j : j - (ny - 2 * dY)) * nx + col;
-            dyEx = cpml<R, CPLX>(dyEx, profy + 3 * ny, ny, j, pyin, pyout, 2, PY, gi, wr);   // H_z
-            dyEz = cpml<R, CPLX>(dyEz, profy + 3 * ny, ny, j, pyin, pyout, 3, PY, gi, wr);   // H_x
-        }
-        const R *cm = coef + 6 * m;
-        hxo = hx * aa - (dyEz - dzA(ey)) * (bb * cm[3]);
-        hyo = hy * aa - (dzA(ex) - dxEz) * (bb * cm[4]);
-        hzo = hz * aa - (dxEy - dyEx) * (bb * cm[5]);
-    };
-    // E at row j from H at rows j and j-1 (backward differences, integer-site profiles)
-    auto updE = [&](int j, int m, V hx, V hy, V hz, V hxp, V hzp, V ex, V ey, V ez, R aa, R bb, bool wr,
-                    bool first_e, size_t g, V &exo, V &eyo, V &ezo) {
-        if (j - 1 < 0) { hxp = hxp.ph(byr, -byi); hzp = hzp.ph(byr, -byi); }
-        V dyHz = (hz - hzp) * idx, dyHx = (hx - hxp) * idx;
-        V dxHz = (hz - left(hz)) * idx, dxHy = (hy - left(hy)) * idx;
-        if (inx) {
-            const size_t gi = (size_t)j * (2 * dX) + sx;
-            dxHz = cpml<R, CPLX>(dxHz, profx, nx, col, pxin, pxout, 0, PX, gi, wr);   // E_y
-            dxHy = cpml<R, CPLX>(dxHy, profx, nx, col, pxin, pxout, 1, PX, gi, wr);   // E_z
-        }
-        if (dY > 0 && (j < dY || j >= ny - dY)) {
-            const size_t gi = (size_t)(j < dY ? j : j - (ny - 2 * dY)) * nx + col;
-            dyHx = cpml<R, CPLX>(dyHx, profy, ny, j, pyin, pyout, 0, PY, gi, wr);   // E_z
-            dyHz = cpml<R, CPLX>(dyHz, profy, ny, j, pyin, pyout, 1, PY, gi, wr);   // E_x
-        }
-        const V c3[3] = {dyHz - dzB(hy), dzB(hx) - dxHz, dxHy - dyHx};
-        const V e3[3] = {ex, ey, ez};
-        V o3[3];
-        const R *cm = coef + 6 * m;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const R de = lin ? (R)S.lorentz[6 * m + 2 * q] : (R)0;
-            if (de != (R)0) {
-                const R w0 = (R)S.lorentz[6 * m + 2 * q + 1];
-                const R w2 = w0 * w0;
-                const V p = ld<R, CPLX>(lin, q, N, g), pm = ld<R, CPLX>(lin, 3 + q, N, g);
-                const V pn = first_e
-                    ? (p * ((R)2 - w2 * dtl * dtl) + e3[q] * (de * w2 * dtl * dtl)) * (R)0.5
-                    : (p * ((R)2 - w2 * dtl * dtl) - pm * ((R)1 - (R)0.5 * sg * dtl) + e3[q] * (de * w2 * dtl * dtl)) *
-                          ((R)1 / ((R)1 + (R)0.5 * sg * dtl));
-                if (wr) {
-                    st<R, CPLX>(lout, q, N, g, pn);
-                    st<R, CPLX>(lout, 3 + q, N, g, p);
-                }
-                o3[q] = e3[q] * aa + (p * aa - pn + c3[q] * bb) * cm[q];
-            } else {
-                o3[q] = e3[q] * aa + c3[q] * (bb * cm[q]);
+    // loads of the psi planes of row j (lo..hi of 0..3) into px / py
+    auto load_psi = [&](RowIn<R, CPLX> &in, int j, int lo, int hi) {
+        if constexpr (PML) {
+            if (inx) {
+                const size_t g = gxi(j);
+                for (int k = lo; k < hi; ++k) in.px[k] = ld<R, CPLX>(pxin, k, PX, g);
+            }
+            if (iny(j)) {
+                const size_t g = gyi(j);
+                for (int k = lo; k < hi; ++k) in.py[k] = ld<R, CPLX>(pyin, k, PY, g);
             }
         }
-        exo = o3[0];
-        eyo = o3[1];
-        ezo = o3[2];
     };
-    auto put6 = [&](size_t g, V ex, V ey, V ez, V hx, V hy, V hz) {
-        st<R, CPLX>(fout, 0, N, g, ex);
-        st<R, CPLX>(fout, 1, N, g, ey);
-        st<R, CPLX>(fout, 2, N, g, ez);
-        st<R, CPLX>(fout, 3, N, g, hx);
-        st<R, CPLX>(fout, 4, N, g, hy);
-        st<R, CPLX>(fout, 5, N, g, hz);
+    auto load_lor = [&](RowIn<R, CPLX> &in, size_t g) {
+        if constexpr (LOR) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                in.p[k] = ld<R, CPLX>(lin, k, N, g);
+                in.pm[k] = ld<R, CPLX>(lin, 3 + k, N, g);
+            }
+        }
+    };
+
+    // H at row j from E at rows j and j+1: new H, and the H-plane psi (2, 3) written when wr
+    auto updH = [&](int j, int m, const V e[3], V exn, V ezn, const V hq[3], const V px[4], const V py[4],
+                    R aa, R bb, bool wr, V ho[3]) {
+        if (j + 1 >= ny) { exn = exn.ph(byr, byi); ezn = ezn.ph(byr, byi); }
+        V dyEz = (ezn - e[2]) * idx, dyEx = (exn - e[0]) * idx;
+        V dxEz = (right(e[2]) - e[2]) * idx, dxEy = (right(e[1]) - e[1]) * idx;
+        if constexpr (PML) {
+            if (inx) {
+                V p2, p3;
+                const R b2[3] = {xh[0], xh[1], xh[2]};
+                dxEz = str(dxEz, b2, px[2], p2);   // H_y
+                dxEy = str(dxEy, b2, px[3], p3);   // H_z
+                if (wr) { const size_t g = gxi(j); st<R, CPLX>(pxout, 2, PX, g, p2); st<R, CPLX>(pxout, 3, PX, g, p3); }
+            }
+            if (iny(j)) {
+                const R pr[3] = {profy[3 * ny + j], profy[4 * ny + j], profy[5 * ny + j]};
+                V p2, p3;
+                dyEx = str(dyEx, pr, py[2], p2);   // H_z
+                dyEz = str(dyEz, pr, py[3], p3);   // H_x
+                if (wr) { const size_t g = gyi(j); st<R, CPLX>(pyout, 2, PY, g, p2); st<R, CPLX>(pyout, 3, PY, g, p3); }
+            }
+        }
+        const R *cm = coef + 6 * m;
+        ho[0] = hq[0] * aa - (dyEz - dzA(e[1])) * (bb * cm[3]);
+        ho[1] = hq[1] * aa - (dzA(e[0]) - dxEz) * (bb * cm[4]);
+        ho[2] = hq[2] * aa - (dxEy - dyEx) * (bb * cm[5]);
+    };
+    // E at row j from H at rows j and j-1: new E, the E-plane psi (0, 1) and P written when wr
+    auto updE = [&](int j, int m, const V hh[3], V hxp, V hzp, const V eo[3], const RowIn<R, CPLX> &in, R aa, R bb,
+                    bool wr, size_t g, V eo_new[3]) {
+        if (j - 1 < 0) { hxp = hxp.ph(byr, -byi); hzp = hzp.ph(byr, -byi); }
+        V dyHz = (hh[2] - hzp) * idx, dyHx = (hh[0] - hxp) * idx;
+        V dxHz = (hh[2] - left(hh[2])) * idx, dxHy = (hh[1] - left(hh[1])) * idx;
+        if constexpr (PML) {
+            if (inx) {
+                V p0, p1;
+                dxHz = str(dxHz, xe, in.px[0], p0);   // E_y
+                dxHy = str(dxHy, xe, in.px[1], p1);   // E_z
+                if (wr) { const size_t gg = gxi(j); st<R, CPLX>(pxout, 0, PX, gg, p0); st<R, CPLX>(pxout, 1, PX, gg, p1); }
+            }
+            if (iny(j)) {
+                const R pr[3] = {profy[j], profy[ny + j], profy[2 * ny + j]};
+                V p0, p1;
+                dyHx = str(dyHx, pr, in.py[0], p0);   // E_z
+                dyHz = str(dyHz, pr, in.py[1], p1);   // E_x
+                if (wr) { const size_t gg = gyi(j); st<R, CPLX>(pyout, 0, PY, gg, p0); st<R, CPLX>(pyout, 1, PY, gg, p1); }
+            }
+        }
+        const V c3[3] = {dyHz - dzB(hh[1]), dzB(hh[0]) - dxHz, dxHy - dyHx};
+        const R *cm = coef + 6 * m;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if constexpr (LOR) {
+                const R *l4 = lc + 12 * m + 4 * k;
+                const R ce = l4[2];
+                if (ce != (R)0) {
+                    // P^{n+1} = [cp P^n - cpm P^{n-1} + ce E^n] cd; the first electric step starts from rest
+                    const V pn = first_e ? (in.p[k] * l4[0] + eo[k] * ce) * (R)0.5
+                                         : (in.p[k] * l4[0] - in.pm[k] * l4[1] + eo[k] * ce) * l4[3];
+                    if (wr) {
+                        st<R, CPLX>(lout, k, N, g, pn);
+                        st<R, CPLX>(lout, 3 + k, N, g, in.p[k]);
+                    }
+                    eo_new[k] = eo[k] * aa + (in.p[k] * aa - pn + c3[k] * bb) * cm[k];
+                    continue;
+                }
+            }
+            eo_new[k] = eo[k] * aa + c3[k] * (bb * cm[k]);
+        }
     };
 
     if (w > 0) {
         const int j0 = t.j0;
         const int jm = rowp(j0 - 1);
         const size_t gm = (size_t)jm * nx + col, g0 = (size_t)j0 * nx + col;
-        if (S.magnetic == 0) {
+        RowIn<R, CPLX> cur, nxt;
+        if (electric) {
             // H (a = 1, b = h) then E (a, b_sigma).  Carried: E^n of row j, H^{n+1/2} of row j-1.
-            V hxp, hyp, hzp;
-            V ex = ld<R, CPLX>(fin, 0, N, g0), ey = ld<R, CPLX>(fin, 1, N, g0), ez = ld<R, CPLX>(fin, 2, N, g0);
-            updH(jm, S.mat[gm], ld<R, CPLX>(fin, 0, N, gm), ld<R, CPLX>(fin, 1, N, gm), ld<R, CPLX>(fin, 2, N, gm), ex, ez,
-                 ld<R, CPLX>(fin, 3, N, gm), ld<R, CPLX>(fin, 4, N, gm), ld<R, CPLX>(fin, 5, N, gm), (R)1, hfirst, false,
-                 hxp, hyp, hzp);
+            V e[3], hp[3];
+            {
+                RowIn<R, CPLX> in0;
+                const V em[3] = {ld<R, CPLX>(fin, 0, N, gm), ld<R, CPLX>(fin, 1, N, gm), ld<R, CPLX>(fin, 2, N, gm)};
+                const V hm[3] = {ld<R, CPLX>(fin, 3, N, gm), ld<R, CPLX>(fin, 4, N, gm), ld<R, CPLX>(fin, 5, N, gm)};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) e[k] = ld<R, CPLX>(fin, k, N, g0);
+                load_psi(in0, jm, 2, 4);
+                updH(jm, mat[gm], em, e[0], e[2], hm, in0.px, in0.py, (R)1, hfirst, false, hp);
+            }
+            auto load_row = [&](RowIn<R, CPLX> &in, int j) {
+                const size_t g = (size_t)j * nx + col, gn = (size_t)rowp(j + 1) * nx + col;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    in.f[k] = ld<R, CPLX>(fin, k, N, gn);
+                    in.q[k] = ld<R, CPLX>(fin, 3 + k, N, g);
+                }
+                in.m = mat[g];
+                load_lor(in, g);
+                load_psi(in, j, 0, 4);
+            };
+            load_row(cur, j0);
             for (int r = 0; r < h; ++r) {
                 const int j = j0 + r;
-                const size_t g = (size_t)j * nx + col, gn = (size_t)rowp(j + 1) * nx + col;
-                const V exn = ld<R, CPLX>(fin, 0, N, gn), eyn = ld<R, CPLX>(fin, 1, N, gn), ezn = ld<R, CPLX>(fin, 2, N, gn);
-                const int m = S.mat[g];
-                V hx, hy, hz;
-                updH(j, m, ex, ey, ez, exn, ezn, ld<R, CPLX>(fin, 3, N, g), ld<R, CPLX>(fin, 4, N, g),
-                     ld<R, CPLX>(fin, 5, N, g), (R)1, hfirst, own, hx, hy, hz);
-                V ex1, ey1, ez1;
-                updE(j, m, hx, hy, hz, hxp, hzp, ex, ey, ez, a, bs, own, n == 1, g, ex1, ey1, ez1);
-                if (own) put6(g, ex1, ey1, ez1, hx, hy, hz);
-                hxp = hx;
-                hzp = hz;
-                ex = exn;
-                ey = eyn;
-                ez = ezn;
+                const size_t g = (size_t)j * nx + col;
+                if (r + 1 < h) load_row(nxt, j + 1);
+                V hn[3], en[3];
+                updH(j, cur.m, e, cur.f[0], cur.f[2], cur.q, cur.px, cur.py, (R)1, hfirst, own, hn);
+                updE(j, cur.m, hn, hp[0], hp[2], e, cur, a, bs, own, g, en);
+                if (own) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        st<R, CPLX>(fout, k, N, g, en[k]);
+                        st<R, CPLX>(fout, 3 + k, N, g, hn[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    hp[k] = hn[k];
+                    e[k] = cur.f[k];
+                }
+                cur = nxt;
             }
         } else {
             // E (a = 1, b = h) one row ahead, then H (a, b_sigma).  Carried: H^n of row j, E^{n+1} of row j.
-            V hx = ld<R, CPLX>(fin, 3, N, g0), hy = ld<R, CPLX>(fin, 4, N, g0), hz = ld<R, CPLX>(fin, 5, N, g0);
-            int m = S.mat[g0];
-            V ex, ey, ez;
-            updE(j0, m, hx, hy, hz, ld<R, CPLX>(fin, 3, N, gm), ld<R, CPLX>(fin, 5, N, gm), ld<R, CPLX>(fin, 0, N, g0),
-                 ld<R, CPLX>(fin, 1, N, g0), ld<R, CPLX>(fin, 2, N, g0), (R)1, hfirst, own, false, g0, ex, ey, ez);
+            V hq[3], e[3];
+            int m;
+            {
+                RowIn<R, CPLX> in0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) hq[k] = ld<R, CPLX>(fin, 3 + k, N, g0);
+                const V eo[3] = {ld<R, CPLX>(fin, 0, N, g0), ld<R, CPLX>(fin, 1, N, g0), ld<R, CPLX>(fin, 2, N, g0)};
+                m = mat[g0];
+                load_lor(in0, g0);
+                load_psi(in0, j0, 0, 2);
+                updE(j0, m, hq, ld<R, CPLX>(fin, 3, N, gm), ld<R, CPLX>(fin, 5, N, gm), eo, in0, (R)1, hfirst, own, g0, e);
+            }
+            auto load_row = [&](RowIn<R, CPLX> &in, int j) {
+                const int jn = rowp(j + 1);
+                const size_t gn = (size_t)jn * nx + col;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    in.f[k] = ld<R, CPLX>(fin, 3 + k, N, gn);
+                    in.q[k] = ld<R, CPLX>(fin, k, N, gn);
+                }
+                in.m = mat[gn];
+                load_lor(in, gn);
+                load_psi(in, jn, 0, 2);
+                load_psi(in, j, 2, 4);
+            };
+            load_row(cur, j0);
             for (int r = 0; r < h; ++r) {
                 const int j = j0 + r, jn = rowp(j + 1);
                 const size_t g = (size_t)j * nx + col, gn = (size_t)jn * nx + col;
-                const V hxn = ld<R, CPLX>(fin, 3, N, gn), hyn = ld<R, CPLX>(fin, 4, N, gn), hzn = ld<R, CPLX>(fin, 5, N, gn);
-                const int mn = S.mat[gn];
-                V exn, eyn, ezn;   // E of row j + 1: psi and P written only for rows of this tile
-                updE(jn, mn, hxn, hyn, hzn, hx, hz, ld<R, CPLX>(fin, 0, N, gn), ld<R, CPLX>(fin, 1, N, gn),
-                     ld<R, CPLX>(fin, 2, N, gn), (R)1, hfirst, own && r + 1 < h, false, gn, exn, eyn, ezn);
-                V hx1, hy1, hz1;
-                updH(j, m, ex, ey, ez, exn, ezn, hx, hy, hz, a, bs, own, hx1, hy1, hz1);
-                if (own) put6(g, ex, ey, ez, hx1, hy1, hz1);
-                ex = exn;
-                ey = eyn;
-                ez = ezn;
-                hx = hxn;
-                hy = hyn;
-                hz = hzn;
-                m = mn;
+                if (r + 1 < h) load_row(nxt, j + 1);
+                V en[3], hn[3];
+                // E of row j + 1: psi and P written only for rows of this strip
+                updE(jn, cur.m, cur.f, hq[0], hq[2], cur.q, cur, (R)1, hfirst, own && r + 1 < h, gn, en);
+                updH(j, m, e, en[0], en[2], hq, cur.px, cur.py, a, bs, own, hn);
+                if (own) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        st<R, CPLX>(fout, k, N, g, e[k]);
+                        st<R, CPLX>(fout, 3 + k, N, g, hn[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    e[k] = en[k];
+                    hq[k] = cur.f[k];
+                }
+                m = cur.m;
+                cur = nxt;
             }
         }
     }
 
     if (t.ne > 0) {
-        __syncthreads();   // the block's field writes are visible to the block
+        __syncwarp();   // the strip's field writes are visible to the warp
         double part = 0.0;
-        for (int e = threadIdx.x; e < t.ne; e += blockDim.x) {
+        for (int e = lane; e < t.ne; e += 32) {
             const DevEnt en = t.ents[e];
             const int loc = en.loc & 0xffff, arr = (en.loc >> 16) & 7, im = (en.loc >> 19) & 1;
-            const int ly = loc / TILE_X, lx = loc - ly * TILE_X;
-            const size_t g = (size_t)(t.j0 + ly) * nx + t.i0 + lx;
+            const int ly = loc / MARCH_W, lx = loc - ly * MARCH_W;
+            const size_t g = (size_t)(t.j0 + ly) * nx + i0 + lx;
             const size_t plane = CPLX ? (size_t)(2 * arr + im) : (size_t)arr;
             // Re(w v) = w_re v_re - w_im v_im: the imaginary weight enters with a minus sign
             part += (im ? -en.w : en.w) * (double)fout[plane * N + g];
         }
         for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
-        if (lane == 0) red[warp] = part;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int q = 0; q < WARPS6; ++q) s += red[q];
-            const double c = S.gw[n - 1] * s;
+        if (lane == 0) {
+            const double c = S.gw[n - 1] * part;
             atomicAdd(S.acc, c);
             if (n > S.tail_from) atomicAdd(S.tail, c);
         }
     }
 }
 
+template <typename R, bool CPLX, int MINB>
+void launch_t(int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles, const int64_t *lb, int64_t la,
+              cudaStream_t st)
+{
+    const int grid = (ntiles + WARPS6 - 1) / WARPS6;
+    switch (variant) {
+    case 0: k_march6<R, CPLX, false, false, MINB><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 1: k_march6<R, CPLX, true, false, MINB><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 2: k_march6<R, CPLX, false, true, MINB><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    default: k_march6<R, CPLX, true, true, MINB><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    }
+}
+
 }  // namespace
 
-void launch_march6(int fp64, int cplx, const DevSim6 *sims, const DevTile *tiles, int ntiles,
+void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles,
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st)
 {
     if (ntiles <= 0) return;
     if (fp64) {
-        if (cplx) k_march6<double, true><<<ntiles, WARPS6 * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
-        else k_march6<double, false><<<ntiles, WARPS6 * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
+        if (cplx) launch_t<double, true, 1>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        else launch_t<double, false, 2>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
     } else {
-        if (cplx) k_march6<float, true><<<ntiles, WARPS6 * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
-        else k_march6<float, false><<<ntiles, WARPS6 * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
+        if (cplx) launch_t<float, true, 3>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        else launch_t<float, false, 4>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
     }
 }
 
