@@ -122,6 +122,7 @@ static int prepare_plan(casimir_plan_t *P)
     }
     // sims, tiles, entries, sources
     int64_t off = 0;
+    std::map<int, std::vector<int>> march_variants;   // per geometry: kernel variant of each march tile
     for (size_t s = 0; s < D.sims.size(); ++s) {
         const Sim &sm = D.sims[s];
         const Geo &g = D.geos[sm.geo];
@@ -206,7 +207,8 @@ static int prepare_plan(casimir_plan_t *P)
                 const char *e = std::getenv("CASIMIR_MARCH6");
                 return !(e && std::atoi(e) == 0);
             }();
-            hs.march = (D.prob.dims == 2 && g.n[2] == 1 && march_env) ? 1 : 0;
+            // (its 32-bit element offsets reach 12 N within one buffer)
+            hs.march = (D.prob.dims == 2 && g.n[2] == 1 && march_env && 12 * N < ((int64_t)1 << 32)) ? 1 : 0;
             const int nbuf = hs.march ? 2 : 1;
             hs.fhalf = 6 * cf * N;
             off += nbuf * hs.fhalf;
@@ -226,8 +228,36 @@ static int prepare_plan(casimir_plan_t *P)
             if (hs.march) {
                 // one strip tile (MARCH_W x MARCH_H) per warp, row bands outer; entries carry the
                 // component in bits 16..18 and, for the imaginary weight of complex fields, bit 19
-                hs.variant = (hs.psi_half > 0 ? 1 : 0) + (g.has_lorentz ? 2 : 0);
                 int tx = (hs.nx + MARCH_W - 1) / MARCH_W, ty = (hs.ny + MARCH_H - 1) / MARCH_H;
+                // kernel variant of each tile: the CPML and Lorentz code paths only where the tile's
+                // halo-extended box [i0-1, i0+w] x [j0-1, j0+h] holds such cells (cached per geometry)
+                auto vit = march_variants.find(sm.geo);
+                if (vit == march_variants.end()) {
+                    std::vector<char> dmat(g.nmat, 0);
+                    for (int id = 0; id < g.nmat; ++id)
+                        for (int q = 0; q < 3; ++q)
+                            if (g.has_lorentz && g.lorentz[(size_t)id * 6 + 2 * q] != 0.0) dmat[id] = 1;
+                    const int dX = g.has_pml[0] ? D.prob.pml_cells[0] : 0, dY = g.has_pml[1] ? D.prob.pml_cells[1] : 0;
+                    auto wrapc = [](int i, int n) { return ((i % n) + n) % n; };
+                    std::vector<int> vs((size_t)tx * ty, 0);
+                    for (int tj = 0; tj < ty; ++tj)
+                        for (int ti = 0; ti < tx; ++ti) {
+                            const int i0 = ti * MARCH_W, j0 = tj * MARCH_H;
+                            const int w = std::min(MARCH_W, hs.nx - i0), h = std::min(MARCH_H, hs.ny - j0);
+                            bool pml = false, lor = false;
+                            for (int jj = j0 - 1; jj <= j0 + h; ++jj) {
+                                const int j = wrapc(jj, hs.ny);
+                                if (dY > 0 && (j < dY || j >= hs.ny - dY)) pml = true;
+                                for (int ii = i0 - 1; ii <= i0 + w; ++ii) {
+                                    const int i = wrapc(ii, hs.nx);
+                                    if (dX > 0 && (i < dX || i >= hs.nx - dX)) pml = true;
+                                    if (dmat[g.mat[(size_t)j * hs.nx + i]]) lor = true;
+                                }
+                            }
+                            vs[(size_t)tj * tx + ti] = (pml ? 1 : 0) + (lor ? 2 : 0);
+                        }
+                    vit = march_variants.emplace(sm.geo, std::move(vs)).first;
+                }
                 std::vector<std::vector<DevEnt>> bucket((size_t)tx * ty);
                 for (const Entry &e : sm.meas) {
                     if (!hs.cplx && inA(e.arr) != inA(sarr)) continue;   // contributes i * real: no real part
@@ -244,7 +274,8 @@ static int prepare_plan(casimir_plan_t *P)
                 for (int tj = 0; tj < ty; ++tj)
                     for (int ti = 0; ti < tx; ++ti) {
                         auto &b = bucket[(size_t)tj * tx + ti];
-                        P->tilesM.push_back(HostTile{(int)s, ti * MARCH_W, tj * MARCH_H, (int)P->entsM.size(), (int)b.size()});
+                        P->tilesM.push_back(HostTile{(int)s, ti * MARCH_W, tj * MARCH_H, (int)P->entsM.size(), (int)b.size(),
+                                                     vit->second[(size_t)tj * tx + ti]});
                         P->entsM.insert(P->entsM.end(), b.begin(), b.end());
                     }
                 hs.nent = (int)P->entsM.size() - hs.ent0;
@@ -581,14 +612,18 @@ static int rebuild(casimir_ctx *c)
                     }
                 }
             } else if (hs.march) {
-                int gi = 4 * (2 * P->fp64 + hs.cplx) + hs.variant;
-                int idx = (int)sm6[gi].size();
+                // the simulation's descriptor goes to each variant group that holds one of its tiles
                 DevSim6 d;
                 make_sim6(P, blk, r->acc, r->tail, w.s0, s, &d);
-                sm6[gi].push_back(d);
+                int idx[4] = {-1, -1, -1, -1};
                 for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
                     const HostTile &ht = P->tilesM[t];
-                    tm6[gi].push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.entsM + ht.ent0});
+                    const int gi = 4 * (2 * P->fp64 + hs.cplx) + ht.variant;
+                    if (idx[ht.variant] < 0) {
+                        idx[ht.variant] = (int)sm6[gi].size();
+                        sm6[gi].push_back(d);
+                    }
+                    tm6[gi].push_back(DevTile{idx[ht.variant], ht.i0, ht.j0, ht.ne, P->dev.entsM + ht.ent0});
                 }
             } else {
                 int gi = 4 * P->fp64 + 2 * hs.cplx + (P->data.prob.dims == 3 ? 1 : 0);
@@ -632,23 +667,48 @@ static int rebuild(casimir_ctx *c)
     return CASIMIR_OK;
 }
 
+// One launch unit of step j (a six-component group's two phases form one unit).
+static void launch_unit(casimir_ctx *c, int gi, int j, cudaStream_t st)
+{
+    const auto &G = c->groups[gi];
+    if (gi < 2)
+        launch_step2d(gi, (const DevSim2D *)G.sims, (const DevTile *)G.tiles, G.ntiles, c->d_launch, j, st);
+    else if (gi < 10)
+        for (int phase = 0; phase < 2; ++phase)
+            launch_full(((gi - 2) >> 2) & 1, ((gi - 2) >> 1) & 1, ((gi - 2) & 1) ? 3 : 2, (const DevSim6 *)G.sims,
+                        (const DevTile6 *)G.tiles, G.ntiles, c->d_launch, j, phase, st);
+    else if (gi < 12)
+        launch_step2d_t2(gi - 10, (const DevSim2D *)c->groups[gi - 10].sims, (const DevTile2 *)G.tiles, G.ntiles,
+                         c->d_launch, j, st);
+    else
+        launch_march6(((gi - 12) >> 3) & 1, ((gi - 12) >> 2) & 1, (gi - 12) & 3, (const DevSim6 *)G.sims,
+                      (const DevTile *)G.tiles, G.ntiles, c->d_launch, j, st);
+}
+
+// Launch k consecutive steps.  The units of one step touch disjoint tiles and read only the
+// previous step's buffers, so with more than one unit they run side by side on auxiliary
+// streams (forked from and joined back into the context's stream every step), which lets one
+// unit's last partial wave overlap the next unit.
 static void launch_steps(casimir_ctx *c, int k)
 {
+    static const bool no_fork = std::getenv("CASIMIR_NO_FORK") != nullptr;
+    int units[28], nu = 0;
+    for (int gi = 0; gi < 28; ++gi)
+        if (c->groups[gi].ntiles > 0) units[nu++] = gi;
+    const bool fork = nu > 1 && !no_fork;
     for (int j = 0; j < k; ++j) {
-        for (int p = 0; p < 2; ++p) {
-            launch_step2d(p, (const DevSim2D *)c->groups[p].sims, (const DevTile *)c->groups[p].tiles,
-                          c->groups[p].ntiles, c->d_launch, j, c->stream);
-            launch_step2d_t2(p, (const DevSim2D *)c->groups[p].sims, (const DevTile2 *)c->groups[10 + p].tiles,
-                             c->groups[10 + p].ntiles, c->d_launch, j, c->stream);
+        if (!fork) {
+            for (int u = 0; u < nu; ++u) launch_unit(c, units[u], j, c->stream);
+            continue;
         }
-        for (int phase = 0; phase < 2; ++phase)
-            for (int gi = 2; gi < 10; ++gi)
-                launch_full(((gi - 2) >> 2) & 1, ((gi - 2) >> 1) & 1, ((gi - 2) & 1) ? 3 : 2, (const DevSim6 *)c->groups[gi].sims,
-                            (const DevTile6 *)c->groups[gi].tiles, c->groups[gi].ntiles, c->d_launch, j, phase,
-                            c->stream);
-        for (int gi = 12; gi < 28; ++gi)
-            launch_march6(((gi - 12) >> 3) & 1, ((gi - 12) >> 2) & 1, (gi - 12) & 3, (const DevSim6 *)c->groups[gi].sims,
-                          (const DevTile *)c->groups[gi].tiles, c->groups[gi].ntiles, c->d_launch, j, c->stream);
+        cudaEventRecord(c->ev_fork, c->stream);
+        const int na = std::min(nu, casimir_ctx::NAUX);
+        for (int a = 0; a < na; ++a) cudaStreamWaitEvent(c->aux[a], c->ev_fork, 0);
+        for (int u = 0; u < nu; ++u) launch_unit(c, units[u], j, c->aux[u % na]);
+        for (int a = 0; a < na; ++a) {
+            cudaEventRecord(c->ev_join[a], c->aux[a]);
+            cudaStreamWaitEvent(c->stream, c->ev_join[a], 0);
+        }
     }
     launch_bump(c->d_launch, k, c->stream);
 }
@@ -885,6 +945,11 @@ int casimir_ctx_create(int device, uint64_t budget, casimir_ctx_t **out)
     cudaMemcpy(c->d_launch, &c->h_launch, sizeof(int64_t), cudaMemcpyHostToDevice);
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
+    cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    for (int a = 0; a < casimir_ctx::NAUX; ++a) {
+        cudaStreamCreateWithFlags(&c->aux[a], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&c->ev_join[a], cudaEventDisableTiming);
+    }
     *out = c;
     return CASIMIR_OK;
 }
@@ -909,6 +974,11 @@ void casimir_ctx_destroy(casimir_ctx_t *c)
     cudaFree(c->d_launch);
     cudaEventDestroy(c->ev0);
     cudaEventDestroy(c->ev1);
+    cudaEventDestroy(c->ev_fork);
+    for (int a = 0; a < casimir_ctx::NAUX; ++a) {
+        cudaStreamDestroy(c->aux[a]);
+        cudaEventDestroy(c->ev_join[a]);
+    }
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }

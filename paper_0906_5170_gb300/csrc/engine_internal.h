@@ -37,7 +37,6 @@ struct HostSim {
     int second_u;
     int full;              // six-component fields
     int march;             // two-dimensional six-component run on the march kernel (ping-pong buffers)
-    int variant;           // march kernel variant: 1 = CPML, + 2 = Lorentz
     int cplx;              // complex fields (Bloch phase)
     int magnetic;
     double kzA, kzB;       // real-phase d/dz factors (two-dimensional k_z runs)
@@ -53,6 +52,7 @@ struct HostSim {
 
 struct HostTile {
     int sim, i0, j0, ent0, ne;
+    int variant = 0;       // march tiles: 1 = touches CPML, + 2 = touches dispersive cells (halo included)
 };
 
 struct HostTile2 {
@@ -186,6 +186,10 @@ struct casimir_ctx {
     int64_t step_launches = 0;
     int64_t cell_updates = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // auxiliary streams for the launch units of one step (forked and joined every step)
+    static constexpr int NAUX = 6;
+    cudaStream_t aux[NAUX] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[NAUX] = {};
     // worker
     std::mutex mu;
     std::condition_variable cv;

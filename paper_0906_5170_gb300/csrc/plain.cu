@@ -114,11 +114,14 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
     std::vector<DevSim2D> s2;
     std::vector<DevSim6> s6;
     std::vector<DevTile> t2;
+    std::vector<DevTile> tv[4];       // march tiles by kernel variant
+    int voff[5] = {0, 0, 0, 0, 0};
     std::vector<DevTile6> t6;
     std::vector<PlainEnt> pe;
     std::vector<PlainSim> ps;
     for (auto &run : runs) {
         s2.clear(); s6.clear(); t2.clear(); t6.clear(); pe.clear(); ps.clear();
+        for (auto &v : tv) v.clear();
         bool full = P->sims[run[0]].full;
         bool march = P->sims[run[0]].march;
         int cplx = P->sims[run[0]].cplx;
@@ -149,7 +152,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                 s6.push_back(d);
                 for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
                     const HostTile &ht = P->tilesM[t];
-                    t2.push_back(DevTile{idx, ht.i0, ht.j0, 0, nullptr});      // projection runs separately
+                    tv[ht.variant].push_back(DevTile{idx, ht.i0, ht.j0, 0, nullptr});   // projection runs separately
                     for (int e = ht.ent0; e < ht.ent0 + ht.ne; ++e) {
                         const DevEnt &en = P->entsM[e];
                         int loc = en.loc & 0xffff, arr = (en.loc >> 16) & 7, im = (en.loc >> 19) & 1;
@@ -179,6 +182,13 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
             }
             one.ne = (int)pe.size() - one.ent0;
             ps.push_back(one);
+        }
+        if (march) {
+            for (int v = 0; v < 4; ++v) {
+                voff[v] = (int)t2.size();
+                t2.insert(t2.end(), tv[v].begin(), tv[v].end());
+            }
+            voff[4] = (int)t2.size();
         }
         void *d_sim = nullptr, *d_tiles = nullptr, *d_pe = nullptr, *d_ps = nullptr;
         size_t bsim = align256(full ? s6.size() * sizeof(DevSim6) : s2.size() * sizeof(DevSim2D));
@@ -210,8 +220,12 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                 launch_step2d(P->fp64, (const DevSim2D *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, s);
                 ++launches;
             } else if (march) {
-                launch_march6(P->fp64, cplx, P->sims[run[0]].variant, (const DevSim6 *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, s);
-                ++launches;
+                for (int v = 0; v < 4; ++v)
+                    if (voff[v + 1] > voff[v]) {
+                        launch_march6(P->fp64, cplx, v, (const DevSim6 *)d_sim, (const DevTile *)d_tiles + voff[v],
+                                      voff[v + 1] - voff[v], d_counter, n - 1, s);
+                        ++launches;
+                    }
             } else {
                 for (int phase = 0; phase < 2; ++phase)
                     launch_full(P->fp64, cplx, D.prob.dims, (const DevSim6 *)d_sim, (const DevTile6 *)d_tiles, (int)t6.size(), d_counter, n - 1, phase, s);

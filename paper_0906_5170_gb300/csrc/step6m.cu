@@ -57,18 +57,19 @@ struct Z<R, true> {
     __device__ Z up() const { return Z(__shfl_up_sync(0xffffffffu, x, 1), __shfl_up_sync(0xffffffffu, y, 1)); }
 };
 
+// Element offsets are 32-bit: a march run's buffer holds fewer than 2^32 elements (checked by the planner).
 template <typename R, bool CPLX>
-__device__ __forceinline__ Z<R, CPLX> ld(const R *__restrict__ p, int plane, size_t N, size_t g)
+__device__ __forceinline__ Z<R, CPLX> ld(const R *__restrict__ p, int plane, unsigned N, unsigned g)
 {
-    if constexpr (CPLX) return Z<R, CPLX>(p[(size_t)(2 * plane) * N + g], p[(size_t)(2 * plane + 1) * N + g]);
-    else return Z<R, CPLX>(p[(size_t)plane * N + g]);
+    if constexpr (CPLX) return Z<R, CPLX>(p[(2u * plane) * N + g], p[(2u * plane + 1u) * N + g]);
+    else return Z<R, CPLX>(p[(unsigned)plane * N + g]);
 }
 
 template <typename R, bool CPLX>
-__device__ __forceinline__ void st(R *__restrict__ p, int plane, size_t N, size_t g, Z<R, CPLX> v)
+__device__ __forceinline__ void st(R *__restrict__ p, int plane, unsigned N, unsigned g, Z<R, CPLX> v)
 {
-    if constexpr (CPLX) { p[(size_t)(2 * plane) * N + g] = v.x; p[(size_t)(2 * plane + 1) * N + g] = v.y; }
-    else p[(size_t)plane * N + g] = v.x;
+    if constexpr (CPLX) { p[(2u * plane) * N + g] = v.x; p[(2u * plane + 1u) * N + g] = v.y; }
+    else p[(unsigned)plane * N + g] = v.x;
 }
 
 // The inputs of one row step, loaded one row ahead.  Electric sources (row j):
@@ -97,14 +98,14 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     const int64_t n = *launch_base + launch_add - S.s0;
     if (n < 1 || n > S.T) return;
     const int nx = S.n[0], ny = S.n[1];
-    const size_t N = (size_t)nx * ny;
+    const unsigned N = (unsigned)nx * (unsigned)ny;
     const int pin_par = (int)((n - 1) & 1), pout_par = (int)(n & 1);
     const R *__restrict__ fin = reinterpret_cast<const R *>(S.fields) + (size_t)pin_par * S.fhalf;
     R *__restrict__ fout = reinterpret_cast<R *>(S.fields) + (size_t)pout_par * S.fhalf;
     const R *__restrict__ coef = reinterpret_cast<const R *>(S.coef);
     const uint8_t *__restrict__ mat = S.mat;
     const int dX = PML ? S.pml_d[0] : 0, dY = PML ? S.pml_d[1] : 0;
-    const size_t PX = PML ? (size_t)S.slab[0] : 0, PY = PML ? (size_t)S.slab[1] : 0;
+    const unsigned PX = PML ? (unsigned)S.slab[0] : 0u, PY = PML ? (unsigned)S.slab[1] : 0u;
     const R *__restrict__ pxin = nullptr, *__restrict__ pyin = nullptr, *__restrict__ profy = nullptr;
     R *__restrict__ pxout = nullptr, *__restrict__ pyout = nullptr;
     if constexpr (PML) {
@@ -152,8 +153,10 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     const bool first_e = electric && n == 1;              // Lorentz start of electric sources
     auto rowp = [&](int j) { return j < 0 ? j + ny : (j >= ny ? j - ny : j); };
     auto iny = [&](int j) { return PML && dY > 0 && (j < dY || j >= ny - dY); };
-    auto gxi = [&](int j) { return (size_t)j * (2 * dX) + sx; };
-    auto gyi = [&](int j) { return (size_t)(j < dY ? j : j - (ny - 2 * dY)) * nx + col; };
+    auto gxi = [&](int j) { return (unsigned)(j * (2 * dX) + sx); };
+    auto gyi = [&](int j) { return (unsigned)((j < dY ? j : j - (ny - 2 * dY)) * nx + col); };
+    // the material's Lorentz coefficients (ce of component k nonzero: dispersive)
+    auto disp = [&](int m, int k) -> bool { if constexpr (LOR) return lc[12 * m + 4 * k + 2] != (R)0; else return false; };
 
     // d/dz of a field of the set {Ex, Ey, Hz} (A) or {Ez, Hx, Hy} (B)
     auto dzA = [&](V f) -> V { if constexpr (CPLX) return f.ik(kc); else return f * kA; };
@@ -167,21 +170,24 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     auto load_psi = [&](RowIn<R, CPLX> &in, int j, int lo, int hi) {
         if constexpr (PML) {
             if (inx) {
-                const size_t g = gxi(j);
+                const unsigned g = gxi(j);
                 for (int k = lo; k < hi; ++k) in.px[k] = ld<R, CPLX>(pxin, k, PX, g);
             }
             if (iny(j)) {
-                const size_t g = gyi(j);
+                const unsigned g = gyi(j);
                 for (int k = lo; k < hi; ++k) in.py[k] = ld<R, CPLX>(pyin, k, PY, g);
             }
         }
     };
-    auto load_lor = [&](RowIn<R, CPLX> &in, size_t g) {
+    // P of the dispersive components of material m at cell g (zero elsewhere: never read)
+    auto load_lor = [&](RowIn<R, CPLX> &in, unsigned g, int m) {
         if constexpr (LOR) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                in.p[k] = ld<R, CPLX>(lin, k, N, g);
-                in.pm[k] = ld<R, CPLX>(lin, 3 + k, N, g);
+                if (disp(m, k)) {
+                    in.p[k] = ld<R, CPLX>(lin, k, N, g);
+                    in.pm[k] = ld<R, CPLX>(lin, 3 + k, N, g);
+                }
             }
         }
     };
@@ -198,14 +204,14 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                 const R b2[3] = {xh[0], xh[1], xh[2]};
                 dxEz = str(dxEz, b2, px[2], p2);   // H_y
                 dxEy = str(dxEy, b2, px[3], p3);   // H_z
-                if (wr) { const size_t g = gxi(j); st<R, CPLX>(pxout, 2, PX, g, p2); st<R, CPLX>(pxout, 3, PX, g, p3); }
+                if (wr) { const unsigned g = gxi(j); st<R, CPLX>(pxout, 2, PX, g, p2); st<R, CPLX>(pxout, 3, PX, g, p3); }
             }
             if (iny(j)) {
                 const R pr[3] = {profy[3 * ny + j], profy[4 * ny + j], profy[5 * ny + j]};
                 V p2, p3;
                 dyEx = str(dyEx, pr, py[2], p2);   // H_z
                 dyEz = str(dyEz, pr, py[3], p3);   // H_x
-                if (wr) { const size_t g = gyi(j); st<R, CPLX>(pyout, 2, PY, g, p2); st<R, CPLX>(pyout, 3, PY, g, p3); }
+                if (wr) { const unsigned g = gyi(j); st<R, CPLX>(pyout, 2, PY, g, p2); st<R, CPLX>(pyout, 3, PY, g, p3); }
             }
         }
         const R *cm = coef + 6 * m;
@@ -215,7 +221,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     };
     // E at row j from H at rows j and j-1: new E, the E-plane psi (0, 1) and P written when wr
     auto updE = [&](int j, int m, const V hh[3], V hxp, V hzp, const V eo[3], const RowIn<R, CPLX> &in, R aa, R bb,
-                    bool wr, size_t g, V eo_new[3]) {
+                    bool wr, unsigned g, V eo_new[3]) {
         if (j - 1 < 0) { hxp = hxp.ph(byr, -byi); hzp = hzp.ph(byr, -byi); }
         V dyHz = (hh[2] - hzp) * idx, dyHx = (hh[0] - hxp) * idx;
         V dxHz = (hh[2] - left(hh[2])) * idx, dxHy = (hh[1] - left(hh[1])) * idx;
@@ -224,14 +230,14 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                 V p0, p1;
                 dxHz = str(dxHz, xe, in.px[0], p0);   // E_y
                 dxHy = str(dxHy, xe, in.px[1], p1);   // E_z
-                if (wr) { const size_t gg = gxi(j); st<R, CPLX>(pxout, 0, PX, gg, p0); st<R, CPLX>(pxout, 1, PX, gg, p1); }
+                if (wr) { const unsigned gg = gxi(j); st<R, CPLX>(pxout, 0, PX, gg, p0); st<R, CPLX>(pxout, 1, PX, gg, p1); }
             }
             if (iny(j)) {
                 const R pr[3] = {profy[j], profy[ny + j], profy[2 * ny + j]};
                 V p0, p1;
                 dyHx = str(dyHx, pr, in.py[0], p0);   // E_z
                 dyHz = str(dyHz, pr, in.py[1], p1);   // E_x
-                if (wr) { const size_t gg = gyi(j); st<R, CPLX>(pyout, 0, PY, gg, p0); st<R, CPLX>(pyout, 1, PY, gg, p1); }
+                if (wr) { const unsigned gg = gyi(j); st<R, CPLX>(pyout, 0, PY, gg, p0); st<R, CPLX>(pyout, 1, PY, gg, p1); }
             }
         }
         const V c3[3] = {dyHz - dzB(hh[1]), dzB(hh[0]) - dxHz, dxHy - dyHx};
@@ -260,10 +266,11 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     if (w > 0) {
         const int j0 = t.j0;
         const int jm = rowp(j0 - 1);
-        const size_t gm = (size_t)jm * nx + col, g0 = (size_t)j0 * nx + col;
+        const unsigned gm = (unsigned)(jm * nx + col), g0 = (unsigned)(j0 * nx + col);
         RowIn<R, CPLX> cur, nxt;
         if (electric) {
             // H (a = 1, b = h) then E (a, b_sigma).  Carried: E^n of row j, H^{n+1/2} of row j-1.
+            // The material of row j+2 is loaded at row j, so that P of row j+1 loads only where dispersive.
             V e[3], hp[3];
             {
                 RowIn<R, CPLX> in0;
@@ -274,22 +281,26 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                 load_psi(in0, jm, 2, 4);
                 updH(jm, mat[gm], em, e[0], e[2], hm, in0.px, in0.py, (R)1, hfirst, false, hp);
             }
-            auto load_row = [&](RowIn<R, CPLX> &in, int j) {
-                const size_t g = (size_t)j * nx + col, gn = (size_t)rowp(j + 1) * nx + col;
+            auto load_row = [&](RowIn<R, CPLX> &in, int j, int m) {
+                const unsigned g = (unsigned)(j * nx + col), gn = (unsigned)(rowp(j + 1) * nx + col);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     in.f[k] = ld<R, CPLX>(fin, k, N, gn);
                     in.q[k] = ld<R, CPLX>(fin, 3 + k, N, g);
                 }
-                in.m = mat[g];
-                load_lor(in, g);
+                in.m = m;
+                load_lor(in, g, m);
                 load_psi(in, j, 0, 4);
             };
-            load_row(cur, j0);
+            load_row(cur, j0, mat[g0]);
+            int m_ahead = h > 1 ? mat[g0 + nx] : 0;                 // material of the next row to load
             for (int r = 0; r < h; ++r) {
                 const int j = j0 + r;
-                const size_t g = (size_t)j * nx + col;
-                if (r + 1 < h) load_row(nxt, j + 1);
+                const unsigned g = (unsigned)(j * nx + col);
+                if (r + 1 < h) {
+                    load_row(nxt, j + 1, m_ahead);
+                    if (r + 2 < h) m_ahead = mat[g + 2 * nx];
+                }
                 V hn[3], en[3];
                 updH(j, cur.m, e, cur.f[0], cur.f[2], cur.q, cur.px, cur.py, (R)1, hfirst, own, hn);
                 updE(j, cur.m, hn, hp[0], hp[2], e, cur, a, bs, own, g, en);
@@ -310,35 +321,39 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
         } else {
             // E (a = 1, b = h) one row ahead, then H (a, b_sigma).  Carried: H^n of row j, E^{n+1} of row j.
             V hq[3], e[3];
-            int m;
+            int m = mat[g0];
             {
                 RowIn<R, CPLX> in0;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) hq[k] = ld<R, CPLX>(fin, 3 + k, N, g0);
                 const V eo[3] = {ld<R, CPLX>(fin, 0, N, g0), ld<R, CPLX>(fin, 1, N, g0), ld<R, CPLX>(fin, 2, N, g0)};
-                m = mat[g0];
-                load_lor(in0, g0);
+                load_lor(in0, g0, m);
                 load_psi(in0, j0, 0, 2);
                 updE(j0, m, hq, ld<R, CPLX>(fin, 3, N, gm), ld<R, CPLX>(fin, 5, N, gm), eo, in0, (R)1, hfirst, own, g0, e);
             }
-            auto load_row = [&](RowIn<R, CPLX> &in, int j) {
+            // inputs of row step j: row j+1 (fields, material mn, P) and the H-plane psi of row j
+            auto load_row = [&](RowIn<R, CPLX> &in, int j, int mn) {
                 const int jn = rowp(j + 1);
-                const size_t gn = (size_t)jn * nx + col;
+                const unsigned gn = (unsigned)(jn * nx + col);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     in.f[k] = ld<R, CPLX>(fin, 3 + k, N, gn);
                     in.q[k] = ld<R, CPLX>(fin, k, N, gn);
                 }
-                in.m = mat[gn];
-                load_lor(in, gn);
+                in.m = mn;
+                load_lor(in, gn, mn);
                 load_psi(in, jn, 0, 2);
                 load_psi(in, j, 2, 4);
             };
-            load_row(cur, j0);
+            load_row(cur, j0, mat[(unsigned)(rowp(j0 + 1) * nx + col)]);
+            int m_ahead = h > 1 ? mat[(unsigned)(rowp(j0 + 2) * nx + col)] : 0;   // material of row j+2
             for (int r = 0; r < h; ++r) {
                 const int j = j0 + r, jn = rowp(j + 1);
-                const size_t g = (size_t)j * nx + col, gn = (size_t)jn * nx + col;
-                if (r + 1 < h) load_row(nxt, j + 1);
+                const unsigned g = (unsigned)(j * nx + col), gn = (unsigned)(jn * nx + col);
+                if (r + 1 < h) {
+                    load_row(nxt, j + 1, m_ahead);
+                    if (r + 2 < h) m_ahead = mat[(unsigned)(rowp(j + 3) * nx + col)];
+                }
                 V en[3], hn[3];
                 // E of row j + 1: psi and P written only for rows of this strip
                 updE(jn, cur.m, cur.f, hq[0], hq[2], cur.q, cur, (R)1, hfirst, own && r + 1 < h, gn, en);
@@ -368,8 +383,8 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
             const DevEnt en = t.ents[e];
             const int loc = en.loc & 0xffff, arr = (en.loc >> 16) & 7, im = (en.loc >> 19) & 1;
             const int ly = loc / MARCH_W, lx = loc - ly * MARCH_W;
-            const size_t g = (size_t)(t.j0 + ly) * nx + i0 + lx;
-            const size_t plane = CPLX ? (size_t)(2 * arr + im) : (size_t)arr;
+            const unsigned g = (unsigned)((t.j0 + ly) * nx + i0 + lx);
+            const unsigned plane = CPLX ? (unsigned)(2 * arr + im) : (unsigned)arr;
             // Re(w v) = w_re v_re - w_im v_im: the imaginary weight enters with a minus sign
             part += (im ? -en.w : en.w) * (double)fout[plane * N + g];
         }
@@ -382,16 +397,17 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     }
 }
 
-template <typename R, bool CPLX, int MINB>
+// MINB per variant (none, CPML, Lorentz, both): resident CTAs per SM asked of the register allocator
+template <typename R, bool CPLX, int M0, int M1, int M2, int M3>
 void launch_t(int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles, const int64_t *lb, int64_t la,
               cudaStream_t st)
 {
     const int grid = (ntiles + WARPS6 - 1) / WARPS6;
     switch (variant) {
-    case 0: k_march6<R, CPLX, false, false, MINB><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    case 1: k_march6<R, CPLX, true, false, MINB><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    case 2: k_march6<R, CPLX, false, true, MINB><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    default: k_march6<R, CPLX, true, true, MINB><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 0: k_march6<R, CPLX, false, false, M0><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 1: k_march6<R, CPLX, true, false, M1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 2: k_march6<R, CPLX, false, true, M2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    default: k_march6<R, CPLX, true, true, M3><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
     }
 }
 
@@ -402,11 +418,11 @@ void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const D
 {
     if (ntiles <= 0) return;
     if (fp64) {
-        if (cplx) launch_t<double, true, 1>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
-        else launch_t<double, false, 2>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        if (cplx) launch_t<double, true, 3, 2, 2, 1>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        else launch_t<double, false, 4, 3, 3, 2>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
     } else {
-        if (cplx) launch_t<float, true, 3>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
-        else launch_t<float, false, 4>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        if (cplx) launch_t<float, true, 4, 3, 3, 3>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        else launch_t<float, false, 6, 4, 5, 4>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
     }
 }
 
