@@ -421,7 +421,7 @@ void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const D
         if (cplx) launch_t<double, true, 3, 2, 2, 1>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
         else launch_t<double, false, 4, 3, 3, 2>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
     } else {
-        if (cplx) launch_t<float, true, 4, 3, 3, 3>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        if (cplx) launch_t<float, true, 4, 4, 3, 3>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
         else launch_t<float, false, 6, 4, 5, 4>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
     }
 }
