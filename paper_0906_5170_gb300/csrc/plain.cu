@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <tuple>
 #include <vector>
 
@@ -51,6 +52,10 @@ __global__ void k_project(const R *base, const PlainSim *sims, const PlainEnt *a
         *acc += gw[n - 1] * s;
     }
 }
+
+// strip tiles a run needs before the plain path takes the march kernel for it: four CTAs of four
+// warps on each of the 152 SMs
+constexpr int64_t kPlainMarchTiles = 4 * 4 * 152;
 
 struct Free {
     casimir_ctx *c;
@@ -123,12 +128,24 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
         s2.clear(); s6.clear(); t2.clear(); t6.clear(); pe.clear(); ps.clear();
         for (auto &v : tv) v.clear();
         bool full = P->sims[run[0]].full;
+        // A two-dimensional six-component run uses the march kernel only when its strip tiles can
+        // fill the GPU; a small run alone is latency-bound there (each warp walks its rows in
+        // sequence) and goes faster through the one-thread-per-cell kernel, in place on buffer 0.
         bool march = P->sims[run[0]].march;
+        if (march) {
+            int64_t nt = 0;
+            for (size_t q : run) nt += P->sims[q].ntile;
+            static const int64_t thr = [] {
+                const char *e = std::getenv("CASIMIR_PLAIN_MARCH_TILES");
+                return e ? (int64_t)std::atoll(e) : kPlainMarchTiles;
+            }();
+            march = nt >= thr;
+        }
         int cplx = P->sims[run[0]].cplx;
         for (size_t q : run) {
             const HostSim &hs = P->sims[q];
             int64_t N = (int64_t)hs.nx * hs.ny * hs.nz;
-            PlainSim one{hs.full ? (hs.march ? hs.fhalf : 0) : 3 * N, (int)pe.size(), 0, acc + q};
+            PlainSim one{hs.full ? (march ? hs.fhalf : 0) : 3 * N, (int)pe.size(), 0, acc + q};
             if (!hs.full) {
                 DevSim2D d;
                 make_sim2d(P, b, acc, tail, 0, q, &d);
@@ -143,6 +160,25 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                         int ly = loc / TILE_X, lx = loc - ly * TILE_X;
                         int64_t g = (int64_t)arr * N + (int64_t)(ht.j0 + ly) * hs.nx + ht.i0 + lx;
                         pe.push_back(PlainEnt{hs.field_off + g, -1, en.w, 0.0});
+                    }
+                }
+            } else if (hs.march && !march) {
+                // march layout run through the two-phase kernel: buffer 0 only, whole-cell tiles
+                DevSim6 d;
+                make_sim6(P, b, acc, tail, 0, q, &d);
+                int idx = (int)s6.size();
+                s6.push_back(d);
+                for (int64_t c0 = 0; c0 < N; c0 += TILE6)
+                    t6.push_back(DevTile6{idx, (int)std::min<int64_t>(TILE6, N - c0), c0, 0, 0, nullptr});
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile &ht = P->tilesM[t];
+                    for (int e = ht.ent0; e < ht.ent0 + ht.ne; ++e) {
+                        const DevEnt &en = P->entsM[e];
+                        int loc = en.loc & 0xffff, arr = (en.loc >> 16) & 7, im = (en.loc >> 19) & 1;
+                        int ly = loc / MARCH_W, lx = loc - ly * MARCH_W;
+                        int64_t plane = hs.cplx ? 2 * arr + im : arr;
+                        int64_t g = plane * N + (int64_t)(ht.j0 + ly) * hs.nx + ht.i0 + lx;
+                        pe.push_back(PlainEnt{hs.field_off + g, -1, im ? -en.w : en.w, 0.0});
                     }
                 }
             } else if (hs.march) {

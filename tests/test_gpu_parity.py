@@ -293,3 +293,31 @@ def test_tiny_grids_six_component(ctx, nx, ny, kind):
     Fb, pb, _ = ctx.plan(p).run(per_sim=True)
     Fp, pp, _ = ctx.plan(p).run(per_sim=True, plain=True)
     assert np.allclose(pp, pb, rtol=1e-9, atol=1e-13 * np.sum(np.abs(pb)))
+
+
+def test_plain_path_march_kernel_in_subprocess():
+    # the plain path runs large two-dimensional six-component runs through the march kernel and
+    # small ones through the two-phase kernel; force the march kernel here and compare with the
+    # batched results of the same plan
+    import os, subprocess, sys, json
+    code = r'''
+import json, sys
+import numpy as np
+sys.path.insert(0, ".")
+import workloads as W
+import paper_0906_5170_gb300 as pk
+p = W.config3_waveguides(0.5, resolution=8, n_cells=48, pml_units=0.75, n_harm=3, n_steps=300,
+                         k_points=[{"k": [0, 0, k], "weight": 0.3} for k in (0.0, 2.5)], precision="fp64")
+ctx = pk.Context(0)
+_, pb, _ = ctx.plan(p).run(per_sim=True)
+_, pp, st = ctx.plan(p).run(per_sim=True, plain=True)
+print(json.dumps({"ok": bool(np.allclose(pp, pb, rtol=1e-9, atol=1e-13 * np.sum(np.abs(pb)))),
+                  "launches": st["kernel_launches"]}))
+ctx.close()
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CASIMIR_PLAIN_MARCH_TILES="0")
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    assert res["ok"]
