@@ -280,7 +280,37 @@ static int prepare_plan(casimir_plan_t *P)
                     }
                 hs.nent = (int)P->entsM.size() - hs.ent0;
             }
-            if (!hs.march) {
+            static const bool line3_env = [] {
+                const char *e = std::getenv("CASIMIR_LINE3");
+                return !(e && std::atoi(e) == 0);
+            }();
+            hs.line3 = (!hs.march && D.prob.dims == 3 && line3_env && 12 * N < ((int64_t)1 << 32)) ? 1 : 0;
+            if (hs.line3) {
+                // tiles of 32 x cells by LINES3 (y, z) lines; entries bucketed per tile
+                const int64_t nl = (int64_t)hs.ny * hs.nz;
+                const int tx = (hs.nx + 31) / 32, tl = (int)((nl + LINES3 - 1) / LINES3);
+                std::vector<std::vector<DevEnt>> bucket((size_t)tx * tl);
+                for (const Entry &e : sm.meas) {
+                    const int64_t line = e.idx / hs.nx;
+                    const int i = (int)(e.idx - line * hs.nx);
+                    const int ti = i / 32, tj = (int)(line / LINES3);
+                    const int loc = (int)(line - (int64_t)tj * LINES3) * 32 + (i - ti * 32);
+                    auto &b = bucket[(size_t)tj * tx + ti];
+                    if (e.re != 0.0 || !hs.cplx) b.push_back(DevEnt{loc | (e.arr << 16), 0, e.re});
+                    if (hs.cplx && e.im != 0.0) b.push_back(DevEnt{loc | ((e.arr | 8) << 16), 0, e.im});
+                }
+                hs.tile0 = (int)P->tilesM.size();
+                hs.ntile = tx * tl;
+                hs.ent0 = (int)P->entsM.size();
+                for (int tj = 0; tj < tl; ++tj)
+                    for (int ti = 0; ti < tx; ++ti) {
+                        auto &b = bucket[(size_t)tj * tx + ti];
+                        P->tilesM.push_back(HostTile{(int)s, ti * 32, tj * LINES3, (int)P->entsM.size(), (int)b.size(), 0});
+                        P->entsM.insert(P->entsM.end(), b.begin(), b.end());
+                    }
+                hs.nent = (int)P->entsM.size() - hs.ent0;
+            }
+            if (!hs.march && !hs.line3) {
                 int ntile = (int)((N + TILE6 - 1) / TILE6);
                 hs.tile0 = (int)P->tiles6.size();
                 hs.ntile = ntile;
@@ -586,6 +616,8 @@ static int rebuild(casimir_ctx *c)
     std::vector<DevTile6> t6[8];
     std::vector<DevSim6> sm6[16];
     std::vector<DevTile> tm6[16];
+    std::vector<DevSim6> sl3[4];
+    std::vector<DevTile> tl3[4];
     for (auto &aw : c->active_waves) {
         casimir_request *r = aw.first;
         const casimir_request::Wave &w = r->waves[aw.second];
@@ -610,6 +642,16 @@ static int rebuild(casimir_ctx *c)
                         const HostTile &ht = P->tiles[t];
                         tv.push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.ents + ht.ent0});
                     }
+                }
+            } else if (hs.line3) {
+                const int gi = 2 * P->fp64 + hs.cplx;
+                DevSim6 d;
+                make_sim6(P, blk, r->acc, r->tail, w.s0, s, &d);
+                const int idx = (int)sl3[gi].size();
+                sl3[gi].push_back(d);
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile &ht = P->tilesM[t];
+                    tl3[gi].push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.entsM + ht.ent0});
                 }
             } else if (hs.march) {
                 // the simulation's descriptor goes to each variant group that holds one of its tiles
@@ -641,14 +683,15 @@ static int rebuild(casimir_ctx *c)
         }
     }
     c->ntiles = 0;
-    for (int gi = 0; gi < 28; ++gi) {
+    for (int gi = 0; gi < casimir_ctx::NGROUPS; ++gi) {
         auto &G = c->groups[gi];
         size_t ns, nt, ss, ts;
         const void *sp, *tp;
         if (gi < 2) { ns = s2[gi].size(); nt = t2[gi].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile); sp = s2[gi].data(); tp = t2[gi].data(); }
         else if (gi < 10) { ns = s6[gi - 2].size(); nt = t6[gi - 2].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile6); sp = s6[gi - 2].data(); tp = t6[gi - 2].data(); }
         else if (gi < 12) { ns = 0; nt = tt[gi - 10].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile2); sp = nullptr; tp = tt[gi - 10].data(); }
-        else { ns = sm6[gi - 12].size(); nt = tm6[gi - 12].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sm6[gi - 12].data(); tp = tm6[gi - 12].data(); }
+        else if (gi < 28) { ns = sm6[gi - 12].size(); nt = tm6[gi - 12].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sm6[gi - 12].data(); tp = tm6[gi - 12].data(); }
+        else { ns = sl3[gi - 28].size(); nt = tl3[gi - 28].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sl3[gi - 28].data(); tp = tl3[gi - 28].data(); }
         int rc = grow(c, &G.sims, &G.sims_cap, ns * ss);
         if (rc) return rc;
         rc = grow(c, &G.tiles, &G.tiles_cap, nt * ts);
@@ -680,9 +723,13 @@ static void launch_unit(casimir_ctx *c, int gi, int j, cudaStream_t st)
     else if (gi < 12)
         launch_step2d_t2(gi - 10, (const DevSim2D *)c->groups[gi - 10].sims, (const DevTile2 *)G.tiles, G.ntiles,
                          c->d_launch, j, st);
-    else
+    else if (gi < 28)
         launch_march6(((gi - 12) >> 3) & 1, ((gi - 12) >> 2) & 1, (gi - 12) & 3, (const DevSim6 *)G.sims,
                       (const DevTile *)G.tiles, G.ntiles, c->d_launch, j, st);
+    else
+        for (int phase = 0; phase < 2; ++phase)
+            launch_line3(((gi - 28) >> 1) & 1, (gi - 28) & 1, (const DevSim6 *)G.sims, (const DevTile *)G.tiles, G.ntiles,
+                         c->d_launch, j, phase, st);
 }
 
 // Launch k consecutive steps.  The units of one step touch disjoint tiles and read only the
@@ -692,8 +739,8 @@ static void launch_unit(casimir_ctx *c, int gi, int j, cudaStream_t st)
 static void launch_steps(casimir_ctx *c, int k)
 {
     static const bool no_fork = std::getenv("CASIMIR_NO_FORK") != nullptr;
-    int units[28], nu = 0;
-    for (int gi = 0; gi < 28; ++gi)
+    int units[casimir_ctx::NGROUPS], nu = 0;
+    for (int gi = 0; gi < casimir_ctx::NGROUPS; ++gi)
         if (c->groups[gi].ntiles > 0) units[nu++] = gi;
     const bool fork = nu > 1 && !no_fork;
     for (int j = 0; j < k; ++j) {
@@ -745,8 +792,8 @@ static int run_chunk(casimir_ctx *c, int k)
     }
     c->h_launch += k;
     int per_step = 0;
-    for (int gi = 0; gi < 28; ++gi)
-        if (c->groups[gi].ntiles > 0) per_step += (gi >= 2 && gi < 10) ? 2 : 1;
+    for (int gi = 0; gi < casimir_ctx::NGROUPS; ++gi)
+        if (c->groups[gi].ntiles > 0) per_step += ((gi >= 2 && gi < 10) || gi >= 28) ? 2 : 1;
     for (casimir_request *r : c->active) r->launches += (int64_t)k * per_step + 1;
     return CASIMIR_OK;
 }

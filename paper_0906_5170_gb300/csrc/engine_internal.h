@@ -37,6 +37,7 @@ struct HostSim {
     int second_u;
     int full;              // six-component fields
     int march;             // two-dimensional six-component run on the march kernel (ping-pong buffers)
+    int line3;             // three-dimensional run on the x-line kernel (tiles in tilesM)
     int cplx;              // complex fields (Bloch phase)
     int magnetic;
     double kzA, kzB;       // real-phase d/dz factors (two-dimensional k_z runs)
@@ -166,12 +167,14 @@ struct casimir_ctx {
     std::vector<casimir_request *> active;
     // launch groups: [0, 1] the 2D kernel in FP32 / FP64; [2 + 4*fp64 + 2*cplx + (dims == 3)]
     // the six-component kernel; [10, 11] the two-step 2D kernel in FP32 / FP64;
-    // [12 + 4 * (2*fp64 + cplx) + variant] the six-component march kernel of two-dimensional runs
+    // [12 + 4 * (2*fp64 + cplx) + variant] the six-component march kernel of two-dimensional runs;
+    // [28 + 2*fp64 + cplx] the x-line kernel of three-dimensional runs
+    static constexpr int NGROUPS = 32;
     struct Group {
         void *sims = nullptr, *tiles = nullptr;
         size_t sims_cap = 0, tiles_cap = 0;
         int ntiles = 0;
-    } groups[28];
+    } groups[NGROUPS];
     int ntiles = 0;                   // over all groups
     // waves: simulations are activated in groups whose field bytes fit `wave_bytes`
     // (0: a whole request at once), so that the active working set can stay in L2

@@ -114,6 +114,14 @@ void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const D
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 void launch_inject6(int fp64, void *fields, const DevSrc6 *src, int nsrc, cudaStream_t st);
 
+// Six-component half step of three-dimensional runs by x lines: a tile is 32 x cells (i0) of
+// LINES3 consecutive (y, z) lines from line j0 (line = z * ny + y), one warp per line at a time,
+// in place (one buffer).  Tile entries: DevEnt with loc = (line - j0) * 32 + (x - i0) in bits
+// 0..15, the component in bits 16..18, bit 19 for the weight of the imaginary part.
+constexpr int LINES3 = 64;
+void launch_line3(int fp64, int cplx, const DevSim6 *sims, const DevTile *tiles, int ntiles,
+                  const int64_t *launch_base, int64_t launch_add, int phase, cudaStream_t st);
+
 // Two-step tiles of the 2D kernel: four warp strips of 28 interior columns; the
 // tile's pixel entries sorted by row, with rowptr[ly] .. rowptr[ly+1] per row.
 constexpr int TILE_X2 = 112;

@@ -132,6 +132,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
         // fill the GPU; a small run alone is latency-bound there (each warp walks its rows in
         // sequence) and goes faster through the one-thread-per-cell kernel, in place on buffer 0.
         bool march = P->sims[run[0]].march;
+        const bool line3 = P->sims[run[0]].line3;
         if (march) {
             int64_t nt = 0;
             for (size_t q : run) nt += P->sims[q].ntile;
@@ -160,6 +161,22 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                         int ly = loc / TILE_X, lx = loc - ly * TILE_X;
                         int64_t g = (int64_t)arr * N + (int64_t)(ht.j0 + ly) * hs.nx + ht.i0 + lx;
                         pe.push_back(PlainEnt{hs.field_off + g, -1, en.w, 0.0});
+                    }
+                }
+            } else if (hs.line3) {
+                DevSim6 d;
+                make_sim6(P, b, acc, tail, 0, q, &d);
+                int idx = (int)s6.size();
+                s6.push_back(d);
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile &ht = P->tilesM[t];
+                    t2.push_back(DevTile{idx, ht.i0, ht.j0, 0, nullptr});      // projection runs separately
+                    for (int e = ht.ent0; e < ht.ent0 + ht.ne; ++e) {
+                        const DevEnt &en = P->entsM[e];
+                        int loc = en.loc & 0xffff, arr = (en.loc >> 16) & 7, im = (en.loc >> 19) & 1;
+                        int64_t plane = hs.cplx ? 2 * arr + im : arr;
+                        int64_t g = plane * N + (int64_t)(ht.j0 + (loc >> 5)) * hs.nx + ht.i0 + (loc & 31);
+                        pe.push_back(PlainEnt{hs.field_off + g, -1, im ? -en.w : en.w, 0.0});
                     }
                 }
             } else if (hs.march && !march) {
@@ -228,7 +245,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
         }
         void *d_sim = nullptr, *d_tiles = nullptr, *d_pe = nullptr, *d_ps = nullptr;
         size_t bsim = align256(full ? s6.size() * sizeof(DevSim6) : s2.size() * sizeof(DevSim2D));
-        size_t btil = align256(full && !march ? t6.size() * sizeof(DevTile6) : t2.size() * sizeof(DevTile));
+        size_t btil = align256(full && !march && !line3 ? t6.size() * sizeof(DevTile6) : t2.size() * sizeof(DevTile));
         size_t bpe = align256(std::max<size_t>(1, pe.size()) * sizeof(PlainEnt));
         size_t bps = align256(ps.size() * sizeof(PlainSim));
         void *rb = nullptr;
@@ -241,7 +258,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
         d_ps = (char *)rb + bsim + btil + bpe;
         if (full) {
             CUDA_TRY(cudaMemcpyAsync(d_sim, s6.data(), s6.size() * sizeof(DevSim6), cudaMemcpyHostToDevice, s));
-            if (march)
+            if (march || line3)
                 CUDA_TRY(cudaMemcpyAsync(d_tiles, t2.data(), t2.size() * sizeof(DevTile), cudaMemcpyHostToDevice, s));
             else
                 CUDA_TRY(cudaMemcpyAsync(d_tiles, t6.data(), t6.size() * sizeof(DevTile6), cudaMemcpyHostToDevice, s));
@@ -255,6 +272,10 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
             if (!full) {
                 launch_step2d(P->fp64, (const DevSim2D *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, s);
                 ++launches;
+            } else if (line3) {
+                for (int phase = 0; phase < 2; ++phase)
+                    launch_line3(P->fp64, cplx, (const DevSim6 *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, phase, s);
+                launches += 2;
             } else if (march) {
                 for (int v = 0; v < 4; ++v)
                     if (voff[v + 1] > voff[v]) {
