@@ -192,6 +192,36 @@ def measure_configs(pk, ctx, peak):
     return out
 
 
+def measure_basis(pk, ctx):
+    """Point-source basis against the cosine basis of Eq. 7 on one config-2 geometry (4000 steps):
+    simulations, GPU time and the force; the truncated cosine series converges to the complete
+    basis, which equals the point basis exactly (Sec. III A)."""
+    import workloads as W
+    base = W.config2_piston(W.config2_heights()[3], n_steps=4000)
+    fa = base["force_axis"]
+
+    def one(p):
+        pl = ctx.plan(p)
+        pl.run()                              # tables uploaded, graphs built
+        ctx.kernel_stats(reset=True)
+        t0 = time.perf_counter()
+        F, _, _ = pl.run()
+        wall = time.perf_counter() - t0
+        ms, _, cu = ctx.kernel_stats(reset=True)
+        n = pl.info()["n_sims"]
+        pl.close()
+        return F[fa], n, wall, ms
+
+    Fp, n_p, w_p, ms_p = one(dict(base, basis="point"))
+    out = {"workload": "config-2 geometry h = 1.225 (400 x 138), TE + TM, 4000 steps, FP32 fields",
+           "point": {"sims": n_p, "wall_s": w_p, "kernel_ms": ms_p, "force": Fp}, "cosine": []}
+    for k in (5, 10, 20, 40):
+        F, n, w, ms = one(dict(base, n_harm=k))
+        out["cosine"].append({"n_harm": k, "sims": n, "wall_s": w, "kernel_ms": ms, "force": F,
+                              "rel_diff_to_point": abs(F - Fp) / abs(Fp)})
+    return out
+
+
 def cpu_baseline(budget_s=15.0):
     """The FP64 oracle on a bounded sample of the workload: simulations of the
     h = 0.5 geometry for a shortened number of steps, one per host core."""
@@ -402,6 +432,7 @@ def main():
     others = None
     if not args.no_configs:
         others = measure_configs(pk, ctx, peaks()[0])
+        others["basis_point_vs_cosine"] = measure_basis(pk, ctx)
 
     cb = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -321,3 +321,17 @@ ctx.close()
     assert out.returncode == 0, out.stderr[-2000:]
     res = json.loads(out.stdout.strip().splitlines()[-1])
     assert res["ok"]
+
+
+def test_complete_cosine_basis_equals_point_basis_on_gpu(ctx):
+    # completeness of the face basis (Sec. III A, Eq. 7): with every harmonic of every face the
+    # cosine-basis force equals the point-source force, on the GPU path alone (no oracle)
+    p = W.piston_small(n_steps=400, precision="fp64")
+    F_cos, per_cos, _ = ctx.plan(dict(p, n_harm=100000)).run(per_sim=True)
+    F_pt, per_pt, _ = ctx.plan(dict(p, basis="point")).run(per_sim=True)
+    fa = p["force_axis"]
+    scale = max(np.sum(np.abs(per_cos)), np.sum(np.abs(per_pt)))
+    assert abs(F_cos[fa] - F_pt[fa]) <= 1e-10 * scale
+    # a truncated cosine basis differs, and the difference shrinks with the harmonic count
+    errs = [abs(ctx.plan(dict(p, n_harm=k)).run()[0][fa] - F_pt[fa]) for k in (2, 4, 8)]
+    assert errs[0] > errs[1] > errs[2] > 1e-10 * scale
