@@ -59,6 +59,7 @@ class _OgGrid(ctypes.Structure):
         ("bloch_re", ctypes.c_double * 3), ("bloch_im", ctypes.c_double * 3),
         ("ce", DP * 3), ("ch", DP * 3), ("lde", DP * 3), ("lw0", DP * 3),
         ("pb", (DP * 2) * 3), ("pc", (DP * 2) * 3), ("pk", (DP * 2) * 3),
+        ("cyl", ctypes.c_int), ("mphi", ctypes.c_double),
     ]
 
 
@@ -243,15 +244,32 @@ def _pml_profile(n, cells, res, dt, half):
     return b, c, 1.0 / kap
 
 
+def is_cyl(problem):
+    """Cylindrical (r, z) cross-section with fields ~ exp(i m phi) (Sec. III C)."""
+    return problem.get("coords", "cartesian") == "cylindrical"
+
+
+def cyl_site_weight(problem, off_r, i):
+    """Volume weight of a cylindrical Yee site (the ring volume over 2 pi Delta^2, in units of
+    length): its radius r = (i + off_r) Delta, and Delta/8 on the axis (the disk of radius
+    Delta/2 around it) -- the weights that make the discrete curl self-adjoint."""
+    d = 1.0 / problem["resolution"]
+    r = (i + off_r) * d
+    return r if r > 0.5 * _TOL * d else d / 8.0
+
+
 class _Setup:
     """Per-(problem, k-point) lattice arrays kept alive for the C core."""
 
-    def __init__(self, problem, kvec):
+    def __init__(self, problem, kvec, m=0):
         self.problem = problem
         dims = problem["dims"]
         nx, ny, nz = problem["n"]
         if dims == 2 and nz != 1:
             raise ValueError("two-dimensional problems have nz == 1")
+        cyl = is_cyl(problem)
+        if cyl and (dims != 2 or problem["bc"][0] != "pec" or "pml" in problem["bc"]):
+            raise ValueError("cylindrical problems are (r, z) cross-sections with a PEC wall at r = R, no PML")
         res = problem["resolution"]
         d = 1.0 / res
         dt = problem["courant"] * d
@@ -262,8 +280,11 @@ class _Setup:
         g.twod = 1 if dims == 2 else 0
         for c in range(3):
             g.eact[c] = g.hact[c] = 1
-        g.kz = float(kvec[2]) if dims == 2 else 0.0
+        g.kz = float(kvec[2]) if dims == 2 and not cyl else 0.0
         g.dx, g.dt, g.sigma = d, dt, float(problem["sigma"])
+        g.cyl = 1 if cyl else 0
+        g.mphi = float(m) if cyl else 0.0
+        self.cyl, self.m = cyl, (int(m) if cyl else 0)
         self.bloch = []
         for a in range(3):
             ph = 1.0 + 0.0j
@@ -277,14 +298,22 @@ class _Setup:
             eps, mu, pec, pmc, lde, lw0 = _materials(problem, pts)
             wall = np.zeros(self.N, dtype=bool)
             for a in range(dims):
+                if cyl and a == 0:
+                    continue        # r = 0 is the axis, not a wall (the wall r = R lies beyond the grid)
                 if problem["bc"][a] in ("pec", "pml") and E_OFF[c][a] == 0.0:
                     wall |= np.abs(pts[a]) < _TOL * d
+            if cyl:
+                axis = np.abs(pts[0]) < _TOL * d
+                if c == 2 or (c == 1 and m != 0):
+                    wall |= axis      # E_phi(0) carries no weight; E_z ~ r^|m| vanishes there for m != 0
             ce = np.where(pec | wall, 0.0, 1.0 / eps)
             self.ce.append(np.ascontiguousarray(ce))
             lde_all.append(np.ascontiguousarray(np.where(pec | wall, 0.0, lde)))
             lw0_all.append(np.ascontiguousarray(lw0))
             pts = _site_coords(problem, H_OFF[c])
             eps, mu, pec, pmc, lde, lw0 = _materials(problem, pts)
+            if cyl and c == 0:
+                pmc = pmc | (np.abs(pts[0]) < _TOL * d)   # H_r(0) carries no weight
             self.ch.append(np.ascontiguousarray(np.where(pmc, 0.0, 1.0 / mu)))
         for c in range(3):
             g.ce[c] = _dp(self.ce[c])
@@ -304,7 +333,7 @@ class _Setup:
                     g.pc[a][half] = _dp(cc)
                     g.pk[a][half] = _dp(ik)
         self.grid = g
-        self.real = (g.kz == 0.0) and all(abs(ph.imag) == 0.0 for ph in self.bloch)
+        self.real = (g.kz == 0.0) and all(abs(ph.imag) == 0.0 for ph in self.bloch) and self.m == 0
         self.dt = dt
         self.d = d
         self.kvec = kvec
@@ -374,6 +403,10 @@ def interp_weights(problem, setup, point, off):
         out = []
         for i, w in ent:
             q = i // n
+            if a == 0 and is_cyl(problem):
+                if q == 0:
+                    out.append((i, w))      # no wrap in r: beyond r = R the tangential E vanishes
+                continue
             out.append((i - q * n, w * setup.bloch[a] ** q))
         per_axis.append(out)
     nx, ny, _ = problem["n"]
@@ -440,11 +473,16 @@ def _sim_vectors(problem, setup, sim):
     c = sim["comp"]
     magnetic = sim["kind"] == "K"
     offs = H_OFF if magnetic else E_OFF
-    # source: D_c(p) = -(dA/dV) sum_k conj(W_c(k,p)) f(x_k)
+    # source: D_c(p) = -(dA/dV) sum_k conj(W_c(k,p)) f(x_k); in cylindrical coordinates the
+    # surface current f e^{i m phi} on the surface of revolution, averaged over the ring of the
+    # site, carries r(x_k) / w(p) (ring area over ring volume)
+    cyl = is_cyl(problem)
+    nx = problem["n"][0]
     src = {}
     for k in range(centres.shape[0]):
         for idx, w in interp_weights(problem, setup, centres[k], offs[c]):
-            src[idx] = src.get(idx, 0.0) - np.conj(w) * f[k] / d
+            scale = centres[k][0] / cyl_site_weight(problem, offs[c][0], idx % nx) if cyl else 1.0
+            src[idx] = src.get(idx, 0.0) - np.conj(w) * f[k] * scale / d
     # measurement: s_i = sum_k dA w_S f(x_k) [n_c F_i(x_k) - 1/2 n_i F_c(x_k)]
     i = problem["force_axis"]
     a = face["axis"]
@@ -465,7 +503,7 @@ def _sim_vectors(problem, setup, sim):
 
 
 def _setups(problem):
-    return [_Setup(problem, kp["k"]) for kp in problem["k_points"]]
+    return [_Setup(problem, kp["k"], kp.get("m", 0)) for kp in problem["k_points"]]
 
 
 def run_vectors(problem, setup, magnetic, src, meas, pol="full"):
@@ -479,7 +517,8 @@ def run_vectors(problem, setup, magnetic, src, meas, pol="full"):
 def run_sim(problem, sim, setup=None):
     """Run one sim; return the complex series s(n), n = 1..T."""
     if setup is None:
-        setup = _Setup(problem, problem["k_points"][sim["k"]]["k"])
+        kp = problem["k_points"][sim["k"]]
+        setup = _Setup(problem, kp["k"], kp.get("m", 0))
     src, meas = _sim_vectors(problem, setup, sim)
     src = {(sim["comp"], k): v for k, v in src.items()}
     return _run(problem, setup, sim, src, meas)
@@ -546,8 +585,8 @@ def force(problem, sims=None, threads=None, return_parts=False):
     return F
 
 
-def grid_setup(problem, kvec=(0.0, 0.0, 0.0)):
-    return _Setup(problem, list(kvec))
+def grid_setup(problem, kvec=(0.0, 0.0, 0.0), m=0):
+    return _Setup(problem, list(kvec), m)
 
 
 def evolve(problem, E0, H0, nsteps, kvec=(0.0, 0.0, 0.0), setup=None):

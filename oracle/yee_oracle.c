@@ -62,6 +62,11 @@ typedef struct {
     const double *lw0[3]; /* Lorentz omega_0 at E_c sites */
     /* CPML along axis a, per site index along that axis, [0] integer sites, [1] half sites */
     const double *pb[3][2], *pc[3][2], *pk[3][2];
+    /* Cylindrical (r, z) cross-section with fields ~ exp(i m phi) (Sec. III C and the appendix on
+     * cylindrical coordinates): axis 0 is r (r = 0 at i = 0, PEC wall at r = n[0] Delta), axis 1
+     * is z; components 0, 1, 2 are (r, z, phi) on the sites of (x, y, z) above. */
+    int cyl;
+    double mphi;
 } og_grid;
 
 typedef struct {
@@ -153,6 +158,69 @@ static void curl_h(const og_grid *g, cx *const H[3], cx *out[3], cx *psi[3][3])
             }
 }
 
+/* Cylindrical curls.  With F ~ exp(i m phi):
+ *   (curl F)_r   = (i m / r) F_z - dF_phi/dz
+ *   (curl F)_phi = dF_r/dz - dF_z/dr
+ *   (curl F)_z   = (1/r) d(r F_phi)/dr - (i m / r) F_r
+ * Sites: E_r, H_z, H_phi at r = (i + 1/2) Delta; E_z, E_phi, H_r at r = i Delta.  Across the
+ * outer wall (i + 1 = n[0]) E vanishes; inside the axis (i - 1 < 0) H is taken as zero.  On
+ * the axis the z component follows Stokes over the disk of radius Delta/2:
+ * (curl H)_z(0) = (Delta/2) H_phi(Delta/2) / ((Delta/8) Delta) = 4 H_phi(Delta/2) / Delta, the weight
+ * of the axis site being the disk area over 2 pi Delta.
+ * E_phi(0) and H_r(0) carry no weight (r = 0) and are masked by the caller, as is E_z(0) for
+ * m != 0 (E_z ~ r^|m| near the axis). */
+static cx zwrap(const og_grid *g, const cx *F, int i, int j, int dir)
+{
+    int jj = j + dir;
+    cx ph = 1.0;
+    if (jj == g->n[1]) { jj = 0; ph = g->bloch_re[1] + CI * g->bloch_im[1]; }
+    if (jj < 0) { jj = g->n[1] - 1; ph = g->bloch_re[1] - CI * g->bloch_im[1]; }
+    return ph * F[jj * g->n[0] + i];
+}
+
+static void curl_e_cyl(const og_grid *g, cx *const E[3], cx *out[3])
+{
+    int nr = g->n[0], nz = g->n[1];
+    double d = g->dx;
+    cx im = CI * g->mphi;
+    for (int j = 0; j < nz; ++j)
+        for (int i = 0; i < nr; ++i) {
+            int m = j * nr + i;
+            double ri = i * d, rh = (i + 0.5) * d, rp = (i + 1) * d;
+            cx ephi_r = i + 1 < nr ? E[2][m + 1] : 0.0;     /* E_phi at r_{i+1} */
+            cx ez_r = i + 1 < nr ? E[1][m + 1] : 0.0;       /* E_z at r_{i+1} */
+            /* H_r at (r_i, z_{j+1/2}) */
+            out[0][m] = (i > 0 ? im / ri * E[1][m] : 0.0) - (zwrap(g, E[2], i, j, 1) - E[2][m]) / d;
+            /* H_z at (r_{i+1/2}, z_j) */
+            out[1][m] = (rp * ephi_r - ri * E[2][m]) / (rh * d) - im / rh * E[0][m];
+            /* H_phi at (r_{i+1/2}, z_{j+1/2}) */
+            out[2][m] = (zwrap(g, E[0], i, j, 1) - E[0][m]) / d - (ez_r - E[1][m]) / d;
+        }
+}
+
+static void curl_h_cyl(const og_grid *g, cx *const H[3], cx *out[3])
+{
+    int nr = g->n[0], nz = g->n[1];
+    double d = g->dx;
+    cx im = CI * g->mphi;
+    for (int j = 0; j < nz; ++j)
+        for (int i = 0; i < nr; ++i) {
+            int m = j * nr + i;
+            double ri = i * d, rh = (i + 0.5) * d, rl = (i - 0.5) * d;
+            cx hphi_l = i > 0 ? H[2][m - 1] : 0.0;          /* H_phi at r_{i-1/2} */
+            cx hz_l = i > 0 ? H[1][m - 1] : 0.0;            /* H_z at r_{i-1/2} */
+            /* E_r at (r_{i+1/2}, z_j) */
+            out[0][m] = im / rh * H[1][m] - (H[2][m] - zwrap(g, H[2], i, j, -1)) / d;
+            /* E_z at (r_i, z_{j+1/2}) */
+            if (i > 0)
+                out[1][m] = (rh * H[2][m] - rl * hphi_l) / (ri * d) - im / ri * H[0][m];
+            else
+                out[1][m] = 4.0 * H[2][m] / d;
+            /* E_phi at (r_i, z_j) */
+            out[2][m] = (H[0][m] - zwrap(g, H[0], i, j, -1)) / d - (H[1][m] - hz_l) / d;
+        }
+}
+
 /* Lorentz polarisation, one step of P'' + sigma P' + w0^2 P = deps w0^2 E
  * (Eq. (9) with omega^2 -> xi^2 + i sigma xi and gamma = 0, central differences).
  * `first` applies the start P(-dt) = P(+dt) (P and P' vanish at the impulse). */
@@ -230,13 +298,13 @@ int oracle_run(const og_grid *g, const og_sim *s, double *out_re, double *out_im
         for (int n = 1; n <= s->nsteps; ++n) {
             /* B^{n-1/2} = B^{n-3/2} - dt curl E^{n-1}; the first step is a half step from B(0) = 0 */
             double h = (n == 1) ? 0.5 * dt : dt;
-            curl_e(g, E, T, pe);
+            if (g->cyl) curl_e_cyl(g, E, T); else curl_e(g, E, T, pe);
             for (int c = 0; c < 3; ++c) if (g->hact[c]) for (int m = 0; m < N; ++m) B[c][m] -= h * T[c][m];
             fields_h(g, H, B, N);
             /* P^n from E^{n-1} */
             lorentz_step(g, P, Pm, E, n == 1, N);
             /* D^n = a D^{n-1} + b curl H^{n-1/2}  (sigma on D) */
-            curl_h(g, H, T, ph);
+            if (g->cyl) curl_h_cyl(g, H, T); else curl_h(g, H, T, ph);
             for (int c = 0; c < 3; ++c) if (g->eact[c]) for (int m = 0; m < N; ++m) D[c][m] = a_s * D[c][m] + b_s * T[c][m];
             fields_e(g, E, D, P, N);
             measure(s, E, n - 1, out_re, out_im);
@@ -248,11 +316,11 @@ int oracle_run(const og_grid *g, const og_sim *s, double *out_re, double *out_im
             /* P^{n-1/2} from E^{n-3/2} (identically zero before the first D update) */
             lorentz_step(g, P, Pm, E, 0, N);
             /* D^{n-1/2} = D^{n-3/2} + dt curl H^{n-1}; half step first (no sigma on D) */
-            curl_h(g, H, T, ph);
+            if (g->cyl) curl_h_cyl(g, H, T); else curl_h(g, H, T, ph);
             for (int c = 0; c < 3; ++c) if (g->eact[c]) for (int m = 0; m < N; ++m) D[c][m] += h * T[c][m];
             fields_e(g, E, D, P, N);
             /* B^n = a B^{n-1} - b curl E^{n-1/2}  (sigma on B) */
-            curl_e(g, E, T, pe);
+            if (g->cyl) curl_e_cyl(g, E, T); else curl_e(g, E, T, pe);
             for (int c = 0; c < 3; ++c) if (g->hact[c]) for (int m = 0; m < N; ++m) B[c][m] = a_s * B[c][m] - b_s * T[c][m];
             fields_h(g, H, B, N);
             measure(s, H, n - 1, out_re, out_im);
@@ -293,10 +361,10 @@ int oracle_evolve(const og_grid *g, int nsteps, double *e_re, double *e_im, doub
     for (int n = 1; n <= nsteps; ++n) {
         double h = first ? 0.5 * dt : dt;
         for (int c = 0; c < 3; ++c) for (int m = 0; m < N; ++m) { hprev_re[c * N + m] = RE(H[c][m]); hprev_im[c * N + m] = IM(H[c][m]); }
-        curl_e(g, E, T, pe);
+        if (g->cyl) curl_e_cyl(g, E, T); else curl_e(g, E, T, pe);
         for (int c = 0; c < 3; ++c) if (g->hact[c]) for (int m = 0; m < N; ++m) B[c][m] -= h * T[c][m];
         fields_h(g, H, B, N);
-        curl_h(g, H, T, ph);
+        if (g->cyl) curl_h_cyl(g, H, T); else curl_h(g, H, T, ph);
         for (int c = 0; c < 3; ++c) if (g->eact[c]) for (int m = 0; m < N; ++m) D[c][m] = a_s * D[c][m] + b_s * T[c][m];
         fields_e(g, E, D, P, N);
         first = 0;

@@ -366,3 +366,35 @@ def _serving_sphere(side, rng):
                              n_harm=2, n_steps=int(round(30.0 / (0.5 / res))))
     p["kind"] = "sphere"
     return p
+
+
+def cylinder_piston(resolution, m_list, *, radius=0.5, thickness=0.1, below=0.5, above=1.0, t_max=25.0,
+                    n_harm=1000, sigma=1.0, precision="fp64", basis="cosine", courant=None):
+    """Rotationally symmetric piston (Sec. III C): a PEC disk of the given thickness inside a PEC
+    tube of radius `radius` closed by PEC end caps, `below` above the lower cap and `above` below
+    the upper one; the (r, z) cross-section with fields ~ exp(i m phi), one k-point per m with
+    weight 1 for m = 0 and 2 for m > 0 (the +m and -m terms).  The closed contour is two disks
+    through the tube wall, one in the middle of each cavity; force along z.  The Courant number
+    defaults to 0.95 of the leapfrog limit of the largest m (the i m / r terms next to the axis)."""
+    d = 1.0 / resolution
+    m_max = max(abs(int(m)) for m in m_list)
+    if courant is None:
+        courant = 0.95 * 2.0 / math.sqrt(max(9.0, 8.0 + 4.0 * m_max * m_max))
+    L = below + thickness + above
+    nr, nz = int(round(radius * resolution)), int(round(L * resolution))
+    p = _base(2, (nr, nz, 1), resolution, int(round(t_max / (courant * d))), sigma=sigma, courant=courant)
+    p["coords"] = "cylindrical"
+    p["bc"] = ["pec", "pec", "pec"]
+    p["polarization"] = "full"
+    p["objects"] = [{"shape": "box", "lo": [0.0, below, 0.0], "hi": [radius, below + thickness, 0.0], "kind": "pec"}]
+    z1 = round(0.5 * below * resolution) * d
+    z2 = round((below + thickness + 0.5 * above) * resolution) * d
+    p["faces"] = [{"axis": 1, "sign": -1, "pos": z1, "lo": [0.0, z1, 0.0], "hi": [radius, z1, 0.0]},
+                  {"axis": 1, "sign": 1, "pos": z2, "lo": [0.0, z2, 0.0], "hi": [radius, z2, 0.0]}]
+    p["n_harm"] = n_harm
+    p["basis"] = basis
+    p["force_axis"] = 1
+    p["k_points"] = [{"k": [0.0, 0.0, 0.0], "m": int(m), "weight": 1.0 if int(m) == 0 else 2.0} for m in m_list]
+    p["precision"] = precision
+    p["kind"] = "cylinder"
+    return p
