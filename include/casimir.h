@@ -66,6 +66,14 @@ enum { CASIMIR_FP32 = 0,           /* FP32 fields, FP64 projection and accumulat
        CASIMIR_FP64 = 1 };         /* FP64 throughout */
 enum { CASIMIR_BASIS_COSINE = 0,   /* per-face cosine series, Eq. (7) */
        CASIMIR_BASIS_POINT = 1 };  /* one source per surface pixel (Sec. II point-source method) */
+enum { CASIMIR_COORDS_CARTESIAN = 0,
+       CASIMIR_COORDS_CYLINDRICAL = 1 };  /* (r, z) cross-section of a rotationally symmetric
+                                             geometry with fields ~ exp(i m phi) (Sec. III C and
+                                             the appendix on cylindrical coordinates): axis 0 is r
+                                             (the symmetry axis at r = 0, a PEC wall at r = n[0]
+                                             Delta), axis 1 is z; the force is along z and sums
+                                             the m sectors through the k-point weights (1 for
+                                             m = 0, 2 for m > 0: the +m and -m terms). */
 
 /* One geometric object; later objects override earlier ones where they overlap.
  * Membership is closed (boundary points belong to the object). */
@@ -90,10 +98,13 @@ typedef struct {
 } casimir_face;
 
 /* A k-point (Bloch k_x, k_y; or k_z for a 2D cross-section) and its weight in
- * the force sum (quadrature weight times the measure, e.g. 1/pi for k_z). */
+ * the force sum (quadrature weight times the measure, e.g. 1/pi for k_z).  In
+ * cylindrical coordinates k must be zero and m is the azimuthal order. */
 typedef struct {
     double k[3];
     double weight;
+    int m;               /* cylindrical coordinates: fields ~ exp(i m phi) */
+    int reserved;
 } casimir_kpoint;
 
 typedef struct {
@@ -118,6 +129,10 @@ typedef struct {
     int g_variant;       /* CASIMIR_G_* */
     int precision;       /* CASIMIR_FP32 / CASIMIR_FP64 */
     int basis;           /* CASIMIR_BASIS_* */
+    int coords;          /* CASIMIR_COORDS_*.  Cylindrical problems: dims 2, polarization FULL,
+                            bc[0] PEC (the wall at r = R), no PML, no Lorentz media, k = 0 and
+                            courant < 2 / sqrt(max(9, 8 + 4 m^2)) for every k-point (the i m / r
+                            terms next to the axis bound the time step); else CASIMIR_EINVAL. */
 } casimir_problem;
 
 /* ---- opaque handles ----------------------------------------------------------- */

@@ -25,6 +25,7 @@ POL = {"TM": 1, "TE": 2, "TE+TM": 3, "full": 4}
 GVAR = {"plain": 0, "zinv": 1}
 PREC = {"fp32": 0, "fp64": 1}
 BASIS = {"cosine": 0, "point": 1}
+COORDS = {"cartesian": 0, "cylindrical": 1}
 
 D3 = ctypes.c_double * 3
 I3 = ctypes.c_int * 3
@@ -43,7 +44,7 @@ class Face(ctypes.Structure):
 
 
 class KPoint(ctypes.Structure):
-    _fields_ = [("k", D3), ("weight", ctypes.c_double)]
+    _fields_ = [("k", D3), ("weight", ctypes.c_double), ("m", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class Problem(ctypes.Structure):
@@ -56,7 +57,7 @@ class Problem(ctypes.Structure):
                 ("n_harm", ctypes.c_int), ("polarization", ctypes.c_int),
                 ("n_kpoints", ctypes.c_int), ("kpoints", ctypes.POINTER(KPoint)),
                 ("force_axis", ctypes.c_int), ("g_variant", ctypes.c_int),
-                ("precision", ctypes.c_int), ("basis", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("basis", ctypes.c_int), ("coords", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -169,6 +170,7 @@ class MarshalledProblem:
         for i, k in enumerate(kps):
             self.kpoints[i].k = _d3(k["k"])
             self.kpoints[i].weight = float(k["weight"])
+            self.kpoints[i].m = int(k.get("m", 0))
         s = Problem()
         s.dims = int(p["dims"])
         s.n = I3(*[int(x) for x in p["n"]])
@@ -192,6 +194,7 @@ class MarshalledProblem:
         s.g_variant = GVAR[p.get("g_variant", "plain")]
         s.precision = PREC[p.get("precision", "fp32")]
         s.basis = BASIS[p.get("basis", "cosine")]
+        s.coords = COORDS[p.get("coords", "cartesian")]
         self.struct = s
 
 

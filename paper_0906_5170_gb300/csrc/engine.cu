@@ -200,8 +200,11 @@ static int prepare_plan(casimir_plan_t *P)
             int sarr = sm.src.empty() ? 0 : sm.src[0].arr;
             auto inA = [](int arr) { return arr == 0 || arr == 1 || arr == 5; };
             double sgn = inA(sarr) ? 1.0 : -1.0;
-            hs.kzA = sgn * g.kz;
-            hs.kzB = -sgn * g.kz;
+            // d/dz -> i k_z (Cartesian) or d/dphi -> i m (cylindrical): the same real-phase split
+            const double kq = g.cyl ? (double)g.mphi : g.kz;
+            hs.kzA = sgn * kq;
+            hs.kzB = -sgn * kq;
+            hs.cyl = g.cyl ? 1 : 0;
             // two-dimensional runs march both half steps in one launch over ping-pong buffers
             static const bool march_env = [] {
                 const char *e = std::getenv("CASIMIR_MARCH6");
@@ -209,6 +212,8 @@ static int prepare_plan(casimir_plan_t *P)
             }();
             // (its 32-bit element offsets reach 12 N within one buffer)
             hs.march = (D.prob.dims == 2 && g.n[2] == 1 && march_env && 12 * N < ((int64_t)1 << 32)) ? 1 : 0;
+            if (g.cyl && !hs.march)   // only the march kernel has the cylindrical form
+                return fail(CASIMIR_EINVAL, "cylindrical runs need the march kernel (12 N < 2^32 cells)");
             const int nbuf = hs.march ? 2 : 1;
             hs.fhalf = 6 * cf * N;
             off += nbuf * hs.fhalf;
@@ -618,6 +623,8 @@ static int rebuild(casimir_ctx *c)
     std::vector<DevTile> tm6[16];
     std::vector<DevSim6> sl3[4];
     std::vector<DevTile> tl3[4];
+    std::vector<DevSim6> sc6[2];
+    std::vector<DevTile> tc6[2];
     for (auto &aw : c->active_waves) {
         casimir_request *r = aw.first;
         const casimir_request::Wave &w = r->waves[aw.second];
@@ -652,6 +659,16 @@ static int rebuild(casimir_ctx *c)
                 for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
                     const HostTile &ht = P->tilesM[t];
                     tl3[gi].push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.entsM + ht.ent0});
+                }
+            } else if (hs.cyl) {
+                const int gi = P->fp64;
+                DevSim6 d;
+                make_sim6(P, blk, r->acc, r->tail, w.s0, s, &d);
+                const int idx = (int)sc6[gi].size();
+                sc6[gi].push_back(d);
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile &ht = P->tilesM[t];
+                    tc6[gi].push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.entsM + ht.ent0});
                 }
             } else if (hs.march) {
                 // the simulation's descriptor goes to each variant group that holds one of its tiles
@@ -691,7 +708,8 @@ static int rebuild(casimir_ctx *c)
         else if (gi < 10) { ns = s6[gi - 2].size(); nt = t6[gi - 2].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile6); sp = s6[gi - 2].data(); tp = t6[gi - 2].data(); }
         else if (gi < 12) { ns = 0; nt = tt[gi - 10].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile2); sp = nullptr; tp = tt[gi - 10].data(); }
         else if (gi < 28) { ns = sm6[gi - 12].size(); nt = tm6[gi - 12].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sm6[gi - 12].data(); tp = tm6[gi - 12].data(); }
-        else { ns = sl3[gi - 28].size(); nt = tl3[gi - 28].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sl3[gi - 28].data(); tp = tl3[gi - 28].data(); }
+        else if (gi < 32) { ns = sl3[gi - 28].size(); nt = tl3[gi - 28].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sl3[gi - 28].data(); tp = tl3[gi - 28].data(); }
+        else { ns = sc6[gi - 32].size(); nt = tc6[gi - 32].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sc6[gi - 32].data(); tp = tc6[gi - 32].data(); }
         int rc = grow(c, &G.sims, &G.sims_cap, ns * ss);
         if (rc) return rc;
         rc = grow(c, &G.tiles, &G.tiles_cap, nt * ts);
@@ -726,10 +744,12 @@ static void launch_unit(casimir_ctx *c, int gi, int j, cudaStream_t st)
     else if (gi < 28)
         launch_march6(((gi - 12) >> 3) & 1, ((gi - 12) >> 2) & 1, (gi - 12) & 3, (const DevSim6 *)G.sims,
                       (const DevTile *)G.tiles, G.ntiles, c->d_launch, j, st);
-    else
+    else if (gi < 32)
         for (int phase = 0; phase < 2; ++phase)
             launch_line3(((gi - 28) >> 1) & 1, (gi - 28) & 1, (const DevSim6 *)G.sims, (const DevTile *)G.tiles, G.ntiles,
                          c->d_launch, j, phase, st);
+    else
+        launch_march6_cyl(gi - 32, (const DevSim6 *)G.sims, (const DevTile *)G.tiles, G.ntiles, c->d_launch, j, st);
 }
 
 // Launch k consecutive steps.  The units of one step touch disjoint tiles and read only the
@@ -793,7 +813,7 @@ static int run_chunk(casimir_ctx *c, int k)
     c->h_launch += k;
     int per_step = 0;
     for (int gi = 0; gi < casimir_ctx::NGROUPS; ++gi)
-        if (c->groups[gi].ntiles > 0) per_step += ((gi >= 2 && gi < 10) || gi >= 28) ? 2 : 1;
+        if (c->groups[gi].ntiles > 0) per_step += ((gi >= 2 && gi < 10) || (gi >= 28 && gi < 32)) ? 2 : 1;
     for (casimir_request *r : c->active) r->launches += (int64_t)k * per_step + 1;
     return CASIMIR_OK;
 }

@@ -38,6 +38,7 @@ struct HostSim {
     int full;              // six-component fields
     int march;             // two-dimensional six-component run on the march kernel (ping-pong buffers)
     int line3;             // three-dimensional run on the x-line kernel (tiles in tilesM)
+    int cyl;               // cylindrical (r, z) run on the march kernel's cylindrical variant
     int cplx;              // complex fields (Bloch phase)
     int magnetic;
     double kzA, kzB;       // real-phase d/dz factors (two-dimensional k_z runs)
@@ -168,8 +169,9 @@ struct casimir_ctx {
     // launch groups: [0, 1] the 2D kernel in FP32 / FP64; [2 + 4*fp64 + 2*cplx + (dims == 3)]
     // the six-component kernel; [10, 11] the two-step 2D kernel in FP32 / FP64;
     // [12 + 4 * (2*fp64 + cplx) + variant] the six-component march kernel of two-dimensional runs;
-    // [28 + 2*fp64 + cplx] the x-line kernel of three-dimensional runs
-    static constexpr int NGROUPS = 32;
+    // [28 + 2*fp64 + cplx] the x-line kernel of three-dimensional runs; [32 + fp64] the
+    // cylindrical march kernel
+    static constexpr int NGROUPS = 34;
     struct Group {
         void *sims = nullptr, *tiles = nullptr;
         size_t sims_cap = 0, tiles_cap = 0;

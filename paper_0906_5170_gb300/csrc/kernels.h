@@ -112,6 +112,10 @@ constexpr int MARCH_W = 30;
 constexpr int MARCH_H = 32;
 void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles,
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
+// The same march on a cylindrical (r, z) lattice (x = r from the axis, y = z), fields ~ exp(i m phi)
+// in the real-phase form (kzA, kzB = +-m), no CPML, no Lorentz media.
+void launch_march6_cyl(int fp64, const DevSim6 *sims, const DevTile *tiles, int ntiles,
+                       const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 void launch_inject6(int fp64, void *fields, const DevSrc6 *src, int nsrc, cudaStream_t st);
 
 // Six-component half step of three-dimensional runs by x lines: a tile is 32 x cells (i0) of

@@ -133,6 +133,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
         // sequence) and goes faster through the one-thread-per-cell kernel, in place on buffer 0.
         bool march = P->sims[run[0]].march;
         const bool line3 = P->sims[run[0]].line3;
+        const bool cylr = P->sims[run[0]].cyl;   // only the march kernel has the cylindrical form
         if (march) {
             int64_t nt = 0;
             for (size_t q : run) nt += P->sims[q].ntile;
@@ -140,7 +141,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                 const char *e = std::getenv("CASIMIR_PLAIN_MARCH_TILES");
                 return e ? (int64_t)std::atoll(e) : kPlainMarchTiles;
             }();
-            march = nt >= thr;
+            march = nt >= thr || cylr;
         }
         int cplx = P->sims[run[0]].cplx;
         for (size_t q : run) {
@@ -277,7 +278,11 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                     launch_line3(P->fp64, cplx, (const DevSim6 *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, phase, s);
                 launches += 2;
             } else if (march) {
-                for (int v = 0; v < 4; ++v)
+                if (cylr) {
+                    launch_march6_cyl(P->fp64, (const DevSim6 *)d_sim, (const DevTile *)d_tiles, voff[4], d_counter, n - 1, s);
+                    ++launches;
+                }
+                for (int v = 0; v < 4 && !cylr; ++v)
                     if (voff[v + 1] > voff[v]) {
                         launch_march6(P->fp64, cplx, v, (const DevSim6 *)d_sim, (const DevTile *)d_tiles + voff[v],
                                       voff[v + 1] - voff[v], d_counter, n - 1, s);

@@ -199,6 +199,15 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err)
         }
     }
     if (p.dims == 2) g->kz = k[2];
+    const bool cyl = p.coords == CASIMIR_COORDS_CYLINDRICAL;
+    if (cyl) {
+        // r is not periodic: nothing couples across r = R (the PEC wall) or below the axis
+        g->cyl = true;
+        g->mphi = P.kpoints[kpt].m;
+        g->kz = 0.0;
+        g->bloch_re[0] = 0.0;
+        g->bloch_im[0] = 0.0;
+    }
     // a complex Bloch phase needs complex fields; k_z alone keeps them real (see the kernel)
     g->complex_fields = cplxf;
     if ((cplxf || g->kz != 0.0) && family != FAM_FULL) { *err = "k_z or a complex Bloch phase needs polarization FULL"; return CASIMIR_EINVAL; }
@@ -218,13 +227,20 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err)
                     bool wall = false;
                     for (int ax = 0; ax < p.dims; ++ax) {
                         x[ax] = canon(x[ax], L[ax]);
+                        if (cyl && ax == 0) continue;   // r = 0 is the axis, the wall r = R lies beyond the grid
                         if (as.field == 0 && (p.bc[ax] == CASIMIR_BC_PEC || p.bc[ax] == CASIMIR_BC_PML) &&
                             std::fabs(x[ax]) < kTol * P.dx)
                             wall = true;
                     }
+                    // on the axis: E_phi and H_r carry no weight (r = 0); E_z ~ r^|m| vanishes for m != 0
+                    bool axis_mask = cyl && i == 0 && as.off[0] == 0.0 &&
+                                     ((as.field == 0 && as.comp == 2) || (as.field == 1 && as.comp == 0) ||
+                                      (as.field == 0 && as.comp == 1 && g->mphi != 0));
                     Mat m = material_at(P, x);
                     double c;
-                    if (as.field == 0) {
+                    if (axis_mask) {
+                        c = 0.0;
+                    } else if (as.field == 0) {
                         c = (m.pec || wall) ? 0.0 : 1.0 / m.eps;
                         if (!(m.pec || wall) && m.de != 0.0) {
                             key[narr + 2 * as.comp] = m.de;
@@ -382,6 +398,23 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
         }
     }
 
+    if (p.coords != CASIMIR_COORDS_CARTESIAN && p.coords != CASIMIR_COORDS_CYLINDRICAL) { *err = "coords"; return CASIMIR_EINVAL; }
+    if (p.coords == CASIMIR_COORDS_CYLINDRICAL) {
+        if (p.dims != 2 || p.polarization != CASIMIR_POL_FULL || p.bc[0] != CASIMIR_BC_PEC) {
+            *err = "cylindrical problems are (r, z) cross-sections with polarization FULL and a PEC wall at r = R";
+            return CASIMIR_EINVAL;
+        }
+        if (p.bc[1] == CASIMIR_BC_PML) { *err = "cylindrical problems take PEC or periodic z boundaries"; return CASIMIR_EINVAL; }
+        for (auto &o : P->objects)
+            if (o.kind == CASIMIR_MAT_LORENTZ) { *err = "cylindrical problems take no Lorentz media"; return CASIMIR_EINVAL; }
+        for (auto &k : P->kpoints) {
+            if (k.k[0] != 0.0 || k.k[1] != 0.0 || k.k[2] != 0.0) { *err = "cylindrical k-points carry m only (k = 0)"; return CASIMIR_EINVAL; }
+            // the i m / r terms next to the axis bound the step: the spatial operator's largest
+            // eigenvalue is below max(9, 8 + 4 m^2) / Delta^2
+            double lam = std::max(9.0, 8.0 + 4.0 * (double)k.m * (double)k.m);
+            if (p.courant * p.courant * lam >= 4.0) { *err = "courant number above the cylindrical stability limit for this m"; return CASIMIR_EINVAL; }
+        }
+    }
     if (twod_pol) {
         for (auto &o : P->objects)
             if (o.kind == CASIMIR_MAT_LORENTZ) { *err = "Lorentz media need polarization FULL"; return CASIMIR_EINVAL; }
@@ -485,7 +518,16 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
                     for (size_t q = 0; q < px.x.size(); ++q) {
                         if (fv[q] == 0.0) continue;
                         stencil(*P, g, arrs[sa], px.x[q].data(), st);
-                        for (auto &e : st) add_entry(sim.src, at, sa, e.first, -std::conj(e.second) * fv[q] / P->dx);
+                        for (auto &e : st) {
+                            // cylindrical: the surface current on the surface of revolution averaged over
+                            // the site's ring carries r(pixel) / w(site), w = r_site (Delta/8 on the axis)
+                            double scale = 1.0;
+                            if (g.cyl) {
+                                double rs = ((double)(e.first % p.n[0]) + arrs[sa].off[0]) * P->dx;
+                                scale = px.x[q][0] / (rs > 0.5 * kTol * P->dx ? rs : 0.125 * P->dx);
+                            }
+                            add_entry(sim.src, at, sa, e.first, -std::conj(e.second) * fv[q] * scale / P->dx);
+                        }
                     }
                     for (auto &e : sim.src) {
                         double c = g.table[(size_t)g.mat[e.idx] * narr + sa] * arrs[sa].sign;

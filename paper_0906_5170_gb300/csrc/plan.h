@@ -50,6 +50,8 @@ struct Geo {
     double bloch_re[3] = {1, 1, 1}, bloch_im[3] = {0, 0, 0};
     double kz = 0.0;
     bool complex_fields = false;
+    bool cyl = false;               // cylindrical (r, z) lattice, fields ~ exp(i m phi)
+    int mphi = 0;
     // CPML per axis a and site kind h (0 integer, 1 half): b, c, 1/kappa along that axis
     std::vector<double> pml[3][2][3];
     bool has_pml[3] = {false, false, false};

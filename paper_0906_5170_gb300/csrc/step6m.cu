@@ -84,7 +84,10 @@ struct RowIn {
     Z<R, CPLX> px[4], py[4];
 };
 
-template <typename R, bool CPLX, bool PML, bool LOR, int MINB>
+// CYL: cylindrical (r, z) lattice (Sec. III C), x = r from the symmetry axis, y = z, stored
+// components (E_r, E_z, E_phi, H_r, H_z, H_phi) on the sites of (E_x, E_y, E_z, H_x, H_y, H_z);
+// d/dphi -> i m in the real-phase form (kzA, kzB = +-m), per-lane radial factors.
+template <typename R, bool CPLX, bool PML, bool LOR, int MINB, bool CYL = false>
 __global__ void __launch_bounds__(WARPS6 * 32, MINB)
 k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, int ntiles,
          const int64_t *__restrict__ launch_base, int64_t launch_add)
@@ -151,6 +154,20 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     const R hfirst = (R)(n == 1 ? 0.5 * S.dt : S.dt);
     const bool electric = S.magnetic == 0;
     const bool first_e = electric && n == 1;              // Lorentz start of electric sources
+    // cylindrical radial factors of this lane's column i (r_i = i Delta, r_{i+1/2}, ...):
+    //   (1/r) d(r E_phi)/dr at r_{i+1/2} = (ga E_phi(i+1) - gb E_phi(i)) / Delta,
+    //   (1/r) d(r H_phi)/dr at r_i = (fa H_phi(i+1/2) - fb H_phi(i-1/2)) / Delta, on the axis
+    //   Stokes over the disk of radius Delta/2: 4 H_phi(Delta/2) / Delta (fa = 4, fb = 0)
+    R inv_ri = 0, inv_rh = 0, ga = 0, gb = 0, fa = 0, fb = 0;
+    if constexpr (CYL) {
+        const double d = 1.0 / S.inv_dx, ri = col * d, rh = (col + 0.5) * d;
+        inv_ri = col > 0 ? (R)(1.0 / ri) : (R)0;
+        inv_rh = (R)(1.0 / rh);
+        ga = (R)((col + 1) * d / rh);
+        gb = (R)(ri / rh);
+        fa = col > 0 ? (R)(rh / ri) : (R)4;
+        fb = col > 0 ? (R)((col - 0.5) * d / ri) : (R)0;
+    }
     auto rowp = [&](int j) { return j < 0 ? j + ny : (j >= ny ? j - ny : j); };
     auto iny = [&](int j) { return PML && dY > 0 && (j < dY || j >= ny - dY); };
     auto gxi = [&](int j) { return (unsigned)(j * (2 * dX) + sx); };
@@ -215,9 +232,18 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
             }
         }
         const R *cm = coef + 6 * m;
-        ho[0] = hq[0] * aa - (dyEz - dzA(e[1])) * (bb * cm[3]);
-        ho[1] = hq[1] * aa - (dzA(e[0]) - dxEz) * (bb * cm[4]);
-        ho[2] = hq[2] * aa - (dxEy - dyEx) * (bb * cm[5]);
+        if constexpr (CYL) {
+            // H_r = -(i m/r E_z - dE_phi/dz), H_z = -((1/r) d(r E_phi)/dr - i m/r E_r),
+            // H_phi = -(dE_r/dz - dE_z/dr)
+            const V dxEphi = (right(e[2]) * ga - e[2] * gb) * idx;
+            ho[0] = hq[0] * aa - (e[1] * (kA * inv_ri) - dyEz) * (bb * cm[3]);
+            ho[1] = hq[1] * aa - (dxEphi - e[0] * (kA * inv_rh)) * (bb * cm[4]);
+            ho[2] = hq[2] * aa - (dyEx - dxEy) * (bb * cm[5]);
+        } else {
+            ho[0] = hq[0] * aa - (dyEz - dzA(e[1])) * (bb * cm[3]);
+            ho[1] = hq[1] * aa - (dzA(e[0]) - dxEz) * (bb * cm[4]);
+            ho[2] = hq[2] * aa - (dxEy - dyEx) * (bb * cm[5]);
+        }
     };
     // E at row j from H at rows j and j-1: new E, the E-plane psi (0, 1) and P written when wr
     auto updE = [&](int j, int m, const V hh[3], V hxp, V hzp, const V eo[3], const RowIn<R, CPLX> &in, R aa, R bb,
@@ -240,7 +266,18 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                 if (wr) { const unsigned gg = gyi(j); st<R, CPLX>(pyout, 0, PY, gg, p0); st<R, CPLX>(pyout, 1, PY, gg, p1); }
             }
         }
-        const V c3[3] = {dyHz - dzB(hh[1]), dzB(hh[0]) - dxHz, dxHy - dyHx};
+        V c3[3];
+        if constexpr (CYL) {
+            // E_r: i m/r H_z - dH_phi/dz; E_z: (1/r) d(r H_phi)/dr - i m/r H_r; E_phi: dH_r/dz - dH_z/dr
+            const V dxHphi = (hh[2] * fa - left(hh[2]) * fb) * idx;
+            c3[0] = hh[1] * (kB * inv_rh) - dyHz;
+            c3[1] = dxHphi - hh[0] * (kB * inv_ri);
+            c3[2] = dyHx - dxHy;
+        } else {
+            c3[0] = dyHz - dzB(hh[1]);
+            c3[1] = dzB(hh[0]) - dxHz;
+            c3[2] = dxHy - dyHx;
+        }
         const R *cm = coef + 6 * m;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -412,6 +449,15 @@ void launch_t(int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles
 }
 
 }  // namespace
+
+void launch_march6_cyl(int fp64, const DevSim6 *sims, const DevTile *tiles, int ntiles,
+                       const int64_t *launch_base, int64_t launch_add, cudaStream_t st)
+{
+    if (ntiles <= 0) return;
+    const int grid = (ntiles + WARPS6 - 1) / WARPS6;
+    if (fp64) k_march6<double, false, false, false, 4, true><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
+    else k_march6<float, false, false, false, 6, true><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
+}
 
 void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles,
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st)

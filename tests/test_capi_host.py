@@ -83,3 +83,29 @@ def test_context_without_device_fails_cleanly():
     with pytest.raises(pk.CasimirError) as e:
         pk.Context(0)
     assert e.value.code in (-1, -3)
+
+
+def test_plan_sim_list_matches_oracle_cylindrical():
+    p = W.cylinder_piston(12, [0, 1, 2], t_max=2.0)
+    plan = pk.Plan(p)
+    got = [tuple(int(v) for v in r) for r in plan.sims()]
+    assert got == _sim_tuples(p)
+    w = plan.weights()
+    assert np.max(np.abs(w - oracle.g_weights(p)) / np.abs(oracle.g_weights(p))) < 1e-12
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda p: p.update(courant=0.41),                                  # above the m = 2 limit 2/sqrt(24) = 0.408
+    lambda p: p.update(bc=["pec", "pml", "pec"], pml_cells=[0, 3, 0]),
+    lambda p: p.update(bc=["periodic", "pec", "pec"]),
+    lambda p: p.update(polarization="TM"),
+    lambda p: p["k_points"][0].update(k=[0.0, 0.3, 0.0]),
+    lambda p: p["objects"].append({"shape": "box", "lo": [0.1, 0.1, 0], "hi": [0.2, 0.2, 0], "kind": "lorentz",
+                                   "eps_inf": 1.0, "delta_eps": 2.0, "omega0": 1.0}),
+])
+def test_plan_rejects_invalid_cylindrical_problems(mutate):
+    p = W.cylinder_piston(12, [0, 1, 2], t_max=2.0)
+    mutate(p)
+    with pytest.raises(pk.CasimirError) as e:
+        pk.Plan(p)
+    assert e.value.code == -1

@@ -335,3 +335,29 @@ def test_complete_cosine_basis_equals_point_basis_on_gpu(ctx):
     # a truncated cosine basis differs, and the difference shrinks with the harmonic count
     errs = [abs(ctx.plan(dict(p, n_harm=k)).run()[0][fa] - F_pt[fa]) for k in (2, 4, 8)]
     assert errs[0] > errs[1] > errs[2] > 1e-10 * scale
+
+
+# ---- cylindrical (r, z) runs with exp(i m phi) fields (Sec. III C) -------------------------
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cylindrical_piston(ctx, prec):
+    p = W.cylinder_piston(12, [0, 1, 2, 3], t_max=6.0, precision=prec)
+    _check(ctx, p, ("cyl", prec), prec == "fp64")
+
+
+def test_cylindrical_multi_strip_ragged(ctx):
+    # 40 radial cells: two warp strips (30 + 10) and two row bands along z
+    p = W.cylinder_piston(40, [0, 2], radius=1.0, below=0.4, above=0.7, t_max=1.5, n_harm=6)
+    _check(ctx, p, "cyl_wide", True)
+
+
+def test_cylindrical_plain_path_and_mixed_batch(ctx):
+    p = W.cylinder_piston(10, [0, 1], t_max=4.0, precision="fp64")
+    Fb, pb, _ = ctx.plan(p).run(per_sim=True)
+    Fp, pp, _ = ctx.plan(p).run(per_sim=True, plain=True)
+    assert np.allclose(pp, pb, rtol=1e-9, atol=1e-13 * np.sum(np.abs(pb)))
+    q = W.piston_small(n_steps=300, precision="fp64")
+    Fq = ctx.plan(q).run()[0]
+    t1, t2 = ctx.plan(p).submit(), ctx.plan(q).submit()
+    assert np.allclose(t1.force(-1)[0], Fb, rtol=1e-12, atol=0)
+    assert np.allclose(t2.force(-1)[0], Fq, rtol=1e-12, atol=0)
