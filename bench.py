@@ -222,6 +222,40 @@ def measure_basis(pk, ctx):
     return out
 
 
+def measure_cylinder(pk, ctx):
+    """The rotationally symmetric two-block piston (Sec. III C; the paper's cylindrical
+    counterpart of the two-block configuration): PEC and PMC tubes at three sidewall spacings,
+    n, m in {0, 1, 2}, all six requests in flight together; plus the share of each m in one force."""
+    import numpy as np
+    import workloads as W
+    meta, plans = [], []
+    for side in ("pec", "pmc"):
+        for h in (0.5, 1.0, 2.0):
+            meta.append((side, h))
+            plans.append(ctx.plan(W.cylinder_blocks(h, sidewall=side)))
+    for pl in plans:
+        pl.run()                               # tables uploaded, graphs built
+    ctx.kernel_stats(reset=True)
+    t0 = time.perf_counter()
+    tickets = [pl.submit(tag=i) for i, pl in enumerate(plans)]
+    res = [t.force(-1) for t in tickets]
+    wall = time.perf_counter() - t0
+    ms, _, cu = ctx.kernel_stats(reset=True)
+    out = {"workload": "two PEC disks (radius 1/2, thickness 1, gap 1) in a tube of radius 1/2 + h, "
+                       "resolution 40, n, m in {0, 1, 2}, 10314 steps, FP32 fields",
+           "forces": [{"sidewall": sd, "h": h, "F_z": float(r[0][1])} for (sd, h), r in zip(meta, res)],
+           "gcell_updates_per_s": cu / (ms / 1e3) / 1e9, "forces_per_s": len(plans) / wall, "kernel_ms": ms}
+    # the share of each m in one force (h = 1, PEC tube)
+    pl = plans[1]
+    _, per, _ = pl.run(per_sim=True)
+    kpt = np.array([r[0] for r in pl.sims()])
+    tot = float(np.sum(per))
+    out["m_shares_h1_pec"] = {str(m): float(np.sum(per[kpt == i]) / tot) for i, m in enumerate((0, 1, 2))}
+    for pl in plans:
+        pl.close()
+    return out
+
+
 def cpu_baseline(budget_s=15.0):
     """The FP64 oracle on a bounded sample of the workload: simulations of the
     h = 0.5 geometry for a shortened number of steps, one per host core."""
@@ -433,6 +467,7 @@ def main():
     if not args.no_configs:
         others = measure_configs(pk, ctx, peaks()[0])
         others["basis_point_vs_cosine"] = measure_basis(pk, ctx)
+        others["cylinder_piston"] = measure_cylinder(pk, ctx)
 
     cb = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -398,3 +398,38 @@ def cylinder_piston(resolution, m_list, *, radius=0.5, thickness=0.1, below=0.5,
     p["precision"] = precision
     p["kind"] = "cylinder"
     return p
+
+
+def cylinder_blocks(h, *, resolution=40, m_list=(0, 1, 2), n_harm=3, t_max=100.0, sidewall="pec",
+                    precision="fp32", sigma=1.0):
+    """The piston of the two-block configuration rotated about its axis (Sec. III C): two PEC disks
+    of radius 1/2 and thickness 1, gap 1 along z, inside a tube of radius 1/2 + h (PEC, or PMC
+    with `sidewall="pmc"`: a one-cell PMC lining inside the PEC wall), PEC end caps 10 apart.
+    Contour: the surface of revolution one pixel outside the upper disk (two disks and a
+    cylinder); force along z, summed over m in m_list (weight 1 for m = 0, 2 otherwise) with
+    n_harm cosine harmonics per face."""
+    d = 1.0 / resolution
+    R = 0.5 + h
+    m_max = max(m_list)
+    courant = 0.95 * 2.0 / math.sqrt(max(9.0, 8.0 + 4.0 * m_max * m_max))
+    nr, nz = int(round(R * resolution)), int(round(10 * resolution))
+    p = _base(2, (nr, nz, 1), resolution, int(round(t_max / (courant * d))), sigma=sigma, courant=courant)
+    p["coords"] = "cylindrical"
+    p["bc"] = ["pec", "pec", "pec"]
+    p["polarization"] = "full"
+    p["objects"] = [
+        {"shape": "box", "lo": [0.0, 3.5, 0.0], "hi": [0.5, 4.5, 0.0], "kind": "pec"},
+        {"shape": "box", "lo": [0.0, 5.5, 0.0], "hi": [0.5, 6.5, 0.0], "kind": "pec"},
+    ]
+    if sidewall == "pmc":
+        p["objects"].append({"shape": "box", "lo": [R - d, 0.0, 0.0], "hi": [R, 10.0, 0.0], "kind": "pmc"})
+    z0, z1, r1 = 5.5 - d, 6.5 + d, 0.5 + d
+    p["faces"] = [{"axis": 1, "sign": -1, "pos": z0, "lo": [0.0, z0, 0.0], "hi": [r1, z0, 0.0]},
+                  {"axis": 1, "sign": 1, "pos": z1, "lo": [0.0, z1, 0.0], "hi": [r1, z1, 0.0]},
+                  {"axis": 0, "sign": 1, "pos": r1, "lo": [r1, z0, 0.0], "hi": [r1, z1, 0.0]}]
+    p["n_harm"] = n_harm
+    p["force_axis"] = 1
+    p["k_points"] = [{"k": [0.0, 0.0, 0.0], "m": int(m), "weight": 1.0 if int(m) == 0 else 2.0} for m in m_list]
+    p["precision"] = precision
+    p["kind"] = "cylinder"
+    return p
