@@ -289,6 +289,10 @@ def profile_case_problems(case, steps):
         return [W.config3_waveguides(0.5, n_harm=6, n_steps=steps, k_points=[kp[3], kp[12]])]
     if case == "sphere3d":     # 160^3 CPML cell, 1 harmonic per face: 20 simulations
         return [W.config4_sphere_notch(0.55, seed=1, n_harm=1, n_steps=steps)]
+    if case == "cylinder":     # rotationally symmetric two-block piston, h = 1: 60 x 400 (r, z), m, n <= 2
+        p = W.cylinder_blocks(1.0)
+        p["n_steps"] = steps
+        return [p]
     if case == "grating":      # 128 x 512 Bloch cell, 16 k_x (complex fields), CPML along y, 8 harmonics
         import numpy as np
         p = W._serving_grating(1.0, np.random.default_rng(0))
@@ -353,7 +357,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=12)
     ap.add_argument("--no-configs", action="store_true")
-    ap.add_argument("--profile-case", choices=["piston", "waveguides", "sphere3d", "grating"], default=None,
+    ap.add_argument("--profile-case", choices=["piston", "waveguides", "sphere3d", "grating", "cylinder"], default=None,
                     help="run one mid-size case for kernel profiling instead of the benchmark")
     args = ap.parse_args()
     if args.impl == "reference":

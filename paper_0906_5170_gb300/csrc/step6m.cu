@@ -26,6 +26,10 @@ namespace cas {
 namespace {
 
 constexpr int WARPS6 = 4;   // warps (strips) per CTA
+#ifndef MARCH_PF
+#define MARCH_PF 2
+#endif
+constexpr int PFMAX = MARCH_PF;   // upper bound of the prefetch depth of every variant
 
 template <typename R, bool CPLX>
 struct Z;
@@ -87,12 +91,15 @@ struct RowIn {
 // CYL: cylindrical (r, z) lattice (Sec. III C), x = r from the symmetry axis, y = z, stored
 // components (E_r, E_z, E_phi, H_r, H_z, H_phi) on the sites of (E_x, E_y, E_z, H_x, H_y, H_z);
 // d/dphi -> i m in the real-phase form (kzA, kzB = +-m), per-lane radial factors.
-template <typename R, bool CPLX, bool PML, bool LOR, int MINB, bool CYL = false>
+// PF: rows whose inputs are in flight ahead of the row being computed (1 or 2; 2 where the
+// registers allow it without spilling, i.e. without the CPML planes)
+template <typename R, bool CPLX, bool PML, bool LOR, int MINB, bool CYL = false, int PFREQ = 1>
 __global__ void __launch_bounds__(WARPS6 * 32, MINB)
 k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, int ntiles,
          const int64_t *__restrict__ launch_base, int64_t launch_add)
 {
     using V = Z<R, CPLX>;
+    constexpr int PF6 = PFREQ < PFMAX ? PFREQ : PFMAX;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ti = blockIdx.x * WARPS6 + warp;
     if (ti >= ntiles) return;
@@ -304,7 +311,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
         const int j0 = t.j0;
         const int jm = rowp(j0 - 1);
         const unsigned gm = (unsigned)(jm * nx + col), g0 = (unsigned)(j0 * nx + col);
-        RowIn<R, CPLX> cur, nxt;
+        RowIn<R, CPLX> cur, nxt, nx2;
         if (electric) {
             // H (a = 1, b = h) then E (a, b_sigma).  Carried: E^n of row j, H^{n+1/2} of row j-1.
             // The material of row j+2 is loaded at row j, so that P of row j+1 loads only where dispersive.
@@ -330,13 +337,15 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                 load_psi(in, j, 0, 4);
             };
             load_row(cur, j0, mat[g0]);
-            int m_ahead = h > 1 ? mat[g0 + nx] : 0;                 // material of the next row to load
+            if (PF6 == 2 && h > 1) load_row(nxt, j0 + 1, mat[g0 + nx]);
+            // material of the next row to load (row j0 + PF6), loaded one row before its fields
+            int m_ahead = h > PF6 ? mat[g0 + PF6 * nx] : 0;
             for (int r = 0; r < h; ++r) {
                 const int j = j0 + r;
                 const unsigned g = (unsigned)(j * nx + col);
-                if (r + 1 < h) {
-                    load_row(nxt, j + 1, m_ahead);
-                    if (r + 2 < h) m_ahead = mat[g + 2 * nx];
+                if (r + PF6 < h) {
+                    load_row(PF6 == 2 ? nx2 : nxt, j + PF6, m_ahead);
+                    if (r + PF6 + 1 < h) m_ahead = mat[g + (PF6 + 1) * nx];
                 }
                 V hn[3], en[3];
                 updH(j, cur.m, e, cur.f[0], cur.f[2], cur.q, cur.px, cur.py, (R)1, hfirst, own, hn);
@@ -354,6 +363,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                     e[k] = cur.f[k];
                 }
                 cur = nxt;
+                if (PF6 == 2) nxt = nx2;
             }
         } else {
             // E (a = 1, b = h) one row ahead, then H (a, b_sigma).  Carried: H^n of row j, E^{n+1} of row j.
@@ -383,13 +393,15 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                 load_psi(in, j, 2, 4);
             };
             load_row(cur, j0, mat[(unsigned)(rowp(j0 + 1) * nx + col)]);
-            int m_ahead = h > 1 ? mat[(unsigned)(rowp(j0 + 2) * nx + col)] : 0;   // material of row j+2
+            if (PF6 == 2 && h > 1) load_row(nxt, j0 + 1, mat[(unsigned)(rowp(j0 + 2) * nx + col)]);
+            // material of the row after the next one to load (its fields arrive one row later)
+            int m_ahead = h > PF6 ? mat[(unsigned)(rowp(j0 + PF6 + 1) * nx + col)] : 0;
             for (int r = 0; r < h; ++r) {
                 const int j = j0 + r, jn = rowp(j + 1);
                 const unsigned g = (unsigned)(j * nx + col), gn = (unsigned)(jn * nx + col);
-                if (r + 1 < h) {
-                    load_row(nxt, j + 1, m_ahead);
-                    if (r + 2 < h) m_ahead = mat[(unsigned)(rowp(j + 3) * nx + col)];
+                if (r + PF6 < h) {
+                    load_row(PF6 == 2 ? nx2 : nxt, j + PF6, m_ahead);
+                    if (r + PF6 + 1 < h) m_ahead = mat[(unsigned)(rowp(j + PF6 + 2) * nx + col)];
                 }
                 V en[3], hn[3];
                 // E of row j + 1: psi and P written only for rows of this strip
@@ -409,6 +421,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                 }
                 m = cur.m;
                 cur = nxt;
+                if (PF6 == 2) nxt = nx2;
             }
         }
     }
@@ -441,10 +454,10 @@ void launch_t(int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles
 {
     const int grid = (ntiles + WARPS6 - 1) / WARPS6;
     switch (variant) {
-    case 0: k_march6<R, CPLX, false, false, M0><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    case 1: k_march6<R, CPLX, true, false, M1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    case 2: k_march6<R, CPLX, false, true, M2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    default: k_march6<R, CPLX, true, true, M3><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 0: k_march6<R, CPLX, false, false, M0, false, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 1: k_march6<R, CPLX, true, false, M1, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 2: k_march6<R, CPLX, false, true, M2, false, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    default: k_march6<R, CPLX, true, true, M3, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
     }
 }
 
@@ -455,8 +468,8 @@ void launch_march6_cyl(int fp64, const DevSim6 *sims, const DevTile *tiles, int 
 {
     if (ntiles <= 0) return;
     const int grid = (ntiles + WARPS6 - 1) / WARPS6;
-    if (fp64) k_march6<double, false, false, false, 4, true><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
-    else k_march6<float, false, false, false, 6, true><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
+    if (fp64) k_march6<double, false, false, false, 4, true, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
+    else k_march6<float, false, false, false, 6, true, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
 }
 
 void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles,
