@@ -357,6 +357,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=12)
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default execution options instead of autotuned ones")
     ap.add_argument("--profile-case", choices=["piston", "waveguides", "sphere3d", "grating", "cylinder"], default=None,
                     help="run one mid-size case for kernel profiling instead of the benchmark")
     args = ap.parse_args()
@@ -382,8 +383,10 @@ def main():
 
     stream = torch.cuda.Stream()
     ctx = pk.Context(local, stream=stream.cuda_stream)
+    ctx.set_autotune(not args.no_autotune)      # schedules picked per problem class by timed trials
     probs = workload_problems(args.time_steps)
     plans = [ctx.plan(p) for p in probs]
+    autotune = {"on": not args.no_autotune, "chosen": [pl.options() for pl in plans]}
     infos = [pl.info() for pl in plans]
     cells_per_step = sum(i["cell_updates"] for i in infos)
     n_forces = len(plans)
@@ -496,6 +499,7 @@ def main():
             "forces_per_s": forces_per_s,
             "latency_ms": {"p50": lat_sorted[len(lat) // 2], "p99": lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))]},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "serving": serving, "other_configs": others,
+            "autotune": autotune,
             "gpu_launches": int(launches + 3 * n_forces * args.steps),
             "clocks": clk,
         }

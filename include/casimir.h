@@ -200,6 +200,29 @@ int casimir_ctx_kernel_stats(casimir_ctx_t *ctx, double *step_ms, int64_t *launc
  * problem), CASIMIR_ENOMEM (the plan alone needs more device memory than the budget). */
 int casimir_plan(casimir_ctx_t *ctx, const casimir_problem *problem, casimir_plan_t **out);
 int casimir_plan_get_info(const casimir_plan_t *plan, casimir_plan_info *info);
+
+/* Execution options of a plan (how the leapfrog of Sec. III A is scheduled; the computed
+ * force does not depend on them beyond rounding).  0 in a field selects the default. */
+typedef struct {
+    int steps_per_launch;   /* 2D TM/TE runs: time steps fused into one pass over memory, 1 or 2 (default 2) */
+    int march_rows;         /* 2D six-component and cylindrical runs: rows per strip tile, 16, 32 or 64 (default 32) */
+    int kernel_3d;          /* 3D runs: 1 = x-line kernel (default), 2 = one-thread-per-cell kernel */
+    int reserved;
+} casimir_plan_options;
+
+/* casimir_plan with explicit options (NULL: defaults).  CASIMIR_EINVAL for values out of range. */
+int casimir_plan_ex(casimir_ctx_t *ctx, const casimir_problem *problem, const casimir_plan_options *opts,
+                    casimir_plan_t **out);
+/* The options a plan was prepared with (after defaults and autotuning). */
+int casimir_plan_get_options(const casimir_plan_t *plan, casimir_plan_options *opts);
+
+/* Autotuning (on != 0): casimir_plan then picks the options itself.  For the first problem of
+ * each class (dimension, polarisation family, precision, coordinates, CPML and Lorentz media,
+ * complex fields, grid size to a factor of two) it runs every candidate option set on a copy of
+ * the problem cut to 128 steps, times the step kernels with CUDA events and keeps the fastest;
+ * later problems of the class reuse the choice.  Trials run only while the context is idle
+ * (otherwise the defaults apply and nothing is cached).  Off by default. */
+int casimir_ctx_set_autotune(casimir_ctx_t *ctx, int on);
 /* Release a plan; blocks until the plan's queued or running requests have finished. */
 void casimir_plan_destroy(casimir_plan_t *plan);
 

@@ -66,6 +66,11 @@ class PlanInfo(ctypes.Structure):
                 ("upload_bytes", ctypes.c_int64)]
 
 
+class PlanOptions(ctypes.Structure):
+    _fields_ = [("steps_per_launch", ctypes.c_int), ("march_rows", ctypes.c_int), ("kernel_3d", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("queue_ms", ctypes.c_double), ("device_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
                 ("cell_updates", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
@@ -87,6 +92,10 @@ SIGNATURES = {
                                                 ctypes.c_int]),
     "casimir_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_void_p)]),
     "casimir_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
+    "casimir_plan_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.POINTER(PlanOptions),
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "casimir_plan_get_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanOptions)]),
+    "casimir_ctx_set_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "casimir_plan_destroy": (None, [ctypes.c_void_p]),
     "casimir_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p)]),
     "casimir_force": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -223,6 +232,9 @@ class Context:
     def set_wave_bytes(self, nbytes):
         check(lib().casimir_ctx_set_wave_bytes(self.h, int(nbytes)))
 
+    def set_autotune(self, on=True):
+        check(lib().casimir_ctx_set_autotune(self.h, 1 if on else 0))
+
     def kernel_stats(self, reset=False):
         ms = ctypes.c_double()
         nl = ctypes.c_int64()
@@ -230,8 +242,8 @@ class Context:
         check(lib().casimir_ctx_kernel_stats(self.h, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(cu), int(reset)))
         return ms.value, nl.value, cu.value
 
-    def plan(self, problem: dict):
-        return Plan(problem, self)
+    def plan(self, problem: dict, options: dict | None = None):
+        return Plan(problem, self, options)
 
     def close(self):
         if self.h:
@@ -250,15 +262,25 @@ class Context:
 class Plan:
     """casimir_plan_t built from a problem dictionary (ctx None: host-only plan)."""
 
-    def __init__(self, problem: dict, ctx: Context | None = None):
+    def __init__(self, problem: dict, ctx: Context | None = None, options: dict | None = None):
         self.problem = problem
         self.ctx = ctx
         self._m = MarshalledProblem(problem)
         h = ctypes.c_void_p()
-        check(lib().casimir_plan(ctx.h if ctx else None, ctypes.byref(self._m.struct), ctypes.byref(h)))
+        if options is None:
+            check(lib().casimir_plan(ctx.h if ctx else None, ctypes.byref(self._m.struct), ctypes.byref(h)))
+        else:
+            o = PlanOptions(**{k: int(v) for k, v in options.items()})
+            check(lib().casimir_plan_ex(ctx.h if ctx else None, ctypes.byref(self._m.struct), ctypes.byref(o),
+                                        ctypes.byref(h)))
         self.h = h
         if ctx is not None:
             ctx._plans.add(self)
+
+    def options(self):
+        o = PlanOptions()
+        check(lib().casimir_plan_get_options(self.h, ctypes.byref(o)))
+        return {f: getattr(o, f) for f, _ in PlanOptions._fields_ if f != "reserved"}
 
     def info(self):
         i = PlanInfo()

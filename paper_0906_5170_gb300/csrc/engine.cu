@@ -205,6 +205,7 @@ static int prepare_plan(casimir_plan_t *P)
             hs.kzA = sgn * kq;
             hs.kzB = -sgn * kq;
             hs.cyl = g.cyl ? 1 : 0;
+            const int rows = P->opts.march_rows;
             // two-dimensional runs march both half steps in one launch over ping-pong buffers
             static const bool march_env = [] {
                 const char *e = std::getenv("CASIMIR_MARCH6");
@@ -233,7 +234,7 @@ static int prepare_plan(casimir_plan_t *P)
             if (hs.march) {
                 // one strip tile (MARCH_W x MARCH_H) per warp, row bands outer; entries carry the
                 // component in bits 16..18 and, for the imaginary weight of complex fields, bit 19
-                int tx = (hs.nx + MARCH_W - 1) / MARCH_W, ty = (hs.ny + MARCH_H - 1) / MARCH_H;
+                int tx = (hs.nx + MARCH_W - 1) / MARCH_W, ty = (hs.ny + rows - 1) / rows;
                 // kernel variant of each tile: the CPML and Lorentz code paths only where the tile's
                 // halo-extended box [i0-1, i0+w] x [j0-1, j0+h] holds such cells (cached per geometry)
                 auto vit = march_variants.find(sm.geo);
@@ -247,8 +248,8 @@ static int prepare_plan(casimir_plan_t *P)
                     std::vector<int> vs((size_t)tx * ty, 0);
                     for (int tj = 0; tj < ty; ++tj)
                         for (int ti = 0; ti < tx; ++ti) {
-                            const int i0 = ti * MARCH_W, j0 = tj * MARCH_H;
-                            const int w = std::min(MARCH_W, hs.nx - i0), h = std::min(MARCH_H, hs.ny - j0);
+                            const int i0 = ti * MARCH_W, j0 = tj * rows;
+                            const int w = std::min(MARCH_W, hs.nx - i0), h = std::min(rows, hs.ny - j0);
                             bool pml = false, lor = false;
                             for (int jj = j0 - 1; jj <= j0 + h; ++jj) {
                                 const int j = wrapc(jj, hs.ny);
@@ -267,8 +268,8 @@ static int prepare_plan(casimir_plan_t *P)
                 for (const Entry &e : sm.meas) {
                     if (!hs.cplx && inA(e.arr) != inA(sarr)) continue;   // contributes i * real: no real part
                     int i = (int)(e.idx % hs.nx), j = (int)(e.idx / hs.nx);
-                    int ti = i / MARCH_W, tj = j / MARCH_H;
-                    int loc = (j - tj * MARCH_H) * MARCH_W + (i - ti * MARCH_W);
+                    int ti = i / MARCH_W, tj = j / rows;
+                    int loc = (j - tj * rows) * MARCH_W + (i - ti * MARCH_W);
                     auto &b = bucket[(size_t)tj * tx + ti];
                     if (e.re != 0.0 || !hs.cplx) b.push_back(DevEnt{loc | (e.arr << 16), 0, e.re});
                     if (hs.cplx && e.im != 0.0) b.push_back(DevEnt{loc | ((e.arr | 8) << 16), 0, e.im});
@@ -279,17 +280,13 @@ static int prepare_plan(casimir_plan_t *P)
                 for (int tj = 0; tj < ty; ++tj)
                     for (int ti = 0; ti < tx; ++ti) {
                         auto &b = bucket[(size_t)tj * tx + ti];
-                        P->tilesM.push_back(HostTile{(int)s, ti * MARCH_W, tj * MARCH_H, (int)P->entsM.size(), (int)b.size(),
+                        P->tilesM.push_back(HostTile{(int)s, ti * MARCH_W, tj * rows, (int)P->entsM.size(), (int)b.size(),
                                                      vit->second[(size_t)tj * tx + ti]});
                         P->entsM.insert(P->entsM.end(), b.begin(), b.end());
                     }
                 hs.nent = (int)P->entsM.size() - hs.ent0;
             }
-            static const bool line3_env = [] {
-                const char *e = std::getenv("CASIMIR_LINE3");
-                return !(e && std::atoi(e) == 0);
-            }();
-            hs.line3 = (!hs.march && D.prob.dims == 3 && line3_env && 12 * N < ((int64_t)1 << 32)) ? 1 : 0;
+            hs.line3 = (!hs.march && D.prob.dims == 3 && P->opts.kernel_3d == 1 && 12 * N < ((int64_t)1 << 32)) ? 1 : 0;
             if (hs.line3) {
                 // tiles of 32 x cells by LINES3 (y, z) lines; entries bucketed per tile
                 const int64_t nl = (int64_t)hs.ny * hs.nz;
@@ -348,12 +345,8 @@ static int prepare_plan(casimir_plan_t *P)
     }
     P->field_elems = off;
     {
-        static const int k_env = [] {
-            const char *e = std::getenv("CASIMIR_STEP2D_K");
-            return e ? std::atoi(e) : 2;
-        }();
         bool all2d = !P->sims.empty() && !P->sims[0].full;
-        P->k2d = (all2d && k_env == 2) ? 2 : 1;
+        P->k2d = (all2d && P->opts.steps_per_launch == 2) ? 2 : 1;
         P->launches = P->k2d == 2 ? (D.prob.n_steps + 1) / 2 : D.prob.n_steps;
     }
     P->table_bytes = (int64_t)(align256(P->ents2.size() * sizeof(DevEnt)) + align256(P->rowptr2.size() * sizeof(int)) +
@@ -596,6 +589,7 @@ void make_sim6(const casimir_plan_t *P, char *blk, double *acc, double *tail, in
     d->kzA = hs.kzA;
     d->kzB = hs.kzB;
     d->fhalf = hs.march ? hs.fhalf : 0;
+    d->tile_rows = P->opts.march_rows;
     d->psi_half = hs.march ? hs.psi_half : 0;
     d->lor_half = hs.march ? hs.lor_half : 0;
 }
@@ -1109,14 +1103,40 @@ int casimir_ctx_kernel_stats(casimir_ctx_t *c, double *step_ms, int64_t *launche
     return CASIMIR_OK;
 }
 
-int casimir_plan(casimir_ctx_t *c, const casimir_problem *p, casimir_plan_t **out)
+// Options with defaults filled in (the environment variables CASIMIR_STEP2D_K and
+// CASIMIR_LINE3 set the defaults of steps_per_launch and kernel_3d, for A/B runs).
+static int resolve_options(const casimir_plan_options *in, casimir_plan_options *out)
 {
-    if (!p || !out) return fail(CASIMIR_EINVAL, "NULL argument");
+    static const int k_env = [] {
+        const char *e = std::getenv("CASIMIR_STEP2D_K");
+        return e ? std::atoi(e) : 2;
+    }();
+    static const int l_env = [] {
+        const char *e = std::getenv("CASIMIR_LINE3");
+        return (e && std::atoi(e) == 0) ? 2 : 1;
+    }();
+    casimir_plan_options o{};
+    if (in) o = *in;
+    if (o.steps_per_launch == 0) o.steps_per_launch = k_env == 1 ? 1 : 2;
+    if (o.march_rows == 0) o.march_rows = MARCH_H;
+    if (o.kernel_3d == 0) o.kernel_3d = l_env;
+    if ((o.steps_per_launch != 1 && o.steps_per_launch != 2) || o.march_rows < 1 || o.march_rows > MARCH_H_MAX ||
+        (o.kernel_3d != 1 && o.kernel_3d != 2))
+        return fail(CASIMIR_EINVAL, "plan options out of range");
+    o.reserved = 0;
+    *out = o;
+    return CASIMIR_OK;
+}
+
+static int make_plan(casimir_ctx_t *c, const casimir_problem *p, const casimir_plan_options *opts, casimir_plan_t **out)
+{
     *out = nullptr;
     auto *P = new casimir_plan_t();
     P->ctx = c;
+    int rc = resolve_options(opts, &P->opts);
+    if (rc) { delete P; return rc; }
     std::string err;
-    int rc = build_plan(p, &P->data, &err);
+    rc = build_plan(p, &P->data, &err);
     if (rc) { delete P; return fail(rc, err); }
     rc = prepare_plan(P);
     if (rc) { delete P; return rc; }
@@ -1125,6 +1145,112 @@ int casimir_plan(casimir_ctx_t *c, const casimir_problem *p, casimir_plan_t **ou
         return fail(CASIMIR_ENOMEM, "plan needs more device memory than the context budget");
     }
     *out = P;
+    return CASIMIR_OK;
+}
+
+// Problem class for autotuning: what decides which schedule is fastest.
+static std::string tune_key(const casimir_problem &p)
+{
+    bool pml = false, lor = false, cplx = false;
+    for (int a = 0; a < p.dims; ++a) pml |= p.bc[a] == CASIMIR_BC_PML;
+    for (int o = 0; o < p.n_objects; ++o) lor |= p.objects[o].kind == CASIMIR_MAT_LORENTZ;
+    for (int k = 0; k < p.n_kpoints; ++k)
+        for (int a = 0; a < p.dims; ++a) cplx |= p.bc[a] == CASIMIR_BC_PERIODIC && p.kpoints[k].k[a] != 0.0;
+    auto bucket = [](int n) { int b = 0; while ((1 << b) < n) ++b; return b; };
+    std::string k = std::to_string(p.dims) + (p.polarization == CASIMIR_POL_FULL ? "F" : "T") + std::to_string(p.precision) +
+                    std::to_string(p.coords) + (pml ? "p" : "") + (lor ? "l" : "") + (cplx ? "c" : "");
+    for (int a = 0; a < 3; ++a) k += "," + std::to_string(bucket(p.n[a]));
+    return k;
+}
+
+// Time each candidate on the problem cut to 128 steps; the fastest per cell-update wins.
+static casimir_plan_options autotune(casimir_ctx *c, const casimir_problem &p)
+{
+    casimir_plan_options dflt{};
+    resolve_options(nullptr, &dflt);
+    std::vector<casimir_plan_options> cand;
+    if (p.dims == 3) {
+        cand = {dflt, dflt};
+        cand[0].kernel_3d = 1;
+        cand[1].kernel_3d = 2;
+    } else if (p.polarization == CASIMIR_POL_FULL) {
+        for (int rows : {32, 16, 64}) {
+            casimir_plan_options o = dflt;
+            o.march_rows = rows;
+            cand.push_back(o);
+        }
+    } else {
+        cand = {dflt, dflt};
+        cand[0].steps_per_launch = 2;
+        cand[1].steps_per_launch = 1;
+    }
+    const std::string key = tune_key(p);
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        auto it = c->tuned.find(key);
+        if (it != c->tuned.end()) return it->second;
+        if (!c->active.empty() || !c->queue.empty() || c->sync_busy) return dflt;   // never disturb running work
+    }
+    casimir_problem trial = p;
+    trial.n_steps = std::min(p.n_steps, 128);
+    // the context's statistics belong to its user: restore them after the trials
+    const double ms0 = c->step_ms;
+    const int64_t l0 = c->step_launches, cu0 = c->cell_updates;
+    double best_t = 0;
+    casimir_plan_options best = dflt;
+    bool any = false;
+    for (const casimir_plan_options &o : cand) {
+        casimir_plan_t *tp = nullptr;
+        if (make_plan(c, &trial, &o, &tp) != CASIMIR_OK) continue;
+        const double m_before = c->step_ms;
+        const int64_t cu_before = c->cell_updates;
+        double F[3];
+        int rc = casimir_run(tp, F, nullptr, nullptr);
+        const double dms = c->step_ms - m_before;
+        const int64_t dcu = c->cell_updates - cu_before;
+        casimir_plan_destroy(tp);
+        if (rc != CASIMIR_OK || dcu <= 0) continue;
+        const double t = dms / (double)dcu;
+        if (!any || t < best_t) { best_t = t; best = o; any = true; }
+    }
+    c->step_ms = ms0;
+    c->step_launches = l0;
+    c->cell_updates = cu0;
+    if (any) {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->tuned[key] = best;
+    }
+    return best;
+}
+
+int casimir_plan_ex(casimir_ctx_t *c, const casimir_problem *p, const casimir_plan_options *opts, casimir_plan_t **out)
+{
+    if (!p || !out) return fail(CASIMIR_EINVAL, "NULL argument");
+    return make_plan(c, p, opts, out);
+}
+
+int casimir_plan(casimir_ctx_t *c, const casimir_problem *p, casimir_plan_t **out)
+{
+    if (!p || !out) return fail(CASIMIR_EINVAL, "NULL argument");
+    if (c && c->autotune) {
+        const casimir_plan_options o = autotune(c, *p);
+        return make_plan(c, p, &o, out);
+    }
+    return make_plan(c, p, nullptr, out);
+}
+
+int casimir_plan_get_options(const casimir_plan_t *P, casimir_plan_options *opts)
+{
+    if (!P || !opts) return fail(CASIMIR_EINVAL, "NULL argument");
+    *opts = P->opts;
+    return CASIMIR_OK;
+}
+
+int casimir_ctx_set_autotune(casimir_ctx_t *c, int on)
+{
+    if (!c) return fail(CASIMIR_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->autotune = on ? 1 : 0;
     return CASIMIR_OK;
 }
 

@@ -90,6 +90,7 @@ struct casimir_ctx;
 struct casimir_plan {
     casimir_ctx *ctx = nullptr;
     PlanData data;
+    casimir_plan_options opts{};      // resolved execution options (no zero fields)
     int fp64 = 0;
     size_t rsize = 4;
     std::vector<HostSim> sims;
@@ -203,6 +204,9 @@ struct casimir_ctx {
     bool worker_on = false;
     bool stop = false;
     std::atomic<int> sync_busy{0};
+    // autotuning: chosen options per problem class
+    int autotune = 0;
+    std::map<std::string, casimir_plan_options> tuned;
 };
 
 

@@ -76,6 +76,8 @@ struct DevSim6 {
     // march kernel (two-dimensional runs): elements from buffer 0 to buffer 1 of the
     // ping-pong fields, psi and Lorentz planes (step n reads buffer (n-1)&1, writes n&1)
     int64_t fhalf, psi_half, lor_half;
+    int tile_rows;         // march kernel: rows per strip tile (<= MARCH_H_MAX)
+    int pad6;
 };
 
 struct DevEnt6 {
@@ -109,7 +111,8 @@ void launch_full(int fp64, int cplx, int dims, const DevSim6 *sims, const DevTil
 // bit 19 set for the weight of the imaginary part (complex fields).  variant: 1 = CPML planes
 // present, + 2 = Lorentz planes present.
 constexpr int MARCH_W = 30;
-constexpr int MARCH_H = 32;
+constexpr int MARCH_H = 32;       // default rows per strip tile
+constexpr int MARCH_H_MAX = 64;   // largest tile height the planner builds (loc stays below 2^16)
 void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles,
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 // The same march on a cylindrical (r, z) lattice (x = r from the axis, y = z), fields ~ exp(i m phi)

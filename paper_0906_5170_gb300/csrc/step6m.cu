@@ -137,7 +137,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
 
     const int i0 = t.i0;
     const int w = min(MARCH_W, nx - i0);
-    const int h = min(MARCH_H, ny - t.j0);
+    const int h = min(S.tile_rows, ny - t.j0);
     const int col = ((i0 - 1 + lane) % nx + nx) % nx;     // lane 0: left halo, lane w + 1: right halo
     const bool own = lane >= 1 && lane <= w;
     const bool wrapR = col == nx - 1;                     // the right neighbour lies across the x wrap

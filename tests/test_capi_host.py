@@ -109,3 +109,20 @@ def test_plan_rejects_invalid_cylindrical_problems(mutate):
     with pytest.raises(pk.CasimirError) as e:
         pk.Plan(p)
     assert e.value.code == -1
+
+
+def test_plan_options_defaults_and_explicit():
+    p = W.piston_small()
+    assert pk.Plan(p).options() == {"steps_per_launch": 2, "march_rows": 32, "kernel_3d": 1}
+    o = pk.Plan(p, options={"steps_per_launch": 1, "march_rows": 16}).options()
+    assert o == {"steps_per_launch": 1, "march_rows": 16, "kernel_3d": 1}
+    for bad in ({"steps_per_launch": 3}, {"march_rows": 65}, {"kernel_3d": 5}):
+        with pytest.raises(pk.CasimirError) as e:
+            pk.Plan(p, options=bad)
+        assert e.value.code == -1
+    # the simulation list does not depend on the options
+    q = W.config3_waveguides(0.5, resolution=8, n_cells=48, pml_units=0.75, n_harm=2, n_steps=20,
+                             k_points=[{"k": [0, 0, 0.5], "weight": 1.0}])
+    a = pk.Plan(q).sims()
+    b = pk.Plan(q, options={"march_rows": 64}).sims()
+    assert np.array_equal(a, b)

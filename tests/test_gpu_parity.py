@@ -361,3 +361,48 @@ def test_cylindrical_plain_path_and_mixed_batch(ctx):
     t1, t2 = ctx.plan(p).submit(), ctx.plan(q).submit()
     assert np.allclose(t1.force(-1)[0], Fb, rtol=1e-12, atol=0)
     assert np.allclose(t2.force(-1)[0], Fq, rtol=1e-12, atol=0)
+
+
+# ---- execution options and the autotuner ---------------------------------------------------
+
+def test_execution_options_do_not_change_results(ctx):
+    cases = [
+        (W.piston_small(n_steps=300, precision="fp64"), [{"steps_per_launch": 1}, {"steps_per_launch": 2}]),
+        (_waveguides_small("fp64", (0.0, 1.3)), [{"march_rows": 16}, {"march_rows": 32}, {"march_rows": 64}]),
+        (W.config4_sphere_notch(0.4, seed=3, resolution=6, n_cells=24, pml_cells=4, n_harm=1, n_steps=60,
+                                precision="fp64", substrate_top=1.0), [{"kernel_3d": 1}, {"kernel_3d": 2}]),
+        (W.cylinder_piston(12, [0, 1, 2], t_max=4.0), [{"march_rows": 16}, {"march_rows": 64}]),
+    ]
+    for p, opts in cases:
+        res = []
+        for o in opts:
+            pl = ctx.plan(p, options=o)
+            assert all(pl.options()[k] == v for k, v in o.items())
+            res.append(pl.run(per_sim=True)[1])
+        scale = np.sum(np.abs(res[0]))
+        for r in res[1:]:
+            assert np.allclose(r, res[0], rtol=1e-10, atol=1e-14 * scale)
+
+
+def test_autotune_picks_caches_and_keeps_results(pk, ctx):
+    c = pk.Context(0)
+    try:
+        c.set_autotune(True)
+        p = W.piston_small(n_steps=300, precision="fp64")
+        pl = c.plan(p)
+        o = pl.options()
+        assert o["steps_per_launch"] in (1, 2)
+        # a problem of the same class reuses the choice
+        assert c.plan(W.piston_small(h=0.55, n_steps=300, precision="fp64")).options() == o
+        F, per, _ = pl.run(per_sim=True)
+        _, ref, _ = ctx.plan(p).run(per_sim=True)
+        assert np.allclose(per, ref, rtol=1e-10, atol=1e-14 * np.sum(np.abs(ref)))
+        # six-component class: one of the candidate tile heights
+        q = _waveguides_small("fp32", (0.0, 1.3))
+        assert c.plan(q).options()["march_rows"] in (16, 32, 64)
+        # the trials leave the user's kernel statistics alone
+        c.kernel_stats(reset=True)
+        c.plan(W.cylinder_piston(10, [0, 1], t_max=2.0))
+        assert c.kernel_stats()[0] == 0.0
+    finally:
+        c.close()
