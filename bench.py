@@ -256,6 +256,34 @@ def measure_cylinder(pk, ctx):
     return out
 
 
+def oracle_check_problems():
+    """Small problems whose GPU forces the bench reports with their error against the FP64 oracle:
+    a config-2 sample (first sidewall spacing, 2 harmonics, 1000 steps) in FP32 and FP64 mode, the
+    first serving request of each kind, and a coarse cylindrical piston."""
+    import workloads as W
+    probs = {}
+    for prec in ("fp32", "fp64"):
+        probs[f"config2_h{W.config2_heights()[0]:.3f}_n2_T1000_{prec}"] = W.config2_piston(
+            W.config2_heights()[0], n_harm=2, n_steps=1000, precision=prec)
+    for _, p in W.serving_requests(0, n_requests=12, rate=50.0, scale=0.15):
+        key = "serving_" + p.get("kind", "?")
+        if key not in probs:
+            probs[key] = p
+    probs["cylinder_blocks_h0.5_res10"] = W.cylinder_blocks(0.5, resolution=10, t_max=20.0)
+    return probs
+
+
+def oracle_reference(probs):
+    """CPU-baseline leg: the FP64 oracle's force and sum of |per-sim contributions| per problem."""
+    import numpy as np
+    import oracle
+    out = {}
+    for name, p in probs.items():
+        F, parts, _ = oracle.force(p, return_parts=True)
+        out[name] = (float(F), float(np.sum(np.abs(parts))))
+    return out
+
+
 def cpu_baseline(budget_s=15.0):
     """The FP64 oracle on a bounded sample of the workload: simulations of the
     h = 0.5 geometry for a shortened number of steps, one per host core."""
@@ -476,6 +504,25 @@ def main():
         others["basis_point_vs_cosine"] = measure_basis(pk, ctx)
         others["cylinder_piston"] = measure_cylinder(pk, ctx)
 
+    check = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # every check problem's GPU force next to the FP64 oracle (the oracle runs in this leg only)
+        try:
+            probs = oracle_check_problems()
+            ref = oracle_reference(probs)
+            check = {}
+            for name, p in probs.items():
+                F = ctx.plan(p).run()[0][p["force_axis"]]
+                Fo, scale = ref[name]
+                check[name] = {"precision": p.get("precision", "fp64"), "force": float(F), "oracle": Fo,
+                               "rel_err": abs(F - Fo) / abs(Fo), "err_over_sum_abs": abs(F - Fo) / scale}
+            cases = list(check.values())
+            for prec in ("fp32", "fp64"):
+                errs = [v["rel_err"] for v in cases if v["precision"] == prec]
+                check[f"max_rel_err_{prec}"] = max(errs) if errs else None
+        except Exception as e:  # the oracle is test infrastructure; report, do not fail the bench
+            check = {"error": repr(e)}
+
     cb = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
@@ -499,7 +546,7 @@ def main():
             "forces_per_s": forces_per_s,
             "latency_ms": {"p50": lat_sorted[len(lat) // 2], "p99": lat_sorted[min(len(lat) - 1, int(0.99 * len(lat)))]},
             "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "serving": serving, "other_configs": others,
-            "autotune": autotune,
+            "autotune": autotune, "oracle_check": check,
             "gpu_launches": int(launches + 3 * n_forces * args.steps),
             "clocks": clk,
         }
