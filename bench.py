@@ -258,10 +258,12 @@ def measure_cylinder(pk, ctx):
 
 def oracle_check_problems():
     """Small problems whose GPU forces the bench reports with their error against the FP64 oracle:
-    a config-2 sample (first sidewall spacing, 2 harmonics, 1000 steps) in FP32 and FP64 mode, the
-    first serving request of each kind, and a coarse cylindrical piston."""
+    the full config-1 plates (FP64), a config-2 sample (first sidewall spacing, 2 harmonics, 1000
+    steps) in FP32 and FP64 mode, the first serving request of each kind, and a coarse cylindrical
+    piston.  err_over_sum_abs divides by the sum of |per-simulation contributions|, the scale of the
+    cancellation the force results from."""
     import workloads as W
-    probs = {}
+    probs = {"config1_plates_fp64_full": W.config1_plates()}
     for prec in ("fp32", "fp64"):
         probs[f"config2_h{W.config2_heights()[0]:.3f}_n2_T1000_{prec}"] = W.config2_piston(
             W.config2_heights()[0], n_harm=2, n_steps=1000, precision=prec)
