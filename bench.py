@@ -117,13 +117,14 @@ def workload_problems(n_steps=20000, n_harm=40):
     return [W.config2_piston(h, n_steps=n_steps, n_harm=n_harm) for h in W.config2_heights()]
 
 
-def serving_trial(pk, ctx, n_requests=12, rate=50.0, scale=0.15, seed=0, plain=False):
+def serving_trial(pk, ctx, n_requests=12, rate=50.0, scale=0.15, seed=0, plain=False, trace=None):
     """Poisson arrivals of the seeded serving mix (2D pistons/waveguides, Bloch gratings, 3D
-    spheres, grid sides scaled by `scale`).  Batched: every request is submitted at its arrival
-    time and joins the running batch.  Plain: requests run one after another through the
-    unbatched path.  Latency = completion - arrival."""
+    spheres, grid sides scaled by `scale`), or the given trace of (arrival s, problem).  Batched:
+    every request is submitted at its arrival time and joins the running batch.  Plain: requests
+    run one after another through the unbatched path.  Latency = completion - arrival."""
     import workloads as W
-    trace = W.serving_requests(seed, n_requests=n_requests, rate=rate, scale=scale)
+    if trace is None:
+        trace = W.serving_requests(seed, n_requests=n_requests, rate=rate, scale=scale)
     plans = [ctx.plan(p) for _, p in trace]
     done = [None] * len(trace)
     t0 = time.perf_counter()
@@ -156,6 +157,23 @@ def serving_trial(pk, ctx, n_requests=12, rate=50.0, scale=0.15, seed=0, plain=F
     return {"forces_per_s": len(trace) / makespan, "p50_ms": lat[len(lat) // 2],
             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "makespan_s": makespan,
             "requests": len(trace), "mix": kinds}
+
+
+def serving_load_sweep(pk, ctx, scale=0.15):
+    """Open loop: the first 200 requests of the seed-0 trace at 50 req/s (overload: the throughput
+    is the capacity, latencies include queueing).  Then the first 60 requests replayed at 0.25,
+    0.5 and 0.8 of that capacity (arrival times rescaled), where p50/p99 are steady-state."""
+    import workloads as W
+    trace = W.serving_requests(0, n_requests=200, rate=50.0, scale=scale)
+    full = serving_trial(pk, ctx, trace=trace)
+    cap = full["forces_per_s"]
+    sweep = []
+    for f in (0.25, 0.5, 0.8):
+        lam = f * cap
+        r = serving_trial(pk, ctx, trace=[(t * 50.0 / lam, p) for t, p in trace[:60]])
+        sweep.append({"load": f, "rate_per_s": lam, **{k: r[k] for k in ("forces_per_s", "p50_ms", "p99_ms")}})
+    return {"open_loop_200_at_50_per_s": {k: full[k] for k in ("forces_per_s", "p50_ms", "p99_ms", "makespan_s", "mix")},
+            "capacity_forces_per_s": cap, "load_sweep": sweep}
 
 
 def measure_configs(pk, ctx, peak):
@@ -387,6 +405,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=12)
     ap.add_argument("--no-configs", action="store_true")
+    ap.add_argument("--no-serving-sweep", action="store_true", help="skip the 200-request trace and the load sweep")
     ap.add_argument("--no-autotune", action="store_true", help="default execution options instead of autotuned ones")
     ap.add_argument("--profile-case", choices=["piston", "waveguides", "sphere3d", "grating", "cylinder"], default=None,
                     help="run one mid-size case for kernel profiling instead of the benchmark")
@@ -494,11 +513,18 @@ def main():
 
     serving = None
     if not args.no_serving:
-        batched = serving_trial(pk, ctx, n_requests=args.serving_requests)
-        plain = serving_trial(pk, ctx, n_requests=args.serving_requests, plain=True)
+        # the serving context: admission under a 150 GB HBM budget, schedules autotuned per class
+        sctx = pk.Context(local, hbm_budget_bytes=150 * 10**9, stream=stream.cuda_stream)
+        sctx.set_autotune(not args.no_autotune)
+        batched = serving_trial(pk, sctx, n_requests=args.serving_requests)
+        plain = serving_trial(pk, sctx, n_requests=args.serving_requests, plain=True)
         serving = {"trace": "seed 0, Poisson 50 req/s, serving mix with grid sides x0.15",
+                   "hbm_budget_bytes": 150 * 10**9,
                    "batched": batched, "plain": plain,
                    "forces_per_s_ratio": batched["forces_per_s"] / plain["forces_per_s"]}
+        if not args.no_serving_sweep:
+            serving.update(serving_load_sweep(pk, sctx))
+        sctx.close()
 
     others = None
     if not args.no_configs:
