@@ -111,9 +111,13 @@ k_line3(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles,
     const int line_end = min(t.j0 + LINES3, ny * nz);
     const bool inx = S.pml_d[0] > 0 && (xc < S.pml_d[0] || xc >= nx - S.pml_d[0]);
     const int cf = CPLX ? 2 : 1;
+    const int dX = S.pml_d[0], dY = S.pml_d[1], dZ = S.pml_d[2];
+    // psi planes of axis a start at psi + psi_off[a] and lie cf * slab[a] elements apart
+    // (32-bit offsets: the planner sends only runs with 12 N < 2^32 here)
+    const unsigned pstride[3] = {(unsigned)(cf * S.slab[0]), (unsigned)(cf * S.slab[1]), (unsigned)(cf * S.slab[2])};
     // stretched difference along axis ax at slab index si: psi' = b psi + c d, d / kappa + psi'
     auto stretch = [&](V d, int ax, const R *pr, int plane, unsigned si, bool wr) -> V {
-        R *ps = psi + S.psi_off[ax] + (size_t)plane * cf * S.slab[ax];
+        R *ps = psi + S.psi_off[ax] + plane * pstride[ax];
         V p;
         if constexpr (CPLX) p = V(ps[si], ps[S.slab[ax] + si]);
         else p = V(ps[si]);
@@ -124,29 +128,23 @@ k_line3(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles,
         }
         return d * pr[2] + p;
     };
+    // (y, z) of this warp's first line, then advanced by WARPS3 lines per iteration (no division in the loop)
+    int y = (t.j0 + warp) % ny, z = (t.j0 + warp) / ny;
 
 #pragma unroll kUnroll3
     for (int q = 0; q < LPW3; ++q) {
         const int line = t.j0 + warp + q * WARPS3;
+        if (q > 0) {
+            y += WARPS3;
+            while (y >= ny) { y -= ny; ++z; }
+        }
         if (line >= line_end) continue;                 // uniform over the warp
-        const int y = line % ny, z = line / ny;
         const unsigned g = (unsigned)line * sy + (unsigned)xc;
-        const int m = mat[g];
-        const R *cm = coef + 6 * m;
-        const int dX = S.pml_d[0], dY = S.pml_d[1], dZ = S.pml_d[2];
         const bool iny = dY > 0 && (y < dY || y >= ny - dY);
         const bool inz = dZ > 0 && (z < dZ || z >= nz - dZ);
-        // slab indices of this cell for the three axes (used only inside the slabs)
-        const int sxp = xc < dX ? xc : xc - (nx - 2 * dX);
-        const unsigned six = ((unsigned)line) * (unsigned)(2 * dX) + (unsigned)sxp;
-        const int syp = y < dY ? y : y - (ny - 2 * dY);
-        const unsigned siy = ((unsigned)z * (unsigned)(2 * dY) + (unsigned)syp) * sy + (unsigned)xc;
-        const int szp = z < dZ ? z : z - (nz - 2 * dZ);
-        const unsigned siz = ((unsigned)szp * (unsigned)ny + (unsigned)y) * sy + (unsigned)xc;
-        const R *prx = pml + S.pml_off[0], *pry = pml + S.pml_off[1], *prz = pml + S.pml_off[2];
         if (updE) {
-            // backward neighbours: x by shuffle except at the segment edge and the wrap (loaded
-            // first, together with the row loads), y and z by row loads
+            // every load of the cell first: own E and H, backward neighbours (x by shuffle except at the
+            // segment edge and the wrap), material
             const bool edge = lane == 0 || x == 0;
             V hyl_e, hzl_e;
             if (edge) {
@@ -155,38 +153,50 @@ k_line3(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles,
                 hzl_e = ld3<R, CPLX>(F, 5, N, gl);
             }
             const V hx = ld3<R, CPLX>(F, 3, N, g), hy = ld3<R, CPLX>(F, 4, N, g), hz = ld3<R, CPLX>(F, 5, N, g);
+            const unsigned gy = y == 0 ? g + (unsigned)(ny - 1) * sy : g - sy;
+            V hxy = ld3<R, CPLX>(F, 3, N, gy), hzy = ld3<R, CPLX>(F, 5, N, gy);
+            const unsigned gz = z == 0 ? g + (unsigned)(nz - 1) * sz : g - sz;
+            V hxz = ld3<R, CPLX>(F, 3, N, gz), hyz = ld3<R, CPLX>(F, 4, N, gz);
+            const V e3[3] = {ld3<R, CPLX>(F, 0, N, g), ld3<R, CPLX>(F, 1, N, g), ld3<R, CPLX>(F, 2, N, g)};
+            const int m = mat[g];
             V hyl = hy.up(), hzl = hz.up();
             if (edge) {
                 hyl = x == 0 ? hyl_e.ph((R)S.bre[0], -(R)S.bim[0]) : hyl_e;
                 hzl = x == 0 ? hzl_e.ph((R)S.bre[0], -(R)S.bim[0]) : hzl_e;
             }
-            const unsigned gy = y == 0 ? g + (unsigned)(ny - 1) * sy : g - sy;
-            V hxy = ld3<R, CPLX>(F, 3, N, gy), hzy = ld3<R, CPLX>(F, 5, N, gy);
             if (y == 0) { hxy = hxy.ph((R)S.bre[1], -(R)S.bim[1]); hzy = hzy.ph((R)S.bre[1], -(R)S.bim[1]); }
-            const unsigned gz = z == 0 ? g + (unsigned)(nz - 1) * sz : g - sz;
-            V hxz = ld3<R, CPLX>(F, 3, N, gz), hyz = ld3<R, CPLX>(F, 4, N, gz);
             if (z == 0) { hxz = hxz.ph((R)S.bre[2], -(R)S.bim[2]); hyz = hyz.ph((R)S.bre[2], -(R)S.bim[2]); }
             V dyHz = (hz - hzy) * idx, dzHy = (hy - hyz) * idx, dzHx = (hx - hxz) * idx;
             V dxHz = (hz - hzl) * idx, dxHy = (hy - hyl) * idx, dyHx = (hx - hxy) * idx;
             if (inx) {
+                const R *prx = pml + S.pml_off[0];
                 const R pr[3] = {prx[xc], prx[nx + xc], prx[2 * nx + xc]};
+                const int sxp = xc < dX ? xc : xc - (nx - 2 * dX);
+                const unsigned six = (unsigned)line * (unsigned)(2 * dX) + (unsigned)sxp;
                 dxHz = stretch(dxHz, 0, pr, 0, six, valid);    // E_y
                 dxHy = stretch(dxHy, 0, pr, 1, six, valid);    // E_z
             }
             if (iny) {
+                const R *pry = pml + S.pml_off[1];
                 const R pr[3] = {pry[y], pry[ny + y], pry[2 * ny + y]};
+                const int syp = y < dY ? y : y - (ny - 2 * dY);
+                const unsigned siy = ((unsigned)z * (unsigned)(2 * dY) + (unsigned)syp) * sy + (unsigned)xc;
                 dyHx = stretch(dyHx, 1, pr, 0, siy, valid);    // E_z
                 dyHz = stretch(dyHz, 1, pr, 1, siy, valid);    // E_x
             }
             if (inz) {
+                const R *prz = pml + S.pml_off[2];
                 const R pr[3] = {prz[z], prz[nz + z], prz[2 * nz + z]};
+                const int szp = z < dZ ? z : z - (nz - 2 * dZ);
+                const unsigned siz = ((unsigned)szp * (unsigned)ny + (unsigned)y) * sy + (unsigned)xc;
                 dzHy = stretch(dzHy, 2, pr, 0, siz, valid);    // E_x
                 dzHx = stretch(dzHx, 2, pr, 1, siz, valid);    // E_y
             }
             const V c3[3] = {dyHz - dzHy, dzHx - dxHz, dxHy - dyHx};
+            const R *cm = coef + 6 * m;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const V e = ld3<R, CPLX>(F, k, N, g);
+                const V e = e3[k];
                 V en = e * a + c3[k] * (b * cm[k]);
                 if (P) {
                     const R *l4 = lc + 12 * m + 4 * k;
@@ -204,8 +214,7 @@ k_line3(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles,
                 if (valid) st3<R, CPLX>(F, k, N, g, en);
             }
         } else {
-            // forward neighbours: x by shuffle except at the segment edge and the wrap (loaded
-            // first, together with the row loads), y and z by row loads
+            // every load of the cell first: own E and H, forward neighbours, material
             const bool edge = lane == 31 || x >= nx - 1;
             V eyr_e, ezr_e;
             if (edge) {
@@ -214,40 +223,50 @@ k_line3(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles,
                 ezr_e = ld3<R, CPLX>(F, 2, N, gr);
             }
             const V ex = ld3<R, CPLX>(F, 0, N, g), ey = ld3<R, CPLX>(F, 1, N, g), ez = ld3<R, CPLX>(F, 2, N, g);
+            const unsigned gy = y == ny - 1 ? g - (unsigned)(ny - 1) * sy : g + sy;
+            V exy = ld3<R, CPLX>(F, 0, N, gy), ezy = ld3<R, CPLX>(F, 2, N, gy);
+            const unsigned gz = z == nz - 1 ? g - (unsigned)(nz - 1) * sz : g + sz;
+            V exz = ld3<R, CPLX>(F, 0, N, gz), eyz = ld3<R, CPLX>(F, 1, N, gz);
+            const V h3[3] = {ld3<R, CPLX>(F, 3, N, g), ld3<R, CPLX>(F, 4, N, g), ld3<R, CPLX>(F, 5, N, g)};
+            const int m = mat[g];
             V eyr = ey.dn(), ezr = ez.dn();
             if (edge) {
                 eyr = xc == nx - 1 ? eyr_e.ph((R)S.bre[0], (R)S.bim[0]) : eyr_e;
                 ezr = xc == nx - 1 ? ezr_e.ph((R)S.bre[0], (R)S.bim[0]) : ezr_e;
             }
-            const unsigned gy = y == ny - 1 ? g - (unsigned)(ny - 1) * sy : g + sy;
-            V exy = ld3<R, CPLX>(F, 0, N, gy), ezy = ld3<R, CPLX>(F, 2, N, gy);
             if (y == ny - 1) { exy = exy.ph((R)S.bre[1], (R)S.bim[1]); ezy = ezy.ph((R)S.bre[1], (R)S.bim[1]); }
-            const unsigned gz = z == nz - 1 ? g - (unsigned)(nz - 1) * sz : g + sz;
-            V exz = ld3<R, CPLX>(F, 0, N, gz), eyz = ld3<R, CPLX>(F, 1, N, gz);
             if (z == nz - 1) { exz = exz.ph((R)S.bre[2], (R)S.bim[2]); eyz = eyz.ph((R)S.bre[2], (R)S.bim[2]); }
             V dyEz = (ezy - ez) * idx, dzEy = (eyz - ey) * idx, dzEx = (exz - ex) * idx;
             V dxEz = (ezr - ez) * idx, dxEy = (eyr - ey) * idx, dyEx = (exy - ex) * idx;
             if (inx) {
+                const R *prx = pml + S.pml_off[0];
                 const R pr[3] = {prx[3 * nx + xc], prx[4 * nx + xc], prx[5 * nx + xc]};
+                const int sxp = xc < dX ? xc : xc - (nx - 2 * dX);
+                const unsigned six = (unsigned)line * (unsigned)(2 * dX) + (unsigned)sxp;
                 dxEz = stretch(dxEz, 0, pr, 2, six, valid);    // H_y
                 dxEy = stretch(dxEy, 0, pr, 3, six, valid);    // H_z
             }
             if (iny) {
+                const R *pry = pml + S.pml_off[1];
                 const R pr[3] = {pry[3 * ny + y], pry[4 * ny + y], pry[5 * ny + y]};
+                const int syp = y < dY ? y : y - (ny - 2 * dY);
+                const unsigned siy = ((unsigned)z * (unsigned)(2 * dY) + (unsigned)syp) * sy + (unsigned)xc;
                 dyEx = stretch(dyEx, 1, pr, 2, siy, valid);    // H_z
                 dyEz = stretch(dyEz, 1, pr, 3, siy, valid);    // H_x
             }
             if (inz) {
+                const R *prz = pml + S.pml_off[2];
                 const R pr[3] = {prz[3 * nz + z], prz[4 * nz + z], prz[5 * nz + z]};
+                const int szp = z < dZ ? z : z - (nz - 2 * dZ);
+                const unsigned siz = ((unsigned)szp * (unsigned)ny + (unsigned)y) * sy + (unsigned)xc;
                 dzEy = stretch(dzEy, 2, pr, 2, siz, valid);    // H_x
                 dzEx = stretch(dzEx, 2, pr, 3, siz, valid);    // H_y
             }
             const V c3[3] = {dyEz - dzEy, dzEx - dxEz, dxEy - dyEx};
+            const R *cm = coef + 6 * m;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const V h = ld3<R, CPLX>(F, 3 + k, N, g);
-                if (valid) st3<R, CPLX>(F, 3 + k, N, g, h * a - c3[k] * (b * cm[3 + k]));
-            }
+            for (int k = 0; k < 3; ++k)
+                if (valid) st3<R, CPLX>(F, 3 + k, N, g, h3[k] * a - c3[k] * (b * cm[3 + k]));
         }
     }
 
