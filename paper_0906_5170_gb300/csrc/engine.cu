@@ -140,6 +140,7 @@ static int prepare_plan(casimir_plan_t *P)
         int64_t N = (int64_t)hs.nx * hs.ny * hs.nz;
         P->cells += N;
         if (!hs.full) {
+            if (3 * N >= ((int64_t)1 << 32)) return fail(CASIMIR_EINVAL, "two-dimensional grid too large (3 N >= 2^32)");
             off += 6 * N;
             off = (off + 63) & ~(int64_t)63;
             int tx = (hs.nx + TILE_X - 1) / TILE_X, ty = (hs.ny + TILE_Y - 1) / TILE_Y;

@@ -84,7 +84,7 @@ k_step2d_t2(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
     const bool two = nA + 1 <= S.T;
 
     const int nx = S.nx, ny = S.ny;
-    const size_t N = (size_t)nx * ny;
+    const unsigned N = (unsigned)nx * (unsigned)ny;   // 32-bit offsets: 3 N < 2^32 (checked by the planner)
     const R *__restrict__ su = reinterpret_cast<const R *>(S.fields) + ((L - 1) & 1) * 3 * N;
     const R *__restrict__ svx = su + N;
     const R *__restrict__ svy = su + 2 * N;
@@ -113,7 +113,7 @@ k_step2d_t2(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
             // ---- sigma on u: v first ----
             // step A starts at row j0-1; its carried state needs row j0-2
             int jm2 = wrap2(j0 - 2, ny), jm1 = wrap2(j0 - 1, ny);
-            size_t g2 = (size_t)jm2 * nx + col, g1 = (size_t)jm1 * nx + col;
+            unsigned g2 = (unsigned)(jm2 * nx + col), g1 = (unsigned)(jm1 * nx + col);
             R u_cur = su[g1];
             int m2 = mat[g2];
             R vxA_prev = svx[g2] - hfA * coef[3 * m2 + 1] * (u_cur - su[g2]);
@@ -128,8 +128,8 @@ k_step2d_t2(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                     int r = rb + q;
                     if (r <= h) {
                         int j = wrap2(j0 + r, ny);
-                        size_t g = (size_t)j * nx + col;
-                        un[q] = su[(size_t)wrap2(j0 + r + 1, ny) * nx + col];
+                        unsigned g = (unsigned)(j * nx + col);
+                        un[q] = su[(unsigned)(wrap2(j0 + r + 1, ny) * nx + col)];
                         vx[q] = svx[g];
                         vy[q] = svy[g];
                         mt[q] = mat[g];
@@ -149,7 +149,7 @@ k_step2d_t2(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                     if (!two) {
                         if (r >= 0 && r < h) {
                             if (store) {
-                                size_t g = (size_t)(j0 + r) * nx + col;
+                                unsigned g = (unsigned)((j0 + r) * nx + col);
                                 du[g] = uA;
                                 dvx[g] = vxA;
                                 dvy[g] = vyA;
@@ -169,7 +169,7 @@ k_step2d_t2(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                             R vyBl = sup(vyB);
                             R uB = a * uA_prev + bf * coef[3 * mp] * ((vyB - vyBl) - (vxB - vxB_prev));
                             if (store) {
-                                size_t g = (size_t)(j0 + r - 1) * nx + col;
+                                unsigned g = (unsigned)((j0 + r - 1) * nx + col);
                                 du[g] = uB;
                                 dvx[g] = vxB;
                                 dvy[g] = vyB;
@@ -190,7 +190,7 @@ k_step2d_t2(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
             // step A: uA of rows j0-1 .. j0+h+1, vA of rows j0-1 .. j0+h; step B: uB of rows
             // j0 .. j0+h, vB of rows j0 .. j0+h-1
             int jm2 = wrap2(j0 - 2, ny), jm1 = wrap2(j0 - 1, ny);
-            size_t g2 = (size_t)jm2 * nx + col, g1 = (size_t)jm1 * nx + col;
+            unsigned g2 = (unsigned)(jm2 * nx + col), g1 = (unsigned)(jm1 * nx + col);
             R vx_o = svx[g1], vy_o = svy[g1];        // old v of the current row (j0-1)
             int m_c = mat[g1];
             R uA_c = su[g1] + hfA * coef[3 * m_c] * ((vy_o - sup(vy_o)) - (vx_o - svx[g2]));
@@ -204,7 +204,7 @@ k_step2d_t2(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                 for (int q = 0; q < ROWS2; ++q) {
                     int r = rb + q;
                     if (r <= h) {
-                        size_t g = (size_t)wrap2(j0 + r + 1, ny) * nx + col;
+                        unsigned g = (unsigned)(wrap2(j0 + r + 1, ny) * nx + col);
                         un[q] = su[g];
                         vx[q] = svx[g];
                         vy[q] = svy[g];
@@ -222,7 +222,7 @@ k_step2d_t2(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                     if (!two) {
                         if (r >= 0 && r < h) {
                             if (store) {
-                                size_t g = (size_t)(j0 + r) * nx + col;
+                                unsigned g = (unsigned)((j0 + r) * nx + col);
                                 du[g] = uA_c;
                                 dvx[g] = vxA;
                                 dvy[g] = vyA;
@@ -239,7 +239,7 @@ k_step2d_t2(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                                 R vxB = a * vxA_prev - bf * coef[3 * mp + 1] * (uB - uB_prev);
                                 R vyB = a * vyA_prev + bf * coef[3 * mp + 2] * (sdn(uB_prev) - uB_prev);
                                 if (store) {
-                                    size_t g = (size_t)(j0 + r - 1) * nx + col;
+                                    unsigned g = (unsigned)((j0 + r - 1) * nx + col);
                                     du[g] = uB_prev;
                                     dvx[g] = vxB;
                                     dvy[g] = vyB;
