@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 # the kernel on the piston profiling case (`--profile-case piston`, 17.0 M cells, above L2).  Traffic grows in
 # proportion to the cells (same tiles, same access pattern), so the benchmark's launch scales by its cell count.
 # Valid only for the kernel build that was captured; remove the entry when the kernel changes.
-DRAM_BYTES_PER_CELL_LAUNCH = {}
+DRAM_BYTES_PER_CELL_LAUNCH = {"k_step2d_t2<float>": (205.327e6 + 163.056e6) / 16998400}
 
 METRIC = "forces/s and Gcell-updates/s (% HBM roofline), p50/p99 latency vs plain at 1e-4 rel"
 WORKLOAD = "2D piston sweep: 8 h x TE+TM x 40 harmonics, 400x(80..280) cells, 20000 steps"
