@@ -332,6 +332,8 @@ def profile_case_problems(case, steps):
     import workloads as W
     if case == "piston":       # one sweep geometry, 16 harmonics: 256 FP32 simulations, 17 M cells
         return [W.config2_piston(W.config2_heights()[3], n_harm=16, n_steps=steps)]
+    if case == "piston64":     # the same in FP64 mode (is the FP64 leapfrog bound by HBM or by FP64 arithmetic?)
+        return [W.config2_piston(W.config2_heights()[3], n_harm=16, n_steps=steps, precision="fp64")]
     if case == "waveguides":   # 256 x 256 CPML cell, Lorentz guides, 2 k_z x 6 harmonics: 192 simulations
         kp = W.config3_kz_points(0.5)
         return [W.config3_waveguides(0.5, n_harm=6, n_steps=steps, k_points=[kp[3], kp[12]])]
@@ -407,7 +409,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--no-serving-sweep", action="store_true", help="skip the 200-request trace and the load sweep")
     ap.add_argument("--no-autotune", action="store_true", help="default execution options instead of autotuned ones")
-    ap.add_argument("--profile-case", choices=["piston", "waveguides", "sphere3d", "grating", "cylinder"], default=None,
+    ap.add_argument("--profile-case", choices=["piston", "piston64", "waveguides", "sphere3d", "grating", "cylinder"], default=None,
                     help="run one mid-size case for kernel profiling instead of the benchmark")
     args = ap.parse_args()
     if args.impl == "reference":
