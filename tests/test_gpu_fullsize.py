@@ -4,6 +4,7 @@ sampled simulations recomputed one by one by the FP64 oracle.
 
   * 2D piston sweep: 400 x 80 and 400 x 280 grids, 40 harmonics, TE + TM, 20000 steps;
   * waveguides: 256 x 256 with 1-unit CPML, Lorentz pole, 4 of the 32 k_z points, 3840 steps;
+  * rotationally symmetric two-block piston: 60 x 400 (r, z), m, n in {0, 1, 2}, 10314 steps;
   * sphere over an indented substrate: 160^3 with 12-cell CPML, one harmonic per face,
     a shortened run of 100 steps (the oracle's cost per full-length 3D simulation is
     about ten minutes).
@@ -80,5 +81,23 @@ def test_sphere_notch_full_grid(ctx):
     per = _run_together(ctx, [p])[0]
     picks = [0, len(per) - 1]
     ref = _oracle_sims(p, picks)
+    for i, r in zip(picks, ref):
+        assert abs(per[i] - r) <= 2e-5 * max(abs(r), 1e-3 * np.max(np.abs(per))), (i, per[i], r)
+
+
+def test_cylinder_blocks_full_size(ctx):
+    # the rotationally symmetric two-block piston at its benchmark size: 60 x 400 (r, z) at
+    # resolution 40, m, n in {0, 1, 2}, 10314 steps; one sampled simulation per m and the last one
+    p = W.cylinder_blocks(1.0)
+    per = _run_together(ctx, [p])[0]
+    sims = oracle.enumerate_sims(p)
+    w = oracle.g_weights(p)
+    picks = sorted({next(i for i, s in enumerate(sims) if s["k"] == k) for k in range(len(p["k_points"]))} | {len(sims) - 1})
+
+    def one(i):
+        s = sims[i]
+        return float(np.sum(w * oracle.run_sim(p, s).real)) * p["k_points"][s["k"]]["weight"]
+    with ThreadPoolExecutor(max_workers=len(picks)) as ex:
+        ref = list(ex.map(one, picks))
     for i, r in zip(picks, ref):
         assert abs(per[i] - r) <= 2e-5 * max(abs(r), 1e-3 * np.max(np.abs(per))), (i, per[i], r)
