@@ -10,5 +10,5 @@ g(t)), plain C loops (yee_oracle.c) for the leapfrog itself.
 from .casimir_oracle import (  # noqa: F401
     build_library, build_all, img_minus_t, g_weights, enumerate_sims, run_sim, force,
     evolve, grid_setup, face_pixels, harmonic, interp_weights, run_vectors,
-    is_cyl, cyl_site_weight, E_OFF, H_OFF,
+    is_cyl, cyl_site_weight, E_OFF, H_OFF, lorentz_poles, MAX_POLES,
 )

@@ -49,6 +49,7 @@ _LIB_LOCK = threading.Lock()
 
 DP = ctypes.POINTER(ctypes.c_double)
 IP = ctypes.POINTER(ctypes.c_int)
+MAX_POLES = 3      # undamped Lorentz poles per material (the silica model of Sec. III D has three)
 
 
 class _OgGrid(ctypes.Structure):
@@ -57,7 +58,8 @@ class _OgGrid(ctypes.Structure):
         ("eact", ctypes.c_int * 3), ("hact", ctypes.c_int * 3), ("kz", ctypes.c_double),
         ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("sigma", ctypes.c_double),
         ("bloch_re", ctypes.c_double * 3), ("bloch_im", ctypes.c_double * 3),
-        ("ce", DP * 3), ("ch", DP * 3), ("lde", DP * 3), ("lw0", DP * 3),
+        ("ce", DP * 3), ("ch", DP * 3), ("npole", ctypes.c_int),
+        ("lde", (DP * 3) * MAX_POLES), ("lw0", (DP * 3) * MAX_POLES),
         ("pb", (DP * 2) * 3), ("pc", (DP * 2) * 3), ("pk", (DP * 2) * 3),
         ("cyl", ctypes.c_int), ("mphi", ctypes.c_double),
     ]
@@ -196,8 +198,20 @@ def _inside(obj, pts, dims, d):
     raise ValueError(obj["shape"])
 
 
+def lorentz_poles(obj):
+    """The (delta_eps_j, omega_j) of a Lorentz object: `delta_eps` and `omega0` are numbers (one
+    pole, Eq. (9) without damping) or equal-length sequences (a sum of poles, as in the silica
+    model of Sec. III D).  Poles with delta_eps_j = 0 contribute nothing."""
+    de, w0 = obj["delta_eps"], obj["omega0"]
+    de = [float(de)] if np.isscalar(de) else [float(x) for x in de]
+    w0 = [float(w0)] if np.isscalar(w0) else [float(x) for x in w0]
+    if len(de) != len(w0) or not 1 <= len(de) <= MAX_POLES:
+        raise ValueError("lorentz: delta_eps and omega0 need 1..%d entries each" % MAX_POLES)
+    return list(zip(de, w0))
+
+
 def _materials(problem, pts):
-    """Material at each point: (eps, mu, pec, pmc, delta_eps, omega0); later objects win."""
+    """Material at each point: (eps, mu, pec, pmc, delta_eps[pole], omega0[pole]); later objects win."""
     dims = problem["dims"]
     d = 1.0 / problem["resolution"]
     M = pts[0].shape[0]
@@ -205,24 +219,24 @@ def _materials(problem, pts):
     mu = np.full(M, float(problem["background"]["mu"]))
     pec = np.zeros(M, dtype=bool)
     pmc = np.zeros(M, dtype=bool)
-    lde = np.zeros(M)
-    lw0 = np.zeros(M)
+    lde = np.zeros((MAX_POLES, M))
+    lw0 = np.zeros((MAX_POLES, M))
     for obj in problem["objects"]:
         m = _inside(obj, pts, dims, d)
         kind = obj["kind"]
         pec[m] = kind == "pec"
         pmc[m] = kind == "pmc"
+        lde[:, m] = 0.0
+        lw0[:, m] = 0.0
         if kind == "dielectric":
             eps[m] = obj.get("eps", 1.0)
             mu[m] = obj.get("mu", 1.0)
-            lde[m] = 0.0
         elif kind == "lorentz":
             eps[m] = obj.get("eps_inf", 1.0)
             mu[m] = 1.0
-            lde[m] = obj["delta_eps"]
-            lw0[m] = obj["omega0"]
-        else:
-            lde[m] = 0.0
+            for j, (de, w0) in enumerate(lorentz_poles(obj)):
+                lde[j, m] = de
+                lw0[j, m] = w0
     return eps, mu, pec, pmc, lde, lw0
 
 
@@ -308,8 +322,8 @@ class _Setup:
                     wall |= axis      # E_phi(0) carries no weight; E_z ~ r^|m| vanishes there for m != 0
             ce = np.where(pec | wall, 0.0, 1.0 / eps)
             self.ce.append(np.ascontiguousarray(ce))
-            lde_all.append(np.ascontiguousarray(np.where(pec | wall, 0.0, lde)))
-            lw0_all.append(np.ascontiguousarray(lw0))
+            lde_all.append([np.ascontiguousarray(np.where(pec | wall, 0.0, lde[j])) for j in range(MAX_POLES)])
+            lw0_all.append([np.ascontiguousarray(lw0[j]) for j in range(MAX_POLES)])
             pts = _site_coords(problem, H_OFF[c])
             eps, mu, pec, pmc, lde, lw0 = _materials(problem, pts)
             if cyl and c == 0:
@@ -318,11 +332,14 @@ class _Setup:
         for c in range(3):
             g.ce[c] = _dp(self.ce[c])
             g.ch[c] = _dp(self.ch[c])
-        if any(np.any(x != 0.0) for x in lde_all):
+        used = [j for j in range(MAX_POLES) if any(np.any(lde_all[c][j] != 0.0) for c in range(3))]
+        if used:
+            g.npole = max(used) + 1
             self.lde, self.lw0 = lde_all, lw0_all
-            for c in range(3):
-                g.lde[c] = _dp(self.lde[c])
-                g.lw0[c] = _dp(self.lw0[c])
+            for j in range(g.npole):
+                for c in range(3):
+                    g.lde[j][c] = _dp(self.lde[c][j])
+                    g.lw0[j][c] = _dp(self.lw0[c][j])
         self.pml = {}
         for a in range(dims):
             if problem["bc"][a] == "pml":

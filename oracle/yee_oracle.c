@@ -49,6 +49,8 @@ typedef double complex cx;
 #define IM(x) cimag(x)
 #endif
 
+#define OG_MAXPOLE 3   /* undamped Lorentz poles per material (the silica model has three) */
+
 typedef struct {
     int n[3];            /* cells along x, y, z; n[2] == 1 for a 2D cross-section */
     int twod;            /* 1: fields vary as exp(i kz z); d/dz -> i kz (Sec. III B) */
@@ -58,8 +60,9 @@ typedef struct {
     double bloch_re[3], bloch_im[3];   /* exp(i k_a L_a) for each axis (1 when not Bloch) */
     const double *ce[3];  /* 1/eps_inf at the E_c sites, 0 inside PEC */
     const double *ch[3];  /* 1/mu at the H_c sites, 0 inside PMC */
-    const double *lde[3]; /* Lorentz Delta-eps at E_c sites (NULL: non-dispersive everywhere) */
-    const double *lw0[3]; /* Lorentz omega_0 at E_c sites */
+    int npole;            /* Lorentz poles per E site, 0..OG_MAXPOLE (0: non-dispersive everywhere) */
+    const double *lde[OG_MAXPOLE][3]; /* Delta-eps_j of pole j at the E_c sites (0: no such pole there) */
+    const double *lw0[OG_MAXPOLE][3]; /* omega_j of pole j at the E_c sites */
     /* CPML along axis a, per site index along that axis, [0] integer sites, [1] half sites */
     const double *pb[3][2], *pc[3][2], *pk[3][2];
     /* Cylindrical (r, z) cross-section with fields ~ exp(i m phi) (Sec. III C and the appendix on
@@ -221,35 +224,39 @@ static void curl_h_cyl(const og_grid *g, cx *const H[3], cx *out[3])
         }
 }
 
-/* Lorentz polarisation, one step of P'' + sigma P' + w0^2 P = deps w0^2 E
- * (Eq. (9) with omega^2 -> xi^2 + i sigma xi and gamma = 0, central differences).
- * `first` applies the start P(-dt) = P(+dt) (P and P' vanish at the impulse). */
-static void lorentz_step(const og_grid *g, cx *P[3], cx *Pm[3], cx *const E[3], int first, int N)
+/* Lorentz polarisation, one step of P_j'' + sigma P_j' + w_j^2 P_j = deps_j w_j^2 E for every pole j
+ * (Eq. (9), or the sum of poles of the silica model, with omega^2 -> xi^2 + i sigma xi and no damping,
+ * central differences).  `first` applies the start P_j(-dt) = P_j(+dt) (P and P' vanish at the impulse). */
+static void lorentz_step(const og_grid *g, cx *P[][3], cx *Pm[][3], cx *const E[3], int first, int N)
 {
-    if (!g->lde[0]) return;
     double dt = g->dt, s = g->sigma;
-    for (int c = 0; c < 3; ++c)
-        for (int m = 0; m < N; ++m) {
-            double de = g->lde[c][m];
-            if (de == 0.0) continue;
-            double w2 = g->lw0[c][m] * g->lw0[c][m];
-            cx pn;
-            if (first)
-                pn = 0.5 * ((2.0 - w2 * dt * dt) * P[c][m] + de * w2 * dt * dt * E[c][m]);
-            else
-                pn = ((2.0 - w2 * dt * dt) * P[c][m] - (1.0 - 0.5 * s * dt) * Pm[c][m] + de * w2 * dt * dt * E[c][m])
-                     / (1.0 + 0.5 * s * dt);
-            Pm[c][m] = P[c][m];
-            P[c][m] = pn;
-        }
+    for (int j = 0; j < g->npole; ++j)
+        for (int c = 0; c < 3; ++c)
+            for (int m = 0; m < N; ++m) {
+                double de = g->lde[j][c][m];
+                if (de == 0.0) continue;
+                double w2 = g->lw0[j][c][m] * g->lw0[j][c][m];
+                cx pn;
+                if (first)
+                    pn = 0.5 * ((2.0 - w2 * dt * dt) * P[j][c][m] + de * w2 * dt * dt * E[c][m]);
+                else
+                    pn = ((2.0 - w2 * dt * dt) * P[j][c][m] - (1.0 - 0.5 * s * dt) * Pm[j][c][m] +
+                          de * w2 * dt * dt * E[c][m]) / (1.0 + 0.5 * s * dt);
+                Pm[j][c][m] = P[j][c][m];
+                P[j][c][m] = pn;
+            }
 }
 
-static void fields_e(const og_grid *g, cx *E[3], cx *const D[3], cx *const P[3], int N)
+/* E = (D - sum_j P_j) / eps_inf */
+static void fields_e(const og_grid *g, cx *E[3], cx *const D[3], cx *P[][3], int N)
 {
     for (int c = 0; c < 3; ++c)
         if (g->eact[c])
-            for (int m = 0; m < N; ++m)
-                E[c][m] = g->ce[c][m] * (D[c][m] - (g->lde[0] ? P[c][m] : 0.0));
+            for (int m = 0; m < N; ++m) {
+                cx d = D[c][m];
+                for (int j = 0; j < g->npole; ++j) d -= P[j][c][m];
+                E[c][m] = g->ce[c][m] * d;
+            }
 }
 
 static void fields_h(const og_grid *g, cx *H[3], cx *const B[3], int N)
@@ -270,19 +277,29 @@ static void measure(const og_sim *s, cx *const F[3], int step, double *out_re, d
     }
 }
 
+/* One zeroed pool for E H D B tmp (x3), P_j and P_j-prev (x3 per pole), psi_e psi_h (x9). */
+static cx *alloc_fields(int N, cx *E[3], cx *H[3], cx *D[3], cx *B[3], cx *P[][3], cx *Pm[][3], cx *T[3],
+                        cx *pe[3][3], cx *ph[3][3])
+{
+    cx *pool = calloc((size_t)N * (3 * 5 + 6 * OG_MAXPOLE + 2 * 9), sizeof(cx));
+    if (!pool) return NULL;
+    cx *p = pool;
+    for (int c = 0; c < 3; ++c) { E[c] = p; p += N; H[c] = p; p += N; D[c] = p; p += N; B[c] = p; p += N;
+                                  T[c] = p; p += N; }
+    for (int j = 0; j < OG_MAXPOLE; ++j)
+        for (int c = 0; c < 3; ++c) { P[j][c] = p; p += N; Pm[j][c] = p; p += N; }
+    for (int c = 0; c < 3; ++c) for (int a = 0; a < 3; ++a) { pe[c][a] = p; p += N; ph[c][a] = p; p += N; }
+    return pool;
+}
+
 /* Run one simulation; out_re/out_im receive nset x nsteps samples s(n), n = 1..T.
  * Returns 0 on success, -1 on allocation failure. */
 int oracle_run(const og_grid *g, const og_sim *s, double *out_re, double *out_im)
 {
     int N = g->n[0] * g->n[1] * g->n[2];
-    int nbuf = 3 * 7 + 2 * 9;   /* E H D B P Pm tmp (x3), psi_e psi_h (x9) */
-    cx *pool = calloc((size_t)N * nbuf, sizeof(cx));
+    cx *E[3], *H[3], *D[3], *B[3], *P[OG_MAXPOLE][3], *Pm[OG_MAXPOLE][3], *T[3], *pe[3][3], *ph[3][3];
+    cx *pool = alloc_fields(N, E, H, D, B, P, Pm, T, pe, ph);
     if (!pool) return -1;
-    cx *E[3], *H[3], *D[3], *B[3], *P[3], *Pm[3], *T[3], *pe[3][3], *ph[3][3];
-    cx *p = pool;
-    for (int c = 0; c < 3; ++c) { E[c] = p; p += N; H[c] = p; p += N; D[c] = p; p += N; B[c] = p; p += N;
-                                  P[c] = p; p += N; Pm[c] = p; p += N; T[c] = p; p += N; }
-    for (int c = 0; c < 3; ++c) for (int a = 0; a < 3; ++a) { pe[c][a] = p; p += N; ph[c][a] = p; p += N; }
 
     double dt = g->dt, sg = g->sigma;
     double a_s = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt);   /* conductive decay */
@@ -338,13 +355,9 @@ int oracle_evolve(const og_grid *g, int nsteps, double *e_re, double *e_im, doub
                   double *hprev_re, double *hprev_im)
 {
     int N = g->n[0] * g->n[1] * g->n[2];
-    cx *pool = calloc((size_t)N * (3 * 7 + 2 * 9), sizeof(cx));
+    cx *E[3], *H[3], *D[3], *B[3], *P[OG_MAXPOLE][3], *Pm[OG_MAXPOLE][3], *T[3], *pe[3][3], *ph[3][3];
+    cx *pool = alloc_fields(N, E, H, D, B, P, Pm, T, pe, ph);
     if (!pool) return -1;
-    cx *E[3], *H[3], *D[3], *B[3], *P[3], *Pm[3], *T[3], *pe[3][3], *ph[3][3];
-    cx *p = pool;
-    for (int c = 0; c < 3; ++c) { E[c] = p; p += N; H[c] = p; p += N; D[c] = p; p += N; B[c] = p; p += N;
-                                  P[c] = p; p += N; Pm[c] = p; p += N; T[c] = p; p += N; }
-    for (int c = 0; c < 3; ++c) for (int a = 0; a < 3; ++a) { pe[c][a] = p; p += N; ph[c][a] = p; p += N; }
     double dt = g->dt, sg = g->sigma;
     double a_s = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt);
     double b_s = dt / (1.0 + 0.5 * sg * dt);

@@ -18,7 +18,9 @@ along each axis a):
     background    {"eps": .., "mu": ..}
     objects       list of {"shape": "box"|"sphere", "lo","hi" | "center","radius",
                   "kind": "pec"|"pmc"|"dielectric"|"lorentz", "eps", "mu",
-                  "eps_inf", "delta_eps", "omega0"}; later objects win
+                  "eps_inf", "delta_eps", "omega0"}; later objects win.  A Lorentz
+                  object's delta_eps / omega0 are numbers (one undamped pole) or
+                  equal-length lists of up to three (a sum of poles)
     bc            per axis "pec" | "pml" | "periodic"
     pml_cells     per axis CPML thickness in cells (for "pml" axes)
     faces         stress-surface faces {"axis", "sign", "pos", "lo", "hi"}
@@ -40,6 +42,7 @@ __all__ = [
     "box_faces", "plates_box_2d", "config1_plates", "config2_piston",
     "config2_heights", "config3_waveguides", "config3_gaps", "config3_kz_points",
     "config4_sphere_notch", "serving_requests", "piston_small",
+    "silicon", "silica", "grating_silica", "cylinder_piston", "cylinder_blocks",
 ]
 
 
@@ -432,4 +435,70 @@ def cylinder_blocks(h, *, resolution=40, m_list=(0, 1, 2), n_harm=3, t_max=100.0
     p["k_points"] = [{"k": [0.0, 0.0, 0.0], "m": int(m), "weight": 1.0 if int(m) == 0 else 2.0} for m in m_list]
     p["precision"] = precision
     p["kind"] = "cylinder"
+    return p
+
+
+# ---------------------------------------------------------------------------
+# Dispersive materials of Sec. III D in units of a = 1 um: omega [rad/s] * a / c
+# ---------------------------------------------------------------------------
+
+C_UM_PER_S = 2.99792458e14      # the speed of light in um / s
+
+
+def silicon():
+    """Silicon, one undamped pole: eps(0) = 11.87, eps(inf) = 1.035, omega_0 = 6.6e15 rad/s
+    (the printed formula's leading term read as eps(inf), so that eps(0) is silicon's 11.87)."""
+    return {"kind": "lorentz", "eps_inf": 1.035, "delta_eps": 11.87 - 1.035, "omega0": 6.6e15 / C_UM_PER_S}
+
+
+def silica():
+    """Silica, three undamped poles: eps = 1 + sum_j C_j w_j^2 / (w_j^2 - w^2),
+    C = (0.829, 0.095, 1.098), w = (0.867, 1.508, 203.4) x 1e14 rad/s."""
+    return {"kind": "lorentz", "eps_inf": 1.0, "delta_eps": [0.829, 0.095, 1.098],
+            "omega0": [w * 1e14 / C_UM_PER_S for w in (0.867, 1.508, 203.4)]}
+
+
+def grating_silica(gap, *, resolution=40, nk_x=8, nk_z=8, n_harm=8, t_max=40.0, courant=0.5,
+                   kz_max=None, pml_units=0.5, precision="fp32"):
+    """A periodic array of silicon waveguides (period 1 along x, 0.5 wide, 0.5 tall, invariant
+    along z) a distance `gap` above a substrate of a 0.25 silicon film on 1.0 of silica, CPML
+    above and below (Sec. III D).  Force along y on one waveguide per unit length: the
+    Brillouin-zone average over nk_x Bloch k_x in [0, pi] (the +-k_x pairs folded) times
+    (1/pi) int_0^K dk_z by nk_z-point Gauss-Legendre, K = min(12/gap, kz_max); the stress
+    surface is two full-period lines one pixel below and above the waveguide."""
+    d = 1.0 / resolution
+    nx = int(round(resolution))
+    pc = int(round(pml_units * resolution))
+    y_silica = pc * d
+    y_film = y_silica + round(1.0 * resolution) * d
+    y_top = y_film + round(0.25 * resolution) * d          # substrate surface
+    y_wg = y_top + round(gap * resolution) * d               # waveguide bottom
+    y_wg_top = y_wg + round(0.5 * resolution) * d
+    ny = int(round((y_wg_top + 0.75) * resolution)) + pc
+    dt = courant * d
+    n_steps = int(round(t_max / dt))
+    p = _base(2, (nx, ny, 1), resolution, n_steps, courant=courant)
+    p["bc"] = ["periodic", "pml", "pec"]
+    p["pml_cells"] = [0, pc, 0]
+    p["objects"] = [
+        dict(shape="box", lo=[-1.0, -1.0, 0.0], hi=[2.0, y_film, 0.0], **silica()),
+        dict(shape="box", lo=[-1.0, y_film, 0.0], hi=[2.0, y_top, 0.0], **silicon()),
+        dict(shape="box", lo=[0.25, y_wg, 0.0], hi=[0.75, y_wg_top, 0.0], **silicon()),
+    ]
+    ylo, yhi = y_wg - d, y_wg_top + d
+    p["faces"] = [
+        {"axis": 1, "sign": -1, "pos": ylo, "lo": [0.0, ylo, 0.0], "hi": [1.0, ylo, 0.0]},
+        {"axis": 1, "sign": +1, "pos": yhi, "lo": [0.0, yhi, 0.0], "hi": [1.0, yhi, 0.0]},
+    ]
+    p["n_harm"] = int(min(n_harm, nx))
+    p["polarization"] = "full"
+    # k_x: midpoints of [0, pi] (each stands for +-k_x); k_z: Gauss-Legendre on [0, K]
+    K = 12.0 / gap if kz_max is None else min(12.0 / gap, kz_max)
+    u, w = np.polynomial.legendre.leggauss(nk_z)
+    kxs = [math.pi * (i + 0.5) / nk_x for i in range(nk_x)]
+    p["k_points"] = [{"k": [kx, 0.0, float(K * (1 + ui) / 2)], "weight": float(wi * K / 2 / math.pi / nk_x)}
+                     for kx in kxs for ui, wi in zip(u, w)]
+    p["force_axis"] = 1
+    p["g_variant"] = "plain"
+    p["precision"] = precision
     return p
