@@ -274,11 +274,36 @@ def measure_cylinder(pk, ctx):
     return out
 
 
+def measure_grating_silica(pk, ctx):
+    """The periodic application of Sec. III D: silicon waveguides (one-pole silicon) over a
+    silicon film on silica (three poles), period 1 um, at three separations, all in flight
+    together: 4 k_x x 8 k_z Bloch points, 8 harmonics per line, 40 x ~160 cells, t = 40."""
+    import workloads as W
+    gaps = (0.25, 0.5, 1.0)
+    plans = [ctx.plan(W.grating_silica(g, nk_x=4)) for g in gaps]
+    for pl in plans:
+        pl.run()                               # tables uploaded, graphs built
+    ctx.kernel_stats(reset=True)
+    t0 = time.perf_counter()
+    tickets = [pl.submit(tag=i) for i, pl in enumerate(plans)]
+    res = [t.force(-1) for t in tickets]
+    wall = time.perf_counter() - t0
+    ms, _, cu = ctx.kernel_stats(reset=True)
+    out = {"workload": "silicon waveguide grating over silicon/silica (1 + 3 undamped Lorentz poles), "
+                       "resolution 40, 4 k_x x 8 k_z, 8 harmonics, 3200 steps, complex FP32 fields",
+           "forces": [{"gap": g, "F_y": float(r[0][1])} for g, r in zip(gaps, res)],
+           "sims_per_force": plans[0].info()["n_sims"],
+           "gcell_updates_per_s": cu / (ms / 1e3) / 1e9, "forces_per_s": len(plans) / wall, "kernel_ms": ms}
+    for pl in plans:
+        pl.close()
+    return out
+
+
 def oracle_check_problems():
     """Small problems whose GPU forces the bench reports with their error against the FP64 oracle:
     the full config-1 plates (FP64), a config-2 sample (first sidewall spacing, 2 harmonics, 1000
-    steps) in FP32 and FP64 mode, the first serving request of each kind, and a coarse cylindrical
-    piston.  err_over_sum_abs divides by the sum of |per-simulation contributions|, the scale of the
+    steps) in FP32 and FP64 mode, the first serving request of each kind, a coarse cylindrical
+    piston and a coarse silicon/silica grating.  err_over_sum_abs divides by the sum of |per-simulation contributions|, the scale of the
     cancellation the force results from."""
     import workloads as W
     probs = {"config1_plates_fp64_full": W.config1_plates()}
@@ -290,6 +315,8 @@ def oracle_check_problems():
         if key not in probs:
             probs[key] = p
     probs["cylinder_blocks_h0.5_res10"] = W.cylinder_blocks(0.5, resolution=10, t_max=20.0)
+    probs["grating_silica_res16_fp32"] = W.grating_silica(0.5, resolution=16, nk_x=2, nk_z=2, n_harm=2, t_max=3.0,
+                                                          courant=0.2, pml_units=0.25, precision="fp32")
     return probs
 
 
@@ -341,6 +368,10 @@ def profile_case_problems(case, steps):
         return [W.config4_sphere_notch(0.55, seed=1, n_harm=1, n_steps=steps)]
     if case == "cylinder":     # rotationally symmetric two-block piston, h = 1: 60 x 400 (r, z), m, n <= 2
         p = W.cylinder_blocks(1.0)
+        p["n_steps"] = steps
+        return [p]
+    if case == "grating_silica":   # 40 x 160 silicon/silica grating, 4 k_x x 8 k_z, 8 harmonics: 3072 sims
+        p = W.grating_silica(0.5, nk_x=4)
         p["n_steps"] = steps
         return [p]
     if case == "grating":      # 128 x 512 Bloch cell, 16 k_x (complex fields), CPML along y, 8 harmonics
@@ -409,7 +440,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--no-serving-sweep", action="store_true", help="skip the 200-request trace and the load sweep")
     ap.add_argument("--no-autotune", action="store_true", help="default execution options instead of autotuned ones")
-    ap.add_argument("--profile-case", choices=["piston", "piston64", "waveguides", "sphere3d", "grating", "cylinder"], default=None,
+    ap.add_argument("--profile-case", choices=["piston", "piston64", "waveguides", "sphere3d", "grating", "grating_silica", "cylinder"], default=None,
                     help="run one mid-size case for kernel profiling instead of the benchmark")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -533,6 +564,7 @@ def main():
         others = measure_configs(pk, ctx, peaks()[0])
         others["basis_point_vs_cosine"] = measure_basis(pk, ctx)
         others["cylinder_piston"] = measure_cylinder(pk, ctx)
+        others["grating_silica"] = measure_grating_silica(pk, ctx)
 
     check = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -54,7 +54,10 @@ enum { CASIMIR_SHAPE_BOX = 0, CASIMIR_SHAPE_SPHERE = 1 };
 enum { CASIMIR_MAT_PEC = 0,        /* eps = -inf (Sec. III A): tangential E vanishes */
        CASIMIR_MAT_PMC = 1,        /* mu = -inf (Sec. III A): tangential H vanishes */
        CASIMIR_MAT_DIELECTRIC = 2, /* constant eps, mu */
-       CASIMIR_MAT_LORENTZ = 3 };  /* eps_inf + delta_eps w0^2/(w0^2 - w^2) (Sec. III B), continued onto the contour */
+       CASIMIR_MAT_LORENTZ = 3 };  /* eps_inf + sum_j delta_eps_j w_j^2/(w_j^2 - w^2): undamped poles, one for
+                                      the silicon model of Eq. (9), three for the silica model of
+                                      Sec. III D; continued onto the contour (w^2 -> xi^2 + i sigma xi) */
+#define CASIMIR_MAX_POLES 3
 enum { CASIMIR_POL_TM = 1, CASIMIR_POL_TE = 2, CASIMIR_POL_TETM = 3, /* 2D, k_z = 0 */
        CASIMIR_POL_FULL = 4 };     /* all six source components (2D with k_z != 0, or 3D) */
 enum { CASIMIR_G_PLAIN = 0,        /* Im g(-t) of Appendix A */
@@ -84,7 +87,11 @@ typedef struct {
     double center[3];    /* sphere centre */
     double radius;       /* sphere radius */
     double eps, mu;      /* dielectric */
-    double eps_inf, delta_eps, omega0;   /* Lorentz pole (gamma = 0) */
+    double eps_inf;      /* Lorentz: eps at high frequency */
+    double delta_eps[CASIMIR_MAX_POLES];  /* Lorentz pole strengths (>= 0; 0: the pole is absent) */
+    double omega0[CASIMIR_MAX_POLES];     /* Lorentz pole frequencies (> 0 where delta_eps > 0); every
+                                             pole needs omega0 dt < 2, and the medium eps(4/dt^2) above
+                                             the lattice's (dt/2)^2 k_max^2 (CASIMIR_EINVAL otherwise) */
 } casimir_object;
 
 /* One axis-aligned face of the stress surface S: normal along `axis`, outward

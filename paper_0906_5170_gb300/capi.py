@@ -29,13 +29,26 @@ COORDS = {"cartesian": 0, "cylindrical": 1}
 
 D3 = ctypes.c_double * 3
 I3 = ctypes.c_int * 3
+MAX_POLES = 3      # CASIMIR_MAX_POLES
+DP3 = ctypes.c_double * MAX_POLES
 
 
 class Object(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int), ("kind", ctypes.c_int), ("lo", D3), ("hi", D3),
                 ("center", D3), ("radius", ctypes.c_double), ("eps", ctypes.c_double),
-                ("mu", ctypes.c_double), ("eps_inf", ctypes.c_double), ("delta_eps", ctypes.c_double),
-                ("omega0", ctypes.c_double)]
+                ("mu", ctypes.c_double), ("eps_inf", ctypes.c_double), ("delta_eps", DP3),
+                ("omega0", DP3)]
+
+
+def _poles(o: dict):
+    """delta_eps / omega0 of a Lorentz object: numbers (one pole) or equal-length sequences."""
+    de, w0 = o.get("delta_eps", 0.0), o.get("omega0", 0.0)
+    de = [de] if isinstance(de, (int, float)) else list(de)
+    w0 = [w0] if isinstance(w0, (int, float)) else list(w0)
+    if len(de) != len(w0) or not 1 <= len(de) <= MAX_POLES:
+        raise ValueError(f"lorentz: delta_eps and omega0 need 1..{MAX_POLES} entries each")
+    pad = [0.0] * (MAX_POLES - len(de))
+    return DP3(*[float(x) for x in de], *pad), DP3(*[float(x) for x in w0], *pad)
 
 
 class Face(ctypes.Structure):
@@ -164,8 +177,7 @@ class MarshalledProblem:
             ob.eps = float(o.get("eps", 1.0))
             ob.mu = float(o.get("mu", 1.0))
             ob.eps_inf = float(o.get("eps_inf", 1.0))
-            ob.delta_eps = float(o.get("delta_eps", 0.0))
-            ob.omega0 = float(o.get("omega0", 0.0))
+            ob.delta_eps, ob.omega0 = _poles(o)
         faces = p["faces"]
         self.faces = (Face * max(1, len(faces)))()
         for i, f in enumerate(faces):

@@ -95,19 +95,19 @@ static int prepare_plan(casimir_plan_t *P)
         while (P->coef_all.size() % 32) P->coef_all.push_back(0.0);
         P->lor_off.push_back((int64_t)P->lor_all.size());
         if (g.family == FAM_FULL) P->lor_all.insert(P->lor_all.end(), g.lorentz.begin(), g.lorentz.end());
-        // march-kernel form of the Lorentz recurrence: P' = (cp P - cpm P_prev + ce E) cd
+        // kernel form of the Lorentz recurrence of every pole: P' = (cp P - cpm P_prev + ce E) cd
         P->lorc_off.push_back((int64_t)P->lorc_all.size());
         if (g.family == FAM_FULL && g.has_lorentz) {
             const double dt = D.dt, sg = D.prob.sigma;
-            for (size_t id = 0; id < g.lorentz.size() / 6; ++id)
-                for (int q = 0; q < 3; ++q) {
-                    const double de = g.lorentz[id * 6 + 2 * q], w0 = g.lorentz[id * 6 + 2 * q + 1];
-                    const double w2dt2 = w0 * w0 * dt * dt;
-                    P->lorc_all.push_back(2.0 - w2dt2);
-                    P->lorc_all.push_back(1.0 - 0.5 * sg * dt);
-                    P->lorc_all.push_back(de * w2dt2);
-                    P->lorc_all.push_back(1.0 / (1.0 + 0.5 * sg * dt));
-                }
+            // [id][pole][component]: the table of Geo::lorentz in the same order
+            for (size_t ic = 0; ic < g.lorentz.size() / 2; ++ic) {
+                const double de = g.lorentz[2 * ic], w0 = g.lorentz[2 * ic + 1];
+                const double w2dt2 = w0 * w0 * dt * dt;
+                P->lorc_all.push_back(2.0 - w2dt2);
+                P->lorc_all.push_back(1.0 - 0.5 * sg * dt);
+                P->lorc_all.push_back(de * w2dt2);
+                P->lorc_all.push_back(1.0 / (1.0 + 0.5 * sg * dt));
+            }
             while (P->lorc_all.size() % 32) P->lorc_all.push_back(0.0);
         }
         std::array<int64_t, 3> po{-1, -1, -1};
@@ -213,7 +213,8 @@ static int prepare_plan(casimir_plan_t *P)
                 return !(e && std::atoi(e) == 0);
             }();
             // (its 32-bit element offsets reach 12 N within one buffer)
-            hs.march = (D.prob.dims == 2 && g.n[2] == 1 && march_env && 12 * N < ((int64_t)1 << 32)) ? 1 : 0;
+            const int64_t planes = 12 * std::max(1, g.npoles);   // complex planes of fields or Lorentz P
+            hs.march = (D.prob.dims == 2 && g.n[2] == 1 && march_env && planes * N < ((int64_t)1 << 32)) ? 1 : 0;
             if (g.cyl && !hs.march)   // only the march kernel has the cylindrical form
                 return fail(CASIMIR_EINVAL, "cylindrical runs need the march kernel (12 N < 2^32 cells)");
             const int nbuf = hs.march ? 2 : 1;
@@ -226,7 +227,8 @@ static int prepare_plan(casimir_plan_t *P)
                 hs.psi_off = off;
                 off += nbuf * hs.psi_half;
             }
-            hs.lor_half = g.has_lorentz ? 6 * cf * N : 0;
+            hs.lor_half = g.has_lorentz ? 6 * g.npoles * cf * N : 0;
+            hs.npoles = g.npoles;
             if (g.has_lorentz) {
                 hs.lor_off = off;
                 off += nbuf * hs.lor_half;
@@ -240,10 +242,12 @@ static int prepare_plan(casimir_plan_t *P)
                 // halo-extended box [i0-1, i0+w] x [j0-1, j0+h] holds such cells (cached per geometry)
                 auto vit = march_variants.find(sm.geo);
                 if (vit == march_variants.end()) {
-                    std::vector<char> dmat(g.nmat, 0);
+                    // poles of each material (the most over its three E components)
+                    std::vector<int> dmat(g.nmat, 0);
                     for (int id = 0; id < g.nmat; ++id)
-                        for (int q = 0; q < 3; ++q)
-                            if (g.has_lorentz && g.lorentz[(size_t)id * 6 + 2 * q] != 0.0) dmat[id] = 1;
+                        for (int q = 0; q < g.npoles; ++q)
+                            for (int c = 0; c < 3; ++c)
+                                if (g.lorentz[((size_t)id * g.npoles + q) * 6 + 2 * c] != 0.0) dmat[id] = std::max(dmat[id], q + 1);
                     const int dX = g.has_pml[0] ? D.prob.pml_cells[0] : 0, dY = g.has_pml[1] ? D.prob.pml_cells[1] : 0;
                     auto wrapc = [](int i, int n) { return ((i % n) + n) % n; };
                     std::vector<int> vs((size_t)tx * ty, 0);
@@ -251,17 +255,18 @@ static int prepare_plan(casimir_plan_t *P)
                         for (int ti = 0; ti < tx; ++ti) {
                             const int i0 = ti * MARCH_W, j0 = tj * rows;
                             const int w = std::min(MARCH_W, hs.nx - i0), h = std::min(rows, hs.ny - j0);
-                            bool pml = false, lor = false;
+                            bool pml = false;
+                            int poles = 0;
                             for (int jj = j0 - 1; jj <= j0 + h; ++jj) {
                                 const int j = wrapc(jj, hs.ny);
                                 if (dY > 0 && (j < dY || j >= hs.ny - dY)) pml = true;
                                 for (int ii = i0 - 1; ii <= i0 + w; ++ii) {
                                     const int i = wrapc(ii, hs.nx);
                                     if (dX > 0 && (i < dX || i >= hs.nx - dX)) pml = true;
-                                    if (dmat[g.mat[(size_t)j * hs.nx + i]]) lor = true;
+                                    poles = std::max(poles, dmat[g.mat[(size_t)j * hs.nx + i]]);
                                 }
                             }
-                            vs[(size_t)tj * tx + ti] = (pml ? 1 : 0) + (lor ? 2 : 0);
+                            vs[(size_t)tj * tx + ti] = (pml ? 1 : 0) + (poles == 0 ? 0 : poles == 1 ? 2 : 4);
                         }
                     vit = march_variants.emplace(sm.geo, std::move(vs)).first;
                 }
@@ -287,7 +292,7 @@ static int prepare_plan(casimir_plan_t *P)
                     }
                 hs.nent = (int)P->entsM.size() - hs.ent0;
             }
-            hs.line3 = (!hs.march && D.prob.dims == 3 && P->opts.kernel_3d == 1 && 12 * N < ((int64_t)1 << 32)) ? 1 : 0;
+            hs.line3 = (!hs.march && D.prob.dims == 3 && P->opts.kernel_3d == 1 && planes * N < ((int64_t)1 << 32)) ? 1 : 0;
             if (hs.line3) {
                 // tiles of 32 x cells by LINES3 (y, z) lines; entries bucketed per tile
                 const int64_t nl = (int64_t)hs.ny * hs.nz;
@@ -591,6 +596,7 @@ void make_sim6(const casimir_plan_t *P, char *blk, double *acc, double *tail, in
     d->kzB = hs.kzB;
     d->fhalf = hs.march ? hs.fhalf : 0;
     d->tile_rows = P->opts.march_rows;
+    d->npoles = hs.npoles;
     d->psi_half = hs.march ? hs.psi_half : 0;
     d->lor_half = hs.march ? hs.lor_half : 0;
 }
@@ -614,8 +620,8 @@ static int rebuild(casimir_ctx *c)
     std::vector<DevTile2> tt[2];
     std::vector<DevSim6> s6[8];
     std::vector<DevTile6> t6[8];
-    std::vector<DevSim6> sm6[16];
-    std::vector<DevTile> tm6[16];
+    std::vector<DevSim6> sm6[4 * MARCH_VARIANTS];
+    std::vector<DevTile> tm6[4 * MARCH_VARIANTS];
     std::vector<DevSim6> sl3[4];
     std::vector<DevTile> tl3[4];
     std::vector<DevSim6> sc6[2];
@@ -669,10 +675,11 @@ static int rebuild(casimir_ctx *c)
                 // the simulation's descriptor goes to each variant group that holds one of its tiles
                 DevSim6 d;
                 make_sim6(P, blk, r->acc, r->tail, w.s0, s, &d);
-                int idx[4] = {-1, -1, -1, -1};
+                int idx[MARCH_VARIANTS];
+                std::fill(idx, idx + MARCH_VARIANTS, -1);
                 for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
                     const HostTile &ht = P->tilesM[t];
-                    const int gi = 4 * (2 * P->fp64 + hs.cplx) + ht.variant;
+                    const int gi = MARCH_VARIANTS * (2 * P->fp64 + hs.cplx) + ht.variant;
                     if (idx[ht.variant] < 0) {
                         idx[ht.variant] = (int)sm6[gi].size();
                         sm6[gi].push_back(d);
@@ -702,9 +709,16 @@ static int rebuild(casimir_ctx *c)
         if (gi < 2) { ns = s2[gi].size(); nt = t2[gi].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile); sp = s2[gi].data(); tp = t2[gi].data(); }
         else if (gi < 10) { ns = s6[gi - 2].size(); nt = t6[gi - 2].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile6); sp = s6[gi - 2].data(); tp = t6[gi - 2].data(); }
         else if (gi < 12) { ns = 0; nt = tt[gi - 10].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile2); sp = nullptr; tp = tt[gi - 10].data(); }
-        else if (gi < 28) { ns = sm6[gi - 12].size(); nt = tm6[gi - 12].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sm6[gi - 12].data(); tp = tm6[gi - 12].data(); }
-        else if (gi < 32) { ns = sl3[gi - 28].size(); nt = tl3[gi - 28].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sl3[gi - 28].data(); tp = tl3[gi - 28].data(); }
-        else { ns = sc6[gi - 32].size(); nt = tc6[gi - 32].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sc6[gi - 32].data(); tp = tc6[gi - 32].data(); }
+        else if (gi < casimir_ctx::G_LINE3) {
+            const int v = gi - casimir_ctx::G_MARCH;
+            ns = sm6[v].size(); nt = tm6[v].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sm6[v].data(); tp = tm6[v].data();
+        } else if (gi < casimir_ctx::G_CYL) {
+            const int v = gi - casimir_ctx::G_LINE3;
+            ns = sl3[v].size(); nt = tl3[v].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sl3[v].data(); tp = tl3[v].data();
+        } else {
+            const int v = gi - casimir_ctx::G_CYL;
+            ns = sc6[v].size(); nt = tc6[v].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sc6[v].data(); tp = tc6[v].data();
+        }
         int rc = grow(c, &G.sims, &G.sims_cap, ns * ss);
         if (rc) return rc;
         rc = grow(c, &G.tiles, &G.tiles_cap, nt * ts);
@@ -736,15 +750,18 @@ static void launch_unit(casimir_ctx *c, int gi, int j, cudaStream_t st)
     else if (gi < 12)
         launch_step2d_t2(gi - 10, (const DevSim2D *)c->groups[gi - 10].sims, (const DevTile2 *)G.tiles, G.ntiles,
                          c->d_launch, j, st);
-    else if (gi < 28)
-        launch_march6(((gi - 12) >> 3) & 1, ((gi - 12) >> 2) & 1, (gi - 12) & 3, (const DevSim6 *)G.sims,
-                      (const DevTile *)G.tiles, G.ntiles, c->d_launch, j, st);
-    else if (gi < 32)
+    else if (gi < casimir_ctx::G_LINE3) {
+        const int v = gi - casimir_ctx::G_MARCH, fc = v / MARCH_VARIANTS;   // 2 * fp64 + cplx
+        launch_march6(fc >> 1, fc & 1, v % MARCH_VARIANTS, (const DevSim6 *)G.sims, (const DevTile *)G.tiles, G.ntiles,
+                      c->d_launch, j, st);
+    } else if (gi < casimir_ctx::G_CYL) {
+        const int v = gi - casimir_ctx::G_LINE3;
         for (int phase = 0; phase < 2; ++phase)
-            launch_line3(((gi - 28) >> 1) & 1, (gi - 28) & 1, (const DevSim6 *)G.sims, (const DevTile *)G.tiles, G.ntiles,
+            launch_line3((v >> 1) & 1, v & 1, (const DevSim6 *)G.sims, (const DevTile *)G.tiles, G.ntiles,
                          c->d_launch, j, phase, st);
-    else
-        launch_march6_cyl(gi - 32, (const DevSim6 *)G.sims, (const DevTile *)G.tiles, G.ntiles, c->d_launch, j, st);
+    } else {
+        launch_march6_cyl(gi - casimir_ctx::G_CYL, (const DevSim6 *)G.sims, (const DevTile *)G.tiles, G.ntiles, c->d_launch, j, st);
+    }
 }
 
 // Launch k consecutive steps.  The units of one step touch disjoint tiles and read only the
@@ -808,7 +825,8 @@ static int run_chunk(casimir_ctx *c, int k)
     c->h_launch += k;
     int per_step = 0;
     for (int gi = 0; gi < casimir_ctx::NGROUPS; ++gi)
-        if (c->groups[gi].ntiles > 0) per_step += ((gi >= 2 && gi < 10) || (gi >= 28 && gi < 32)) ? 2 : 1;
+        if (c->groups[gi].ntiles > 0)
+            per_step += ((gi >= 2 && gi < 10) || (gi >= casimir_ctx::G_LINE3 && gi < casimir_ctx::G_CYL)) ? 2 : 1;
     for (casimir_request *r : c->active) r->launches += (int64_t)k * per_step + 1;
     return CASIMIR_OK;
 }

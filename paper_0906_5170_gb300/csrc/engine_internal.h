@@ -46,6 +46,7 @@ struct HostSim {
     int64_t psi_off;       // element offset of its CPML planes (full kernel, -1: none)
     int64_t lor_off;       // element offset of its Lorentz planes (full kernel, -1: none)
     int64_t fhalf, psi_half, lor_half;   // march runs: elements of one buffer of fields, psi, Lorentz planes
+    int npoles = 0;        // Lorentz poles in use (6 planes each)
     int tile0, ntile;      // range in the plan's tile list (2D and march runs) or tile6 list (full)
     int tile2_0, ntile2;   // range in the plan's two-step tile list (2D)
     int ent0, nent;        // range in the plan's entry list (bucketed by tile)
@@ -54,7 +55,7 @@ struct HostSim {
 
 struct HostTile {
     int sim, i0, j0, ent0, ne;
-    int variant = 0;       // march tiles: 1 = touches CPML, + 2 = touches dispersive cells (halo included)
+    int variant = 0;       // march tiles: 1 = touches CPML, + 2 (4) = the most Lorentz poles of its cells is 1 (> 1)
 };
 
 struct HostTile2 {
@@ -169,10 +170,13 @@ struct casimir_ctx {
     std::vector<casimir_request *> active;
     // launch groups: [0, 1] the 2D kernel in FP32 / FP64; [2 + 4*fp64 + 2*cplx + (dims == 3)]
     // the six-component kernel; [10, 11] the two-step 2D kernel in FP32 / FP64;
-    // [12 + 4 * (2*fp64 + cplx) + variant] the six-component march kernel of two-dimensional runs;
-    // [28 + 2*fp64 + cplx] the x-line kernel of three-dimensional runs; [32 + fp64] the
-    // cylindrical march kernel
-    static constexpr int NGROUPS = 34;
+    // [G_MARCH + MARCH_VARIANTS * (2*fp64 + cplx) + variant] the six-component march kernel of
+    // two-dimensional runs; [G_LINE3 + 2*fp64 + cplx] the x-line kernel of three-dimensional
+    // runs; [G_CYL + fp64] the cylindrical march kernel
+    static constexpr int G_MARCH = 12;
+    static constexpr int G_LINE3 = G_MARCH + 4 * MARCH_VARIANTS;
+    static constexpr int G_CYL = G_LINE3 + 4;
+    static constexpr int NGROUPS = G_CYL + 2;
     struct Group {
         void *sims = nullptr, *tiles = nullptr;
         size_t sims_cap = 0, tiles_cap = 0;

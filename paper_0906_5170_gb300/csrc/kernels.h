@@ -51,12 +51,12 @@ struct DevSrc {
 struct DevSim6 {
     void *fields;          // E_x..E_z, H_x..H_z planes of N elements (re, im pairs when complex)
     void *psi;             // CPML auxiliary fields, 4 planes per PML axis over its two slabs
-    void *lor;             // Lorentz P then P_prev per E component (NULL: non-dispersive)
+    void *lor;             // Lorentz planes, per pole q: P_q of E_x..E_z then P_q-prev (6 planes; NULL: non-dispersive)
     const uint8_t *mat;    // per-cell material id
     const void *coef;      // [id][6]: 1/eps at E_x..E_z sites, 1/mu at H_x..H_z sites (0 masks)
-    const double *lorentz; // [id][3][2]: (delta_eps, omega0) per E component
-    const void *lorc;      // [id][3][4] in the run's precision: cp = 2 - w0^2 dt^2, cpm = 1 - sigma dt/2,
-                           // ce = delta_eps w0^2 dt^2, cd = 1/(1 + sigma dt/2) (march kernel)
+    const double *lorentz; // [id][pole][3][2]: (delta_eps, omega0) per E component
+    const void *lorc;      // [id][pole][3][4] in the run's precision: cp = 2 - w0^2 dt^2, cpm = 1 - sigma dt/2,
+                           // ce = delta_eps w0^2 dt^2 (0: no such pole), cd = 1/(1 + sigma dt/2)
     const void *pml;       // CPML profiles: axis a at pml_off[a]: [half][b, c, 1/kappa][n_a]
     const double *gw;
     double *acc;
@@ -77,7 +77,7 @@ struct DevSim6 {
     // ping-pong fields, psi and Lorentz planes (step n reads buffer (n-1)&1, writes n&1)
     int64_t fhalf, psi_half, lor_half;
     int tile_rows;         // march kernel: rows per strip tile (<= MARCH_H_MAX)
-    int pad6;
+    int npoles;            // Lorentz poles in use (present poles first at every site; 0: none)
 };
 
 struct DevEnt6 {
@@ -109,7 +109,8 @@ void launch_full(int fp64, int cplx, int dims, const DevSim6 *sims, const DevTil
 // MARCH_H rows, one full step per launch (both half steps), ping-pong buffers.  Tile entries:
 // DevEnt with loc = ly * MARCH_W + lx in bits 0..15, the field component in bits 16..18 and
 // bit 19 set for the weight of the imaginary part (complex fields).  variant: 1 = CPML planes
-// present, + 2 = Lorentz planes present.
+// present, + 2 = cells with one Lorentz pole at most, + 4 = cells with up to three poles.
+constexpr int MARCH_VARIANTS = 6;
 constexpr int MARCH_W = 30;
 constexpr int MARCH_H = 32;       // default rows per strip tile
 constexpr int MARCH_H_MAX = 64;   // largest tile height the planner builds (loc stays below 2^16)

@@ -119,8 +119,8 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
     std::vector<DevSim2D> s2;
     std::vector<DevSim6> s6;
     std::vector<DevTile> t2;
-    std::vector<DevTile> tv[4];       // march tiles by kernel variant
-    int voff[5] = {0, 0, 0, 0, 0};
+    std::vector<DevTile> tv[MARCH_VARIANTS];    // march tiles by kernel variant
+    int voff[MARCH_VARIANTS + 1] = {};
     std::vector<DevTile6> t6;
     std::vector<PlainEnt> pe;
     std::vector<PlainSim> ps;
@@ -238,11 +238,11 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
             ps.push_back(one);
         }
         if (march) {
-            for (int v = 0; v < 4; ++v) {
+            for (int v = 0; v < MARCH_VARIANTS; ++v) {
                 voff[v] = (int)t2.size();
                 t2.insert(t2.end(), tv[v].begin(), tv[v].end());
             }
-            voff[4] = (int)t2.size();
+            voff[MARCH_VARIANTS] = (int)t2.size();
         }
         void *d_sim = nullptr, *d_tiles = nullptr, *d_pe = nullptr, *d_ps = nullptr;
         size_t bsim = align256(full ? s6.size() * sizeof(DevSim6) : s2.size() * sizeof(DevSim2D));
@@ -279,10 +279,10 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                 launches += 2;
             } else if (march) {
                 if (cylr) {
-                    launch_march6_cyl(P->fp64, (const DevSim6 *)d_sim, (const DevTile *)d_tiles, voff[4], d_counter, n - 1, s);
+                    launch_march6_cyl(P->fp64, (const DevSim6 *)d_sim, (const DevTile *)d_tiles, voff[MARCH_VARIANTS], d_counter, n - 1, s);
                     ++launches;
                 }
-                for (int v = 0; v < 4 && !cylr; ++v)
+                for (int v = 0; v < MARCH_VARIANTS && !cylr; ++v)
                     if (voff[v + 1] > voff[v]) {
                         launch_march6(P->fp64, cplx, v, (const DevSim6 *)d_sim, (const DevTile *)d_tiles + voff[v],
                                       voff[v + 1] - voff[v], d_counter, n - 1, s);

@@ -22,7 +22,7 @@ constexpr double kTol = 1e-6;   // geometric tolerance, in cells
 struct Mat {
     double eps, mu;
     bool pec, pmc;
-    double de, w0;   // Lorentz pole
+    double de[CASIMIR_MAX_POLES], w0[CASIMIR_MAX_POLES];   // Lorentz poles, the present ones first
 };
 
 bool inside(const casimir_object &o, const double x[3], int dims, double d)
@@ -41,16 +41,23 @@ bool inside(const casimir_object &o, const double x[3], int dims, double d)
 Mat material_at(const PlanData &P, const double x[3])
 {
     const casimir_problem &p = P.prob;
-    Mat m{p.bg_eps, p.bg_mu, false, false, 0.0, 0.0};
+    Mat m{p.bg_eps, p.bg_mu, false, false, {}, {}};
     double d = P.dx;
     for (const auto &o : P.objects) {
         if (!inside(o, x, p.dims, d)) continue;
-        m = Mat{p.bg_eps, p.bg_mu, false, false, 0.0, 0.0};
+        m = Mat{p.bg_eps, p.bg_mu, false, false, {}, {}};
         switch (o.kind) {
         case CASIMIR_MAT_PEC: m.pec = true; break;
         case CASIMIR_MAT_PMC: m.pmc = true; break;
         case CASIMIR_MAT_DIELECTRIC: m.eps = o.eps; m.mu = o.mu; break;
-        case CASIMIR_MAT_LORENTZ: m.eps = o.eps_inf; m.mu = 1.0; m.de = o.delta_eps; m.w0 = o.omega0; break;
+        case CASIMIR_MAT_LORENTZ: {
+            m.eps = o.eps_inf;
+            m.mu = 1.0;
+            int q = 0;
+            for (int j = 0; j < CASIMIR_MAX_POLES; ++j)
+                if (o.delta_eps[j] != 0.0) { m.de[q] = o.delta_eps[j]; m.w0[q] = o.omega0[j]; ++q; }
+            break;
+        }
         }
     }
     return m;
@@ -215,7 +222,8 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err)
     int64_t ncell = (int64_t)p.n[0] * p.n[1] * p.n[2];
     g->mat.assign(ncell, 0);
     std::map<std::vector<double>, int> ids;
-    std::vector<double> key(narr + 6);
+    constexpr int NPK = 6 * CASIMIR_MAX_POLES;   // (delta_eps, omega0) per pole and E component
+    std::vector<double> key(narr + NPK);
     double L[3] = {p.n[0] * P.dx, p.n[1] * P.dx, p.n[2] * P.dx};
     for (int kk = 0; kk < p.n[2]; ++kk)
         for (int j = 0; j < p.n[1]; ++j)
@@ -242,10 +250,11 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err)
                         c = 0.0;
                     } else if (as.field == 0) {
                         c = (m.pec || wall) ? 0.0 : 1.0 / m.eps;
-                        if (!(m.pec || wall) && m.de != 0.0) {
-                            key[narr + 2 * as.comp] = m.de;
-                            key[narr + 2 * as.comp + 1] = m.w0;
-                        }
+                        if (!(m.pec || wall))
+                            for (int q = 0; q < CASIMIR_MAX_POLES && m.de[q] != 0.0; ++q) {
+                                key[narr + 6 * q + 2 * as.comp] = m.de[q];
+                                key[narr + 6 * q + 2 * as.comp + 1] = m.w0[q];
+                            }
                     } else {
                         c = m.pmc ? 0.0 : 1.0 / m.mu;
                     }
@@ -264,13 +273,17 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err)
             }
     g->nmat = (int)ids.size();
     g->table.assign((size_t)g->nmat * narr, 0.0);
-    g->lorentz.assign((size_t)g->nmat * 6, 0.0);
+    // poles in use: the highest pole present at any site
+    g->npoles = 0;
+    for (auto &kv : ids)
+        for (int q = 0; q < CASIMIR_MAX_POLES; ++q)
+            for (int c = 0; c < 3; ++c)
+                if (kv.first[narr + 6 * q + 2 * c] != 0.0) g->npoles = std::max(g->npoles, q + 1);
+    g->has_lorentz = g->npoles > 0;
+    g->lorentz.assign((size_t)g->nmat * 6 * g->npoles, 0.0);
     for (auto &kv : ids) {
         for (int a = 0; a < narr; ++a) g->table[(size_t)kv.second * narr + a] = kv.first[a];
-        for (int q = 0; q < 6; ++q) {
-            g->lorentz[(size_t)kv.second * 6 + q] = kv.first[narr + q];
-            if (kv.first[narr + q] != 0.0) g->has_lorentz = true;
-        }
+        for (int q = 0; q < 6 * g->npoles; ++q) g->lorentz[(size_t)kv.second * 6 * g->npoles + q] = kv.first[narr + q];
     }
     for (int a = 0; a < p.dims; ++a)
         if (p.bc[a] == CASIMIR_BC_PML) {
@@ -386,7 +399,14 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
     for (auto &o : P->objects) {
         if (o.kind < 0 || o.kind > 3 || o.shape < 0 || o.shape > 1) { *err = "object kind/shape"; return CASIMIR_EINVAL; }
         if (o.kind == CASIMIR_MAT_DIELECTRIC && !(o.eps > 0 && o.mu > 0)) { *err = "dielectric eps, mu must be > 0"; return CASIMIR_EINVAL; }
-        if (o.kind == CASIMIR_MAT_LORENTZ && !(o.eps_inf > 0 && o.omega0 > 0)) { *err = "lorentz eps_inf, omega0 must be > 0"; return CASIMIR_EINVAL; }
+        if (o.kind == CASIMIR_MAT_LORENTZ) {
+            if (!(o.eps_inf > 0)) { *err = "lorentz eps_inf must be > 0"; return CASIMIR_EINVAL; }
+            for (int j = 0; j < CASIMIR_MAX_POLES; ++j)
+                if (!(o.delta_eps[j] >= 0) || (o.delta_eps[j] > 0 && !(o.omega0[j] > 0))) {
+                    *err = "lorentz poles need delta_eps >= 0 and omega0 > 0";
+                    return CASIMIR_EINVAL;
+                }
+        }
     }
     if (!(p.bg_eps > 0 && p.bg_mu > 0)) { *err = "background eps, mu must be > 0"; return CASIMIR_EINVAL; }
     for (auto &f : P->faces) {
@@ -427,6 +447,29 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
             double lim = 0.25 * P->dt * P->dt * (2.0 * 4.0 / (P->dx * P->dx) + k.k[2] * k.k[2]);
             if (lim >= 1.0) { *err = "k_z beyond the time-step stability limit"; return CASIMIR_EINVAL; }
         }
+    // Dispersive media: the lattice dispersion relation Omega^2 eps(Omega^2) = k^2, with
+    // Omega = (2/dt) sin(omega dt / 2), has every root Omega^2 below X = 4/dt^2 (omega real)
+    // exactly when each pole has omega_j dt < 2 and X eps(X) exceeds the largest lattice k^2
+    // (x eps(x) increases on every branch between poles), i.e. eps(X) > (dt/2)^2 k_max^2.
+    {
+        double q = 3.0 * p.courant * p.courant;   // 3D: (dt/2)^2 * 12 / dx^2
+        if (p.dims == 2) {
+            q = 0.0;
+            for (auto &k : P->kpoints)
+                q = std::max(q, 0.25 * P->dt * P->dt * (8.0 / (P->dx * P->dx) + k.k[2] * k.k[2]));
+        }
+        for (auto &o : P->objects) {
+            if (o.kind != CASIMIR_MAT_LORENTZ) continue;
+            double epsX = o.eps_inf;
+            for (int j = 0; j < CASIMIR_MAX_POLES; ++j) {
+                if (o.delta_eps[j] == 0.0) continue;
+                const double wd2 = o.omega0[j] * o.omega0[j] * P->dt * P->dt;
+                if (wd2 >= 4.0) { *err = "lorentz pole with omega0 dt >= 2 (unstable)"; return CASIMIR_EINVAL; }
+                epsX -= o.delta_eps[j] * wd2 / (4.0 - wd2);
+            }
+            if (epsX <= q) { *err = "lorentz medium unstable at this time step (eps(4/dt^2) below the lattice bound)"; return CASIMIR_EINVAL; }
+        }
+    }
     // families
     std::vector<int> fams;
     if (p.polarization == CASIMIR_POL_TM || p.polarization == CASIMIR_POL_TETM) fams.push_back(FAM_TM);

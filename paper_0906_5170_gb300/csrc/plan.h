@@ -44,8 +44,9 @@ struct Geo {
     std::vector<uint8_t> mat;       // per cell
     std::vector<double> table;      // [id * narr + a]: 1/eps or 1/mu at that site, 0 masks PEC/PMC
     int nmat = 0;
-    // Lorentz ADE (FULL family only): per E-array id -> (delta_eps, omega0)
-    std::vector<double> lorentz;    // [id * 6 + 2*c + {0,1}] for c = 0..2
+    // Lorentz ADE (FULL family only): per E-array id and pole q -> (delta_eps, omega0)
+    std::vector<double> lorentz;    // [(id * npoles + q) * 6 + 2*c + {0,1}] for c = 0..2
+    int npoles = 0;                 // poles in use (present poles come first at every site)
     bool has_lorentz = false;
     double bloch_re[3] = {1, 1, 1}, bloch_im[3] = {0, 0, 0};
     double kz = 0.0;

@@ -193,21 +193,28 @@ k_full(const DevSim6 *__restrict__ sims, const DevTile6 *__restrict__ tiles,
                 R ce = coef[cpt];
                 Vt e = F.get(cpt, m);
                 Vt enew;
-                R de = S.lor ? (R)S.lorentz[6 * id + 2 * cpt] : (R)0;
-                if (de != (R)0) {
-                    R w2 = (R)(S.lorentz[6 * id + 2 * cpt + 1] * S.lorentz[6 * id + 2 * cpt + 1]);
-                    R dt = (R)S.dt_full, sg = (R)S.sigma;
+                if (S.lor && S.lorentz[6 * S.npoles * id + 2 * cpt] != 0.0) {
+                    // E' = a E + (a sum_q P_q - sum_q P_q' + b curl) / eps_inf
+                    const R dt = (R)S.dt_full, sg = (R)S.sigma;
                     Fields<R, CPLX> P{reinterpret_cast<R *>(S.lor), (size_t)N};
-                    Vt p = P.get(cpt, m), pm = P.get(3 + cpt, m);
-                    Vt pn;
-                    if (S.magnetic == 0 && n == 1)
-                        pn = (p.scale((R)2 - w2 * dt * dt) + e.scale(de * w2 * dt * dt)).scale((R)0.5);
-                    else
-                        pn = (p.scale((R)2 - w2 * dt * dt) - pm.scale((R)1 - (R)0.5 * sg * dt) +
-                              e.scale(de * w2 * dt * dt)).scale((R)1 / ((R)1 + (R)0.5 * sg * dt));
-                    P.put(3 + cpt, m, p);
-                    P.put(cpt, m, pn);
-                    enew = e.scale(a) + (p.scale(a) - pn + curl[cpt].scale(b)).scale(ce);
+                    Vt sp = curl[cpt].scale(b);
+                    for (int q = 0; q < S.npoles; ++q) {
+                        const double *lq = S.lorentz + 6 * (S.npoles * id + q) + 2 * cpt;
+                        const R de = (R)lq[0];
+                        if (de == (R)0) break;   // present poles come first
+                        const R w2 = (R)(lq[1] * lq[1]);
+                        Vt p = P.get(6 * q + cpt, m), pm = P.get(6 * q + 3 + cpt, m);
+                        Vt pn;
+                        if (S.magnetic == 0 && n == 1)
+                            pn = (p.scale((R)2 - w2 * dt * dt) + e.scale(de * w2 * dt * dt)).scale((R)0.5);
+                        else
+                            pn = (p.scale((R)2 - w2 * dt * dt) - pm.scale((R)1 - (R)0.5 * sg * dt) +
+                                  e.scale(de * w2 * dt * dt)).scale((R)1 / ((R)1 + (R)0.5 * sg * dt));
+                        P.put(6 * q + 3 + cpt, m, p);
+                        P.put(6 * q + cpt, m, pn);
+                        sp = sp + p.scale(a) - pn;
+                    }
+                    enew = e.scale(a) + sp.scale(ce);
                 } else {
                     enew = e.scale(a) + curl[cpt].scale(b * ce);
                 }

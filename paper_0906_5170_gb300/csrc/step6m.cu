@@ -16,7 +16,7 @@
 // Storage within one buffer is that of step6.cu: E_x..H_z planes of nx*ny
 // elements (real and imaginary planes when complex), psi planes per PML axis
 // over its two slabs (planes 0, 1 for the E update, 2, 3 for the H update),
-// Lorentz P then P_prev per E component.
+// per Lorentz pole, P then P_prev per E component.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -80,25 +80,31 @@ __device__ __forceinline__ void st(R *__restrict__ p, int plane, unsigned N, uns
 // f = E(j+1), q = H(j), m, P(j), psi(j) of all four planes.  Magnetic sources:
 // f = H(j+1), q = E(j+1) (old), m of row j+1, P(j+1), psi planes 0, 1 of row j+1
 // and 2, 3 of row j.
-template <typename R, bool CPLX>
+// P and P_prev of pole q, component k at p[3 q + k], pm[3 q + k] (NPL poles: 0, 1 or 3).
+template <typename R, bool CPLX, int NPL>
 struct RowIn {
+    static constexpr int NP = NPL > 0 ? NPL : 1;
     Z<R, CPLX> f[3], q[3];
     int m;
-    Z<R, CPLX> p[3], pm[3];
+    Z<R, CPLX> p[3 * NP], pm[3 * NP];
     Z<R, CPLX> px[4], py[4];
 };
 
 // CYL: cylindrical (r, z) lattice (Sec. III C), x = r from the symmetry axis, y = z, stored
 // components (E_r, E_z, E_phi, H_r, H_z, H_phi) on the sites of (E_x, E_y, E_z, H_x, H_y, H_z);
 // d/dphi -> i m in the real-phase form (kzA, kzB = +-m), per-lane radial factors.
+// NPL: Lorentz poles the variant carries (0: no dispersive cell in the tile, 1: one pole at
+// most, 3: up to three; a tile takes the smallest that covers its materials).
 // PF: rows whose inputs are in flight ahead of the row being computed (1 or 2; 2 where the
 // registers allow it without spilling, i.e. without the CPML planes)
-template <typename R, bool CPLX, bool PML, bool LOR, int MINB, bool CYL = false, int PFREQ = 1>
+template <typename R, bool CPLX, bool PML, int NPL, int MINB, bool CYL = false, int PFREQ = 1>
 __global__ void __launch_bounds__(WARPS6 * 32, MINB)
 k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, int ntiles,
          const int64_t *__restrict__ launch_base, int64_t launch_add)
 {
     using V = Z<R, CPLX>;
+    using In = RowIn<R, CPLX, NPL>;
+    constexpr bool LOR = NPL > 0;
     constexpr int PF6 = PFREQ < PFMAX ? PFREQ : PFMAX;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ti = blockIdx.x * WARPS6 + warp;
@@ -132,8 +138,9 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     if constexpr (LOR) {
         lin = reinterpret_cast<const R *>(S.lor) + (size_t)pin_par * S.lor_half;
         lout = reinterpret_cast<R *>(S.lor) + (size_t)pout_par * S.lor_half;
-        lc = reinterpret_cast<const R *>(S.lorc);                    // [id][3][cp, cpm, ce, cd]
+        lc = reinterpret_cast<const R *>(S.lorc);                    // [id][pole][3][cp, cpm, ce, cd]
     }
+    const int np = LOR ? S.npoles : 0;
 
     const int i0 = t.i0;
     const int w = min(MARCH_W, nx - i0);
@@ -179,8 +186,8 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     auto iny = [&](int j) { return PML && dY > 0 && (j < dY || j >= ny - dY); };
     auto gxi = [&](int j) { return (unsigned)(j * (2 * dX) + sx); };
     auto gyi = [&](int j) { return (unsigned)((j < dY ? j : j - (ny - 2 * dY)) * nx + col); };
-    // the material's Lorentz coefficients (ce of component k nonzero: dispersive)
-    auto disp = [&](int m, int k) -> bool { if constexpr (LOR) return lc[12 * m + 4 * k + 2] != (R)0; else return false; };
+    // the material's Lorentz coefficients (ce of pole 0 of component k nonzero: dispersive)
+    auto disp = [&](int m, int k) -> bool { if constexpr (LOR) return lc[12 * np * m + 4 * k + 2] != (R)0; else return false; };
 
     // d/dz of a field of the set {Ex, Ey, Hz} (A) or {Ez, Hx, Hy} (B)
     auto dzA = [&](V f) -> V { if constexpr (CPLX) return f.ik(kc); else return f * kA; };
@@ -191,7 +198,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     auto str = [&](V d, const R *pr, V psi, V &pn) -> V { pn = psi * pr[0] + d * pr[1]; return d * pr[2] + pn; };
 
     // loads of the psi planes of row j (lo..hi of 0..3) into px / py
-    auto load_psi = [&](RowIn<R, CPLX> &in, int j, int lo, int hi) {
+    auto load_psi = [&](In &in, int j, int lo, int hi) {
         if constexpr (PML) {
             if (inx) {
                 const unsigned g = gxi(j);
@@ -203,16 +210,18 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
             }
         }
     };
-    // P of the dispersive components of material m at cell g (zero elsewhere: never read)
-    auto load_lor = [&](RowIn<R, CPLX> &in, unsigned g, int m) {
+    // P of the poles material m has at cell g, per component (absent poles: never read)
+    auto load_lor = [&](In &in, unsigned g, int m) {
         if constexpr (LOR) {
+            const R *lm = lc + 12 * np * m;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                if (disp(m, k)) {
-                    in.p[k] = ld<R, CPLX>(lin, k, N, g);
-                    in.pm[k] = ld<R, CPLX>(lin, 3 + k, N, g);
-                }
-            }
+            for (int q = 0; q < NPL; ++q)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    if (q < np && lm[12 * q + 4 * k + 2] != (R)0) {
+                        in.p[3 * q + k] = ld<R, CPLX>(lin, 6 * q + k, N, g);
+                        in.pm[3 * q + k] = ld<R, CPLX>(lin, 6 * q + 3 + k, N, g);
+                    }
         }
     };
 
@@ -253,7 +262,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
         }
     };
     // E at row j from H at rows j and j-1: new E, the E-plane psi (0, 1) and P written when wr
-    auto updE = [&](int j, int m, const V hh[3], V hxp, V hzp, const V eo[3], const RowIn<R, CPLX> &in, R aa, R bb,
+    auto updE = [&](int j, int m, const V hh[3], V hxp, V hzp, const V eo[3], const In &in, R aa, R bb,
                     bool wr, unsigned g, V eo_new[3]) {
         if (j - 1 < 0) { hxp = hxp.ph(byr, -byi); hzp = hzp.ph(byr, -byi); }
         V dyHz = (hh[2] - hzp) * idx, dyHx = (hh[0] - hxp) * idx;
@@ -289,17 +298,26 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             if constexpr (LOR) {
-                const R *l4 = lc + 12 * m + 4 * k;
-                const R ce = l4[2];
-                if (ce != (R)0) {
-                    // P^{n+1} = [cp P^n - cpm P^{n-1} + ce E^n] cd; the first electric step starts from rest
-                    const V pn = first_e ? (in.p[k] * l4[0] + eo[k] * ce) * (R)0.5
-                                         : (in.p[k] * l4[0] - in.pm[k] * l4[1] + eo[k] * ce) * l4[3];
-                    if (wr) {
-                        st<R, CPLX>(lout, k, N, g, pn);
-                        st<R, CPLX>(lout, 3 + k, N, g, in.p[k]);
+                const R *l4 = lc + 12 * np * m + 4 * k;
+                if (l4[2] != (R)0) {
+                    // per pole: P^{n+1} = [cp P^n - cpm P^{n-1} + ce E^n] cd (the first electric step
+                    // starts from rest); E^{n+1} = a E^n + (a sum P^n - sum P^{n+1} + b curl) / eps_inf
+                    V sp = c3[k] * bb;
+#pragma unroll
+                    for (int q = 0; q < NPL; ++q) {
+                        const R *lq = l4 + 12 * q;
+                        if (q > 0 && !(q < np && lq[2] != (R)0)) continue;   // pole q absent here
+                        const R ce = lq[2];
+                        const V p = in.p[3 * q + k], pm = in.pm[3 * q + k];
+                        const V pn = first_e ? (p * lq[0] + eo[k] * ce) * (R)0.5
+                                             : (p * lq[0] - pm * lq[1] + eo[k] * ce) * lq[3];
+                        if (wr) {
+                            st<R, CPLX>(lout, 6 * q + k, N, g, pn);
+                            st<R, CPLX>(lout, 6 * q + 3 + k, N, g, p);
+                        }
+                        sp = sp + p * aa - pn;
                     }
-                    eo_new[k] = eo[k] * aa + (in.p[k] * aa - pn + c3[k] * bb) * cm[k];
+                    eo_new[k] = eo[k] * aa + sp * cm[k];
                     continue;
                 }
             }
@@ -311,13 +329,13 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
         const int j0 = t.j0;
         const int jm = rowp(j0 - 1);
         const unsigned gm = (unsigned)(jm * nx + col), g0 = (unsigned)(j0 * nx + col);
-        RowIn<R, CPLX> cur, nxt, nx2;
+        In cur, nxt, nx2;
         if (electric) {
             // H (a = 1, b = h) then E (a, b_sigma).  Carried: E^n of row j, H^{n+1/2} of row j-1.
             // The material of row j+2 is loaded at row j, so that P of row j+1 loads only where dispersive.
             V e[3], hp[3];
             {
-                RowIn<R, CPLX> in0;
+                In in0;
                 const V em[3] = {ld<R, CPLX>(fin, 0, N, gm), ld<R, CPLX>(fin, 1, N, gm), ld<R, CPLX>(fin, 2, N, gm)};
                 const V hm[3] = {ld<R, CPLX>(fin, 3, N, gm), ld<R, CPLX>(fin, 4, N, gm), ld<R, CPLX>(fin, 5, N, gm)};
 #pragma unroll
@@ -325,7 +343,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                 load_psi(in0, jm, 2, 4);
                 updH(jm, mat[gm], em, e[0], e[2], hm, in0.px, in0.py, (R)1, hfirst, false, hp);
             }
-            auto load_row = [&](RowIn<R, CPLX> &in, int j, int m) {
+            auto load_row = [&](In &in, int j, int m) {
                 const unsigned g = (unsigned)(j * nx + col), gn = (unsigned)(rowp(j + 1) * nx + col);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
@@ -370,7 +388,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
             V hq[3], e[3];
             int m = mat[g0];
             {
-                RowIn<R, CPLX> in0;
+                In in0;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) hq[k] = ld<R, CPLX>(fin, 3 + k, N, g0);
                 const V eo[3] = {ld<R, CPLX>(fin, 0, N, g0), ld<R, CPLX>(fin, 1, N, g0), ld<R, CPLX>(fin, 2, N, g0)};
@@ -379,7 +397,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                 updE(j0, m, hq, ld<R, CPLX>(fin, 3, N, gm), ld<R, CPLX>(fin, 5, N, gm), eo, in0, (R)1, hfirst, own, g0, e);
             }
             // inputs of row step j: row j+1 (fields, material mn, P) and the H-plane psi of row j
-            auto load_row = [&](RowIn<R, CPLX> &in, int j, int mn) {
+            auto load_row = [&](In &in, int j, int mn) {
                 const int jn = rowp(j + 1);
                 const unsigned gn = (unsigned)(jn * nx + col);
 #pragma unroll
@@ -447,17 +465,20 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     }
 }
 
-// MINB per variant (none, CPML, Lorentz, both): resident CTAs per SM asked of the register allocator
-template <typename R, bool CPLX, int M0, int M1, int M2, int M3>
+// MINB per variant (none, CPML, one pole, one pole + CPML, three poles, three poles + CPML):
+// resident CTAs per SM asked of the register allocator
+template <typename R, bool CPLX, int M0, int M1, int M2, int M3, int M4, int M5>
 void launch_t(int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles, const int64_t *lb, int64_t la,
               cudaStream_t st)
 {
     const int grid = (ntiles + WARPS6 - 1) / WARPS6;
     switch (variant) {
-    case 0: k_march6<R, CPLX, false, false, M0, false, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    case 1: k_march6<R, CPLX, true, false, M1, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    case 2: k_march6<R, CPLX, false, true, M2, false, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    default: k_march6<R, CPLX, true, true, M3, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 0: k_march6<R, CPLX, false, 0, M0, false, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 1: k_march6<R, CPLX, true, 0, M1, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 2: k_march6<R, CPLX, false, 1, M2, false, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 3: k_march6<R, CPLX, true, 1, M3, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    case 4: k_march6<R, CPLX, false, 3, M4, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+    default: k_march6<R, CPLX, true, 3, M5, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
     }
 }
 
@@ -468,8 +489,8 @@ void launch_march6_cyl(int fp64, const DevSim6 *sims, const DevTile *tiles, int 
 {
     if (ntiles <= 0) return;
     const int grid = (ntiles + WARPS6 - 1) / WARPS6;
-    if (fp64) k_march6<double, false, false, false, 4, true, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
-    else k_march6<float, false, false, false, 6, true, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
+    if (fp64) k_march6<double, false, false, 0, 4, true, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
+    else k_march6<float, false, false, 0, 6, true, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
 }
 
 void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles,
@@ -477,11 +498,11 @@ void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const D
 {
     if (ntiles <= 0) return;
     if (fp64) {
-        if (cplx) launch_t<double, true, 3, 2, 2, 1>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
-        else launch_t<double, false, 4, 3, 3, 2>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        if (cplx) launch_t<double, true, 3, 2, 2, 1, 1, 1>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        else launch_t<double, false, 4, 3, 3, 2, 2, 2>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
     } else {
-        if (cplx) launch_t<float, true, 4, 4, 3, 3>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
-        else launch_t<float, false, 6, 4, 5, 4>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        if (cplx) launch_t<float, true, 4, 4, 3, 3, 2, 2>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        else launch_t<float, false, 6, 4, 5, 4, 3, 3>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
     }
 }
 

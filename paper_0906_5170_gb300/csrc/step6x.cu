@@ -199,16 +199,22 @@ k_line3(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles,
                 const V e = e3[k];
                 V en = e * a + c3[k] * (b * cm[k]);
                 if (P) {
-                    const R *l4 = lc + 12 * m + 4 * k;
-                    const R ce = l4[2];
-                    if (ce != (R)0) {
-                        const V p = ld3<R, CPLX>(P, k, N, g), pm = ld3<R, CPLX>(P, 3 + k, N, g);
-                        const V pn = first_e ? (p * l4[0] + e * ce) * (R)0.5 : (p * l4[0] - pm * l4[1] + e * ce) * l4[3];
-                        if (valid) {
-                            st3<R, CPLX>(P, 3 + k, N, g, p);
-                            st3<R, CPLX>(P, k, N, g, pn);
+                    const R *l4 = lc + 12 * S.npoles * m + 4 * k;
+                    if (l4[2] != (R)0) {
+                        // per pole q (present poles first): P_q' = [cp P_q - cpm P_q-prev + ce E] cd
+                        V sp = c3[k] * b;
+                        for (int q = 0; q < S.npoles; ++q, l4 += 12) {
+                            const R ce = l4[2];
+                            if (ce == (R)0) break;
+                            const V p = ld3<R, CPLX>(P, 6 * q + k, N, g), pm = ld3<R, CPLX>(P, 6 * q + 3 + k, N, g);
+                            const V pn = first_e ? (p * l4[0] + e * ce) * (R)0.5 : (p * l4[0] - pm * l4[1] + e * ce) * l4[3];
+                            if (valid) {
+                                st3<R, CPLX>(P, 6 * q + 3 + k, N, g, p);
+                                st3<R, CPLX>(P, 6 * q + k, N, g, pn);
+                            }
+                            sp = sp + p * a - pn;
                         }
-                        en = e * a + (p * a - pn + c3[k] * b) * cm[k];
+                        en = e * a + sp * cm[k];
                     }
                 }
                 if (valid) st3<R, CPLX>(F, k, N, g, en);

@@ -126,3 +126,69 @@ def test_plan_options_defaults_and_explicit():
     a = pk.Plan(q).sims()
     b = pk.Plan(q, options={"march_rows": 64}).sims()
     assert np.array_equal(a, b)
+
+
+def _small_grating(**kw):
+    args = dict(resolution=16, nk_x=2, nk_z=2, n_harm=2, t_max=2.0, courant=0.2, pml_units=0.25,
+                precision="fp64")
+    args.update(kw)
+    return W.grating_silica(0.5, **args)
+
+
+def test_plan_sim_list_matches_oracle_multipole():
+    p = _small_grating()
+    plan = pk.Plan(p)
+    got = [tuple(int(v) for v in r) for r in plan.sims()]
+    assert got == _sim_tuples(p)
+    assert plan.info()["n_sims"] == len(got)
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda p: p.update(courant=0.5),                                   # silicon's pole: eps(4/dt^2) < 0.5
+    lambda p: p["objects"][0].update(delta_eps=[0.829, -0.095, 1.098]),
+    lambda p: p["objects"][0].update(omega0=[0.29, 0.0, 67.8]),
+    lambda p: p["objects"][0].update(omega0=[0.29, 0.5, 700.0]),       # omega0 dt >= 2
+])
+def test_plan_rejects_unstable_or_invalid_poles(mutate):
+    p = _small_grating()
+    mutate(p)
+    with pytest.raises(pk.CasimirError) as e:
+        pk.Plan(p)
+    assert e.value.code == -1
+
+
+def test_binding_rejects_malformed_pole_lists():
+    p = _small_grating()
+    p["objects"][0].update(delta_eps=[1.0, 2.0], omega0=[1.0])
+    with pytest.raises(ValueError):
+        pk.Plan(p)
+    p["objects"][0].update(delta_eps=[1.0] * 4, omega0=[1.0] * 4)
+    with pytest.raises(ValueError):
+        pk.Plan(p)
+
+
+@pytest.mark.parametrize("eps_x,stable", [(0.52, True), (0.48, False)])
+def test_stability_bound_matches_the_oracle(eps_x, stable):
+    """The planner admits a uniform one-pole medium exactly when eps(4/dt^2) exceeds the
+    lattice bound (dt/2)^2 k_max^2 = 2 courant^2 = 0.5; the oracle's fields stay bounded
+    just inside it and blow up just outside."""
+    import math
+    res, cour, de, nx = 8.0, 0.5, 10.0, 8
+    r = 1.0 - eps_x                    # eps(X) = 1 - de y / (4 - y), y = (w0 dt)^2
+    y = 4 * r / (de + r)
+    w0 = math.sqrt(y) / (cour / res)
+    p = W._base(2, (nx, nx, 1), res, 3000, sigma=0.0, courant=cour)
+    p["bc"] = ["periodic", "periodic", "pec"]
+    p["objects"] = [{"shape": "box", "lo": [-1, -1, 0], "hi": [10, 10, 0], "kind": "lorentz",
+                     "eps_inf": 1.0, "delta_eps": de, "omega0": w0}]
+    q = dict(p, polarization="full", faces=[{"axis": 1, "sign": 1, "pos": 0.5, "lo": [0, 0.5, 0], "hi": [1, 0.5, 0]}])
+    if stable:
+        pk.Plan(q)
+    else:
+        with pytest.raises(pk.CasimirError):
+            pk.Plan(q)
+    st = oracle.grid_setup(p)
+    with np.errstate(all="ignore"):
+        s = np.abs(oracle.run_vectors(p, st, False, {(2, 3 * nx + 3): 1.0}, {(2, 3 * nx + 3): 1.0}, pol="TM"))
+    late = np.nan_to_num(s[-300:], nan=np.inf).max()
+    assert (late < 10.0) == stable
