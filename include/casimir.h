@@ -154,6 +154,9 @@ typedef struct {
     int64_t device_bytes;      /* device memory the plan needs while running */
     int64_t bytes_per_update;  /* algorithmic bytes per cell-update of the dominant kernel */
     int64_t upload_bytes;      /* host-to-device bytes copied when the plan is first admitted */
+    int64_t bytes_per_step;    /* algorithmic bytes of one time step over all simulations: every
+                                  stored field, CPML auxiliary and Lorentz (P, P_prev per present
+                                  pole) value read and written once, plus the material ids */
 } casimir_plan_info;
 
 typedef struct {

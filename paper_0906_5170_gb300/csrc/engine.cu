@@ -93,6 +93,19 @@ static int prepare_plan(casimir_plan_t *P)
         P->coef_off.push_back((int64_t)P->coef_all.size());
         P->coef_all.insert(P->coef_all.end(), g.table.begin(), g.table.end());
         while (P->coef_all.size() % 32) P->coef_all.push_back(0.0);
+        // (site, pole) pairs of the grid: the Lorentz planes one step reads and writes
+        {
+            int64_t pairs = 0;
+            if (g.family == FAM_FULL && g.has_lorentz) {
+                std::vector<int64_t> per_id(g.nmat, 0);
+                for (int id = 0; id < g.nmat; ++id)
+                    for (int q = 0; q < g.npoles; ++q)
+                        for (int c = 0; c < 3; ++c)
+                            if (g.lorentz[((size_t)id * g.npoles + q) * 6 + 2 * c] != 0.0) ++per_id[id];
+                for (uint8_t id : g.mat) pairs += per_id[id];
+            }
+            P->lor_sites.push_back(pairs);
+        }
         P->lor_off.push_back((int64_t)P->lor_all.size());
         if (g.family == FAM_FULL) P->lor_all.insert(P->lor_all.end(), g.lorentz.begin(), g.lorentz.end());
         // kernel form of the Lorentz recurrence of every pole: P' = (cp P - cpm P_prev + ce E) cd
@@ -249,6 +262,7 @@ static int prepare_plan(casimir_plan_t *P)
                             for (int c = 0; c < 3; ++c)
                                 if (g.lorentz[((size_t)id * g.npoles + q) * 6 + 2 * c] != 0.0) dmat[id] = std::max(dmat[id], q + 1);
                     const int dX = g.has_pml[0] ? D.prob.pml_cells[0] : 0, dY = g.has_pml[1] ? D.prob.pml_cells[1] : 0;
+                    const bool xper = D.prob.bc[0] == CASIMIR_BC_PERIODIC, yper = D.prob.bc[1] == CASIMIR_BC_PERIODIC;
                     auto wrapc = [](int i, int n) { return ((i % n) + n) % n; };
                     std::vector<int> vs((size_t)tx * ty, 0);
                     for (int tj = 0; tj < ty; ++tj)
@@ -263,6 +277,10 @@ static int prepare_plan(casimir_plan_t *P)
                                 for (int ii = i0 - 1; ii <= i0 + w; ++ii) {
                                     const int i = wrapc(ii, hs.nx);
                                     if (dX > 0 && (i < dX || i >= hs.nx - dX)) pml = true;
+                                    // across a closed (PEC or CPML) wall the halo cell is the wall
+                                    // row or column: the components the tile uses there are masked
+                                    // and carry no poles
+                                    if ((jj != j && !yper) || (ii != i && !xper)) continue;
                                     poles = std::max(poles, dmat[g.mat[(size_t)j * hs.nx + i]]);
                                 }
                             }
@@ -1285,6 +1303,19 @@ int casimir_plan_get_info(const casimir_plan_t *P, casimir_plan_info *info)
     int cf = full && P->sims[0].cplx ? 2 : 1;
     info->bytes_per_update = (full ? 12 * cf : 6) * (int64_t)P->rsize + 1;
     info->upload_bytes = P->table_bytes;
+    // one step over every simulation: the field planes, the CPML psi planes of the slab cells
+    // (4 per PML axis) and P, P_prev of every (site, pole) pair, each read and written once
+    int64_t bps = 0;
+    for (const HostSim &hs : P->sims) {
+        const int64_t N = (int64_t)hs.nx * hs.ny * hs.nz, c = hs.cplx ? 2 : 1, rs = P->rsize;
+        bps += N * ((hs.full ? 12 * c : 6) * rs + 1);
+        if (!hs.full) continue;
+        const int n[3] = {hs.nx, hs.ny, hs.nz};
+        for (int a = 0; a < 3; ++a)
+            if (P->data.geos[hs.geo].has_pml[a]) bps += 4 * 2 * c * rs * (N / n[a]) * 2 * P->data.prob.pml_cells[a];
+        bps += P->lor_sites[hs.geo] * 4 * c * rs;
+    }
+    info->bytes_per_step = bps;
     return CASIMIR_OK;
 }
 

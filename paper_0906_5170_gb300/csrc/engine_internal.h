@@ -112,9 +112,10 @@ struct casimir_plan {
     std::vector<DevEnt> entsM;
     std::vector<DevEnt6> ents6;
     std::vector<DevSrc6> src6;
-    std::vector<double> lor_all;      // per geo [id][6]
+    std::vector<int64_t> lor_sites;   // per geo: (E site, present pole) pairs over the grid
+    std::vector<double> lor_all;      // per geo [id][pole][6]
     std::vector<int64_t> lor_off;     // per geo, elements
-    std::vector<double> lorc_all;     // per geo [id][3][4] march-kernel Lorentz coefficients
+    std::vector<double> lorc_all;     // per geo [id][pole][3][4] kernel Lorentz coefficients
     std::vector<int64_t> lorc_off;    // per geo, elements
     std::vector<double> pml_all;      // per geo, per PML axis [half][b, c, 1/kappa][n_a]
     std::vector<std::array<int64_t, 3>> pml_off;   // per geo and axis, elements (-1: no PML)

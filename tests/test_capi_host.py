@@ -192,3 +192,25 @@ def test_stability_bound_matches_the_oracle(eps_x, stable):
         s = np.abs(oracle.run_vectors(p, st, False, {(2, 3 * nx + 3): 1.0}, {(2, 3 * nx + 3): 1.0}, pol="TM"))
     late = np.nan_to_num(s[-300:], nan=np.inf).max()
     assert (late < 10.0) == stable
+
+
+def test_plan_bytes_per_step_counts_every_plane():
+    # an 8 x 8 periodic k_z cross-section filled with a two-pole medium, real FP32 fields: per cell
+    # 6 field values read and written (48 B) + the material id, and per E site and pole P, P_prev
+    # read and written (16 B); no walls, so all 3 x 64 E sites carry both poles
+    p = W._base(2, (8, 8, 1), 8.0, 10)
+    p["bc"] = ["periodic", "periodic", "pec"]
+    p["objects"] = [{"shape": "box", "lo": [-1, -1, 0], "hi": [2, 2, 0], "kind": "lorentz", "eps_inf": 2.0,
+                     "delta_eps": [1.0, 0.5], "omega0": [2.0, 3.0]}]
+    p["faces"] = [{"axis": 1, "sign": 1, "pos": 0.5, "lo": [0, 0.5, 0], "hi": [1, 0.5, 0]}]
+    p["polarization"] = "full"
+    p["k_points"] = [{"k": [0, 0, 1.0], "weight": 1.0}]
+    p["precision"] = "fp32"
+    i = pk.Plan(p).info()
+    assert i["bytes_per_step"] == i["n_sims"] * (64 * 49 + 64 * 3 * 2 * 16)
+    # CPML along y (2 x 2 slab rows of 8 cells, 4 psi planes read and written) instead of the poles
+    p["objects"] = []
+    p["bc"] = ["periodic", "pml", "pec"]
+    p["pml_cells"] = [0, 2, 0]
+    i = pk.Plan(p).info()
+    assert i["bytes_per_step"] == i["n_sims"] * (64 * 49 + 4 * 8 * 4 * 2 * 4)
