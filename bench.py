@@ -182,7 +182,7 @@ def measure_configs(pk, ctx, peak):
     algorithmic bytes.  Bounded subsets where the full configuration would take minutes."""
     import workloads as W
     out = {}
-    kp = W.config3_kz_points(0.5)
+    kp = W.config3_kz_points(0.5, medium=W.waveguide_material())
     cases = {
         "plates_2d_tm_fp64_full": ([W.config1_plates()], "full configuration (24 sims, 60x40, 4000 steps, FP64)"),
         "waveguides_kz_cpml_lorentz": ([W.config3_waveguides(0.5, k_points=[kp[i] for i in (0, 8, 16, 24)])],
@@ -368,7 +368,7 @@ def profile_case_problems(case, steps):
     if case == "piston64":     # the same in FP64 mode (is the FP64 leapfrog bound by HBM or by FP64 arithmetic?)
         return [W.config2_piston(W.config2_heights()[3], n_harm=16, n_steps=steps, precision="fp64")]
     if case == "waveguides":   # 256 x 256 CPML cell, Lorentz guides, 2 k_z x 6 harmonics: 192 simulations
-        kp = W.config3_kz_points(0.5)
+        kp = W.config3_kz_points(0.5, medium=W.waveguide_material())
         return [W.config3_waveguides(0.5, n_harm=6, n_steps=steps, k_points=[kp[3], kp[12]])]
     if case == "sphere3d":     # 160^3 CPML cell, 1 harmonic per face: 20 simulations
         return [W.config4_sphere_notch(0.55, seed=1, n_harm=1, n_steps=steps)]

@@ -214,3 +214,20 @@ def test_plan_bytes_per_step_counts_every_plane():
     p["pml_cells"] = [0, 2, 0]
     i = pk.Plan(p).info()
     assert i["bytes_per_step"] == i["n_sims"] * (64 * 49 + 4 * 8 * 4 * 2 * 4)
+
+
+@pytest.mark.parametrize("scale", [0.15, 1.0])
+def test_serving_mix_is_stable(scale):
+    # every request of the seeded serving trace passes the planner's stability bounds, and the
+    # coarsest Lorentz waveguide stays bounded in the oracle at its largest k_z (that k_z grows
+    # without bound when the grid ignores the medium: 1e57 within 240 steps)
+    reqs = W.serving_requests(0, n_requests=200, rate=50.0, scale=scale)
+    for _, p in reqs:
+        if scale == 0.15 or p.get("kind") == "waveguide":   # the dispersive kind (3D spheres plan slowly)
+            pk.Plan(p)
+    if scale == 0.15:
+        wg = min((p for _, p in reqs if p.get("kind") == "waveguide"), key=lambda p: p["resolution"])
+        kp = max(wg["k_points"], key=lambda k: k["k"][2])
+        q = dict(wg, n_steps=2000, k_points=[kp])
+        s = np.abs(oracle.run_sim(q, oracle.enumerate_sims(q)[0], oracle.grid_setup(q, kp["k"])))
+        assert np.all(np.isfinite(s)) and s[-200:].max() < s[:200].max()

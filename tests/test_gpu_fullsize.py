@@ -66,7 +66,7 @@ def test_piston_sweep_full_size(ctx):
 
 
 def test_waveguides_full_size(ctx):
-    kp = W.config3_kz_points(0.5)
+    kp = W.config3_kz_points(0.5, medium=W.waveguide_material())
     p = W.config3_waveguides(0.5, k_points=[kp[i] for i in (0, 7, 15, 22)])
     per = _run_together(ctx, [p])[0]
     n = len(per)

@@ -177,16 +177,28 @@ def config3_gaps():
     return [round(16.0 * (0.3 + 0.1 * j)) / 16.0 for j in range(8)]
 
 
-def config3_kz_points(gap, n=32, resolution=32, courant=0.5):
+def waveguide_material():
+    """The waveguides' single undamped Lorentz pole (eps_inf 1, delta_eps 10.7, omega_0 3)."""
+    return {"kind": "lorentz", "eps_inf": 1.0, "delta_eps": 10.7, "omega0": 3.0}
+
+
+def config3_kz_points(gap, n=32, resolution=32, courant=0.5, medium=None):
     """n Gauss-Legendre nodes for the k_z integral on [0, K].
 
     K = min(12/gap, 0.8 k_max): the integrand decays like exp(-2 gap k_z), and k_max is
-    the largest k_z the time step resolves, (dt/2)^2 (8/Delta^2 + k_max^2) = 1.
+    the largest k_z the time step resolves, (dt/2)^2 (8/Delta^2 + k_max^2) = min(1, eps_X),
+    where eps_X is the Lorentz `medium`'s permittivity at Omega^2 = 4/dt^2 (a lattice mode
+    above it grows without bound) and 1 without one.
     The weight includes the Jacobian K/2 and the 1/pi of the k_z measure.
     """
     d = 1.0 / resolution
     dt = courant * d
-    kmax = math.sqrt((2.0 / dt) ** 2 - 8.0 / d**2)
+    eps_x = 1.0
+    if medium is not None and medium.get("kind") == "lorentz":
+        des, ws = medium["delta_eps"], medium["omega0"]
+        des, ws = ([des], [ws]) if np.isscalar(des) else (des, ws)
+        eps_x = medium["eps_inf"] - sum(de * (w * dt) ** 2 / (4.0 - (w * dt) ** 2) for de, w in zip(des, ws))
+    kmax = math.sqrt(max(0.0, (2.0 / dt) ** 2 * min(1.0, eps_x) - 8.0 / d**2))
     K = min(12.0 / gap, 0.8 * kmax)
     u, w = np.polynomial.legendre.leggauss(n)
     return [{"k": [0.0, 0.0, float(K * (1 + ui) / 2)], "weight": float(wi * K / 2 / math.pi)}
@@ -201,7 +213,7 @@ def config3_waveguides(gap, *, resolution=32, n_cells=256, pml_units=1.0, n_harm
     L = n_cells * d
     p = _base(2, (n_cells, n_cells, 1), resolution, n_steps)
     xc, yc = L / 2, L / 2
-    mat = {"kind": "lorentz", "eps_inf": 1.0, "delta_eps": 10.7, "omega0": 3.0}
+    mat = waveguide_material()
     p["objects"] = [
         dict(shape="box", lo=[xc - gap / 2 - 1.0, yc - 0.25, 0.0], hi=[xc - gap / 2, yc + 0.25, 0.0], **mat),
         dict(shape="box", lo=[xc + gap / 2, yc - 0.25, 0.0], hi=[xc + gap / 2 + 1.0, yc + 0.25, 0.0], **mat),
@@ -212,7 +224,8 @@ def config3_waveguides(gap, *, resolution=32, n_cells=256, pml_units=1.0, n_harm
     p["faces"] = box_faces([xc + gap / 2 - d, yc - 0.25 - d], [xc + gap / 2 + 1.0 + d, yc + 0.25 + d], 2)
     p["n_harm"] = n_harm
     p["polarization"] = "full"
-    p["k_points"] = config3_kz_points(gap, resolution=resolution) if k_points is None else k_points
+    p["k_points"] = (config3_kz_points(gap, resolution=resolution, medium=mat) if k_points is None
+                     else k_points)
     p["force_axis"] = 0
     p["g_variant"] = "plain"
     p["precision"] = precision
@@ -320,7 +333,7 @@ def _serving_waveguide(side, n_harm, rng):
     side = max(32, side // 16 * 16)
     res = side / 8.0
     gap = float(rng.uniform(0.3, 1.0))
-    kp = config3_kz_points(gap, n=4, resolution=res)
+    kp = config3_kz_points(gap, n=4, resolution=res, medium=waveguide_material())
     p = config3_waveguides(round(gap * res / 2) * 2 / res, resolution=res, n_cells=side, pml_units=1.0,
                            n_harm=int(min(n_harm, 12)), n_steps=int(round(30.0 / (0.5 / res))), k_points=kp)
     p["kind"] = "waveguide"
