@@ -1028,6 +1028,7 @@ int casimir_ctx_create(int device, uint64_t budget, casimir_ctx_t **out)
     CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return fail(CASIMIR_EINVAL, "no such CUDA device");
     CUDA_TRY(cudaSetDevice(device));
+    march6_prepare();
     auto *c = new casimir_ctx();
     c->device = device;
     size_t fr = 0, tot = 0;

@@ -116,6 +116,9 @@ constexpr int MARCH_H = 32;       // default rows per strip tile
 constexpr int MARCH_H_MAX = 64;   // largest tile height the planner builds (loc stays below 2^16)
 void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles,
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
+// Shared-memory limits of the staged march variants; once per device before the first launch
+// (outside any stream capture).
+void march6_prepare();
 // The same march on a cylindrical (r, z) lattice (x = r from the axis, y = z), fields ~ exp(i m phi)
 // in the real-phase form (kzA, kzB = +-m), no CPML, no Lorentz media.
 void launch_march6_cyl(int fp64, const DevSim6 *sims, const DevTile *tiles, int ntiles,

@@ -76,6 +76,19 @@ __device__ __forceinline__ void st(R *__restrict__ p, int plane, unsigned N, uns
     else p[(unsigned)plane * N + g] = v.x;
 }
 
+// Asynchronous global -> shared copies of one element (cp.async, the thread's own data): the
+// staged march keeps the rows in flight in shared memory instead of registers.
+template <typename R>
+__device__ __forceinline__ void cpa(R *sdst, const R *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    if constexpr (sizeof(R) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // The inputs of one row step, loaded one row ahead.  Electric sources (row j):
 // f = E(j+1), q = H(j), m, P(j), psi(j) of all four planes.  Magnetic sources:
 // f = H(j+1), q = E(j+1) (old), m of row j+1, P(j+1), psi planes 0, 1 of row j+1
@@ -97,7 +110,9 @@ struct RowIn {
 // most, 3: up to three; a tile takes the smallest that covers its materials).
 // PF: rows whose inputs are in flight ahead of the row being computed (1 or 2; 2 where the
 // registers allow it without spilling, i.e. without the CPML planes)
-template <typename R, bool CPLX, bool PML, int NPL, int MINB, bool CYL = false, int PFREQ = 1>
+// STG > 0: the inputs of the next STG rows are in flight in a per-warp shared-memory ring
+// (cp.async of each lane's own elements, STG + 1 slots) instead of registers; PF is unused.
+template <typename R, bool CPLX, bool PML, int NPL, int MINB, bool CYL = false, int PFREQ = 1, int STG = 0>
 __global__ void __launch_bounds__(WARPS6 * 32, MINB)
 k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, int ntiles,
          const int64_t *__restrict__ launch_base, int64_t launch_add)
@@ -326,6 +341,211 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     };
 
     if (w > 0) {
+        if constexpr (STG > 0) {
+            // value slots of one staged row (in units of V): f[3], q[3], then P, P_prev per pole
+            // and component, then the psi planes px[4], py[4]
+            constexpr int CF = CPLX ? 2 : 1;
+            constexpr int VF = 0, VQ = 3, VP = 6, VX = 6 + 6 * (NPL > 0 ? NPL : 0), VY = VX + 4;
+            constexpr int NV = CF * (VX + (PML ? 8 : 0));
+            extern __shared__ __align__(16) unsigned char smem6[];
+            R *const ring = reinterpret_cast<R *>(smem6) + (size_t)warp * (STG + 1) * NV * 32 + lane;
+            auto sg = [&](int slot, int v, const R *p, int plane, unsigned NN, unsigned g) {
+                R *d = ring + (slot * NV + v * CF) * 32;
+                if constexpr (CPLX) { cpa(d, p + (2u * plane) * NN + g); cpa(d + 32, p + (2u * plane + 1u) * NN + g); }
+                else cpa(d, p + (unsigned)plane * NN + g);
+            };
+            auto fv = [&](int slot, int v) -> V {
+                const R *d = ring + (slot * NV + v * CF) * 32;
+                if constexpr (CPLX) return V(d[0], d[32]);
+                else return V(d[0]);
+            };
+            // the same predicates as load_psi / load_lor
+            auto stage_psi = [&](int slot, int j, int lo, int hi) {
+                if constexpr (PML) {
+                    if (inx) { const unsigned g = gxi(j); for (int k = lo; k < hi; ++k) sg(slot, VX + k, pxin, k, PX, g); }
+                    if (iny(j)) { const unsigned g = gyi(j); for (int k = lo; k < hi; ++k) sg(slot, VY + k, pyin, k, PY, g); }
+                }
+            };
+            auto fetch_psi = [&](int slot, In &in, int j, int lo, int hi) {
+                if constexpr (PML) {
+                    if (inx) for (int k = lo; k < hi; ++k) in.px[k] = fv(slot, VX + k);
+                    if (iny(j)) for (int k = lo; k < hi; ++k) in.py[k] = fv(slot, VY + k);
+                }
+            };
+            auto stage_lor = [&](int slot, unsigned g, int m) {
+                if constexpr (LOR) {
+                    const R *lm = lc + 12 * np * m;
+#pragma unroll
+                    for (int q = 0; q < NPL; ++q)
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+                            if (q < np && lm[12 * q + 4 * k + 2] != (R)0) {
+                                sg(slot, VP + 2 * (3 * q + k), lin, 6 * q + k, N, g);
+                                sg(slot, VP + 2 * (3 * q + k) + 1, lin, 6 * q + 3 + k, N, g);
+                            }
+                }
+            };
+            auto fetch_lor = [&](int slot, In &in, int m) {
+                if constexpr (LOR) {
+                    const R *lm = lc + 12 * np * m;
+#pragma unroll
+                    for (int q = 0; q < NPL; ++q)
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+                            if (q < np && lm[12 * q + 4 * k + 2] != (R)0) {
+                                in.p[3 * q + k] = fv(slot, VP + 2 * (3 * q + k));
+                                in.pm[3 * q + k] = fv(slot, VP + 2 * (3 * q + k) + 1);
+                            }
+                }
+            };
+            const int j0 = t.j0;
+            const int jm = rowp(j0 - 1);
+            const unsigned gm = (unsigned)(jm * nx + col), g0 = (unsigned)(j0 * nx + col);
+            int mr[STG + 1];   // materials of the rows whose inputs are staged next (see below)
+            if (electric) {
+                // as the register path: H (a = 1, b = h) then E (a, b_sigma), E^n of row j and
+                // H^{n+1/2} of row j-1 carried; mr[i] is the material of row j + i
+                V e[3], hp[3];
+                {
+                    In in0;
+                    const V em[3] = {ld<R, CPLX>(fin, 0, N, gm), ld<R, CPLX>(fin, 1, N, gm), ld<R, CPLX>(fin, 2, N, gm)};
+                    const V hm[3] = {ld<R, CPLX>(fin, 3, N, gm), ld<R, CPLX>(fin, 4, N, gm), ld<R, CPLX>(fin, 5, N, gm)};
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) e[k] = ld<R, CPLX>(fin, k, N, g0);
+                    load_psi(in0, jm, 2, 4);
+                    updH(jm, mat[gm], em, e[0], e[2], hm, in0.px, in0.py, (R)1, hfirst, false, hp);
+                }
+                auto stage_row = [&](int slot, int j, int m) {
+                    const unsigned g = (unsigned)(j * nx + col), gn = (unsigned)(rowp(j + 1) * nx + col);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        sg(slot, VF + k, fin, k, N, gn);
+                        sg(slot, VQ + k, fin, 3 + k, N, g);
+                    }
+                    stage_lor(slot, g, m);
+                    stage_psi(slot, j, 0, 4);
+                };
+#pragma unroll
+                for (int i = 0; i <= STG; ++i) mr[i] = i < h ? mat[g0 + i * nx] : 0;
+#pragma unroll
+                for (int i = 0; i < STG; ++i) {
+                    if (i < h) stage_row(i, j0 + i, mr[i]);
+                    cpa_commit();
+                }
+                int m_far = STG + 1 < h ? mat[g0 + (STG + 1) * nx] : 0;
+                int slot = 0;
+                for (int r = 0; r < h; ++r) {
+                    const int j = j0 + r;
+                    const unsigned g = (unsigned)(j * nx + col);
+                    const int sl_in = slot == 0 ? STG : slot - 1;    // (r + STG) mod (STG + 1)
+                    if (r + STG < h) stage_row(sl_in, j + STG, mr[STG]);
+                    cpa_commit();
+                    cpa_wait<STG>();
+                    In cur;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        cur.f[k] = fv(slot, VF + k);
+                        cur.q[k] = fv(slot, VQ + k);
+                    }
+                    cur.m = mr[0];
+                    fetch_lor(slot, cur, cur.m);
+                    fetch_psi(slot, cur, j, 0, 4);
+#pragma unroll
+                    for (int i = 0; i < STG; ++i) mr[i] = mr[i + 1];
+                    mr[STG] = m_far;
+                    if (r + STG + 2 < h) m_far = mat[g + (STG + 2) * nx];
+                    slot = slot == STG ? 0 : slot + 1;
+                    V hn[3], en[3];
+                    updH(j, cur.m, e, cur.f[0], cur.f[2], cur.q, cur.px, cur.py, (R)1, hfirst, own, hn);
+                    updE(j, cur.m, hn, hp[0], hp[2], e, cur, a, bs, own, g, en);
+                    if (own) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            st<R, CPLX>(fout, k, N, g, en[k]);
+                            st<R, CPLX>(fout, 3 + k, N, g, hn[k]);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        hp[k] = hn[k];
+                        e[k] = cur.f[k];
+                    }
+                }
+            } else {
+                // as the register path: E one row ahead, then H; mr[i] is the material of row j + 1 + i
+                V hq[3], e[3];
+                int m = mat[g0];
+                {
+                    In in0;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) hq[k] = ld<R, CPLX>(fin, 3 + k, N, g0);
+                    const V eo[3] = {ld<R, CPLX>(fin, 0, N, g0), ld<R, CPLX>(fin, 1, N, g0), ld<R, CPLX>(fin, 2, N, g0)};
+                    load_lor(in0, g0, m);
+                    load_psi(in0, j0, 0, 2);
+                    updE(j0, m, hq, ld<R, CPLX>(fin, 3, N, gm), ld<R, CPLX>(fin, 5, N, gm), eo, in0, (R)1, hfirst, own, g0, e);
+                }
+                auto stage_row = [&](int slot, int j, int mn) {
+                    const int jn = rowp(j + 1);
+                    const unsigned gn = (unsigned)(jn * nx + col);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        sg(slot, VF + k, fin, 3 + k, N, gn);
+                        sg(slot, VQ + k, fin, k, N, gn);
+                    }
+                    stage_lor(slot, gn, mn);
+                    stage_psi(slot, jn, 0, 2);
+                    stage_psi(slot, j, 2, 4);
+                };
+#pragma unroll
+                for (int i = 0; i <= STG; ++i) mr[i] = i < h ? mat[(unsigned)(rowp(j0 + 1 + i) * nx + col)] : 0;
+#pragma unroll
+                for (int i = 0; i < STG; ++i) {
+                    if (i < h) stage_row(i, j0 + i, mr[i]);
+                    cpa_commit();
+                }
+                int m_far = STG + 1 < h ? mat[(unsigned)(rowp(j0 + STG + 2) * nx + col)] : 0;
+                int slot = 0;
+                for (int r = 0; r < h; ++r) {
+                    const int j = j0 + r, jn = rowp(j + 1);
+                    const unsigned g = (unsigned)(j * nx + col), gn = (unsigned)(jn * nx + col);
+                    const int sl_in = slot == 0 ? STG : slot - 1;
+                    if (r + STG < h) stage_row(sl_in, j + STG, mr[STG]);
+                    cpa_commit();
+                    cpa_wait<STG>();
+                    In cur;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        cur.f[k] = fv(slot, VF + k);
+                        cur.q[k] = fv(slot, VQ + k);
+                    }
+                    cur.m = mr[0];
+                    fetch_lor(slot, cur, cur.m);
+                    fetch_psi(slot, cur, jn, 0, 2);
+                    fetch_psi(slot, cur, j, 2, 4);
+#pragma unroll
+                    for (int i = 0; i < STG; ++i) mr[i] = mr[i + 1];
+                    mr[STG] = m_far;
+                    if (r + STG + 2 < h) m_far = mat[(unsigned)(rowp(j + STG + 3) * nx + col)];
+                    slot = slot == STG ? 0 : slot + 1;
+                    V en[3], hn[3];
+                    updE(jn, cur.m, cur.f, hq[0], hq[2], cur.q, cur, (R)1, hfirst, own && r + 1 < h, gn, en);
+                    updH(j, m, e, en[0], en[2], hq, cur.px, cur.py, a, bs, own, hn);
+                    if (own) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            st<R, CPLX>(fout, k, N, g, e[k]);
+                            st<R, CPLX>(fout, 3 + k, N, g, hn[k]);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        e[k] = en[k];
+                        hq[k] = cur.f[k];
+                    }
+                    m = cur.m;
+                }
+            }
+        } else {
         const int j0 = t.j0;
         const int jm = rowp(j0 - 1);
         const unsigned gm = (unsigned)(jm * nx + col), g0 = (unsigned)(j0 * nx + col);
@@ -442,6 +662,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                 if (PF6 == 2) nxt = nx2;
             }
         }
+            }
     }
 
     if (t.ne > 0) {
@@ -465,22 +686,82 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     }
 }
 
+// Rows staged ahead in shared memory (cp.async) by the non-cylindrical variants.  Measured on
+// GB300 against the register prefetch: two staged rows move the FP32 real-field variants 5%
+// faster (waveguides with CPML and a Lorentz pole) and the FP32 dispersive complex ones 8%
+// (silicon/silica grating); four rows cost occupancy through shared memory (the complex Bloch
+// grating 18% slower).  The FP32 complex non-dispersive variants (no gain) and the FP64 ones
+// (bound by FP64 arithmetic, where the extra shared-memory reads only add instructions) keep
+// the register prefetch.  At most MARCH_STG rows, within about 56 KB per CTA.
+#ifndef MARCH_STG
+#define MARCH_STG 2
+#endif
+constexpr int kStageBudget = 56 * 1024;
+
+template <typename R, bool CPLX, bool PML, int NPL>
+constexpr size_t slot_bytes()
+{
+    return (size_t)WARPS6 * 32 * (CPLX ? 2 : 1) * (6 + 6 * NPL + (PML ? 8 : 0)) * sizeof(R);
+}
+
+template <typename R, bool CPLX, bool PML, int NPL>
+constexpr int stage_depth()
+{
+    if (sizeof(R) != 4 || (CPLX && NPL == 0) || MARCH_STG <= 0) return 0;
+    const int fit = (int)(kStageBudget / slot_bytes<R, CPLX, PML, NPL>()) - 1;
+    return fit < 1 ? 1 : (fit > MARCH_STG ? MARCH_STG : fit);
+}
+
+template <typename R, bool CPLX, bool PML, int NPL, int MINB, int PF>
+struct Variant {
+    static constexpr int STG = stage_depth<R, CPLX, PML, NPL>();
+    static constexpr size_t SMEM = STG > 0 ? (STG + 1) * slot_bytes<R, CPLX, PML, NPL>() : 0;
+    static void prepare()
+    {
+        if (SMEM > 48 * 1024)
+            cudaFuncSetAttribute(k_march6<R, CPLX, PML, NPL, MINB, false, PF, STG>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    }
+    static void launch(int grid, const DevSim6 *sims, const DevTile *tiles, int ntiles, const int64_t *lb, int64_t la,
+                       cudaStream_t st)
+    {
+        k_march6<R, CPLX, PML, NPL, MINB, false, PF, STG><<<grid, WARPS6 * 32, SMEM, st>>>(sims, tiles, ntiles, lb, la);
+    }
+};
+
 // MINB per variant (none, CPML, one pole, one pole + CPML, three poles, three poles + CPML):
 // resident CTAs per SM asked of the register allocator
 template <typename R, bool CPLX, int M0, int M1, int M2, int M3, int M4, int M5>
-void launch_t(int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles, const int64_t *lb, int64_t la,
-              cudaStream_t st)
-{
-    const int grid = (ntiles + WARPS6 - 1) / WARPS6;
-    switch (variant) {
-    case 0: k_march6<R, CPLX, false, 0, M0, false, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    case 1: k_march6<R, CPLX, true, 0, M1, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    case 2: k_march6<R, CPLX, false, 1, M2, false, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    case 3: k_march6<R, CPLX, true, 1, M3, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    case 4: k_march6<R, CPLX, false, 3, M4, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
-    default: k_march6<R, CPLX, true, 3, M5, false, 1><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, lb, la); break;
+struct Variants {
+    using V0 = Variant<R, CPLX, false, 0, M0, 2>;
+    using V1 = Variant<R, CPLX, true, 0, M1, 1>;
+    using V2 = Variant<R, CPLX, false, 1, M2, 2>;
+    using V3 = Variant<R, CPLX, true, 1, M3, 1>;
+    using V4 = Variant<R, CPLX, false, 3, M4, 1>;
+    using V5 = Variant<R, CPLX, true, 3, M5, 1>;
+    static void prepare()
+    {
+        V0::prepare(); V1::prepare(); V2::prepare(); V3::prepare(); V4::prepare(); V5::prepare();
     }
-}
+    static void launch(int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles, const int64_t *lb,
+                       int64_t la, cudaStream_t st)
+    {
+        const int grid = (ntiles + WARPS6 - 1) / WARPS6;
+        switch (variant) {
+        case 0: V0::launch(grid, sims, tiles, ntiles, lb, la, st); break;
+        case 1: V1::launch(grid, sims, tiles, ntiles, lb, la, st); break;
+        case 2: V2::launch(grid, sims, tiles, ntiles, lb, la, st); break;
+        case 3: V3::launch(grid, sims, tiles, ntiles, lb, la, st); break;
+        case 4: V4::launch(grid, sims, tiles, ntiles, lb, la, st); break;
+        default: V5::launch(grid, sims, tiles, ntiles, lb, la, st); break;
+        }
+    }
+};
+
+using VarD1 = Variants<double, true, 3, 2, 2, 1, 1, 1>;
+using VarD0 = Variants<double, false, 4, 3, 3, 2, 2, 2>;
+using VarF1 = Variants<float, true, 4, 4, 3, 3, 2, 2>;
+using VarF0 = Variants<float, false, 7, 5, 6, 5, 4, 4>;
 
 }  // namespace
 
@@ -498,12 +779,20 @@ void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const D
 {
     if (ntiles <= 0) return;
     if (fp64) {
-        if (cplx) launch_t<double, true, 3, 2, 2, 1, 1, 1>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
-        else launch_t<double, false, 4, 3, 3, 2, 2, 2>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        if (cplx) VarD1::launch(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        else VarD0::launch(variant, sims, tiles, ntiles, launch_base, launch_add, st);
     } else {
-        if (cplx) launch_t<float, true, 4, 4, 3, 3, 2, 2>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
-        else launch_t<float, false, 6, 4, 5, 4, 3, 3>(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        if (cplx) VarF1::launch(variant, sims, tiles, ntiles, launch_base, launch_add, st);
+        else VarF0::launch(variant, sims, tiles, ntiles, launch_base, launch_add, st);
     }
+}
+
+void march6_prepare()
+{
+    VarD1::prepare();
+    VarD0::prepare();
+    VarF1::prepare();
+    VarF0::prepare();
 }
 
 }  // namespace cas
