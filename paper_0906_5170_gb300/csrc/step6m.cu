@@ -770,8 +770,13 @@ void launch_march6_cyl(int fp64, const DevSim6 *sims, const DevTile *tiles, int 
 {
     if (ntiles <= 0) return;
     const int grid = (ntiles + WARPS6 - 1) / WARPS6;
-    if (fp64) k_march6<double, false, false, 0, 4, true, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
-    else k_march6<float, false, false, 0, 6, true, 2><<<grid, WARPS6 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
+    // real fields without CPML or poles: the staging policy of the real-field variants
+    constexpr int SD = stage_depth<double, false, false, 0>(), SF = stage_depth<float, false, false, 0>();
+    constexpr size_t BD = SD > 0 ? (SD + 1) * slot_bytes<double, false, false, 0>() : 0;
+    constexpr size_t BF = SF > 0 ? (SF + 1) * slot_bytes<float, false, false, 0>() : 0;
+    static_assert(BD <= 48 * 1024 && BF <= 48 * 1024, "cylindrical march: no opt-in shared memory");
+    if (fp64) k_march6<double, false, false, 0, 4, true, 2, SD><<<grid, WARPS6 * 32, BD, st>>>(sims, tiles, ntiles, launch_base, launch_add);
+    else k_march6<float, false, false, 0, 6, true, 2, SF><<<grid, WARPS6 * 32, BF, st>>>(sims, tiles, ntiles, launch_base, launch_add);
 }
 
 void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles,
