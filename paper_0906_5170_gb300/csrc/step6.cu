@@ -1,8 +1,9 @@
 // Six-component Yee leapfrog for the simulations that need every field:
 // two-dimensional cross-sections with k_z != 0 (Sec. III B), Bloch-periodic
 // cells (Sec. III D) and full three-dimensional runs (Sec. III E), with CPML
-// absorbing layers (Sec. III B) and single-pole Lorentz media continued onto
-// the complex-frequency contour (Eq. (9), Sec. III B).
+// absorbing layers (Sec. III B) and Lorentz media of up to three undamped poles
+// continued onto the complex-frequency contour (Eq. (9), Sec. III B; the silica
+// model of Sec. III D).
 //
 // Storage: E_x, E_y, E_z, H_x, H_y, H_z on the standard Yee sites, one plane of
 // nx*ny*nz elements each (two planes, real and imaginary, for complex fields).

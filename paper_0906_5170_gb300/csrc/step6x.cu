@@ -1,6 +1,7 @@
 // Six-component Yee half steps of three-dimensional simulations (Sec. III E),
-// with CPML (Sec. III B), Bloch-periodic walls (Sec. III D) and single-pole
-// Lorentz media on the contour (Eq. (9)), organised by x lines: every warp
+// with CPML (Sec. III B), Bloch-periodic walls (Sec. III D) and Lorentz media of
+// up to three undamped poles on the contour (Eq. (9); the silica model of
+// Sec. III D), organised by x lines: every warp
 // takes 32 consecutive x cells of one (y, z) line, so coordinates need no
 // per-cell division, x neighbours come by shuffle (one explicit load at the
 // segment edge or across the wrap), and y / z neighbours are coalesced row
@@ -10,6 +11,7 @@
 // w_n s(n) (Eq. (1)).  Fields are updated in place (one buffer).
 #include <cuda_runtime.h>
 
+#include "casimir.h"
 #include "kernels.h"
 
 namespace cas {
@@ -202,12 +204,16 @@ k_line3(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles,
                     const R *l4 = lc + 12 * S.npoles * m + 4 * k;
                     if (l4[2] != (R)0) {
                         // per pole q (present poles first): P_q' = [cp P_q - cpm P_q-prev + ce E] cd
+                        // (unrolled to the largest pole count, so that every present pole's loads
+                        // issue together)
                         V sp = c3[k] * b;
-                        for (int q = 0; q < S.npoles; ++q, l4 += 12) {
-                            const R ce = l4[2];
-                            if (ce == (R)0) break;
+#pragma unroll
+                        for (int q = 0; q < CASIMIR_MAX_POLES; ++q) {
+                            const R *lq = l4 + 12 * q;
+                            if (q > 0 && !(q < S.npoles && lq[2] != (R)0)) continue;
+                            const R ce = lq[2];
                             const V p = ld3<R, CPLX>(P, 6 * q + k, N, g), pm = ld3<R, CPLX>(P, 6 * q + 3 + k, N, g);
-                            const V pn = first_e ? (p * l4[0] + e * ce) * (R)0.5 : (p * l4[0] - pm * l4[1] + e * ce) * l4[3];
+                            const V pn = first_e ? (p * lq[0] + e * ce) * (R)0.5 : (p * lq[0] - pm * lq[1] + e * ce) * lq[3];
                             if (valid) {
                                 st3<R, CPLX>(P, 6 * q + 3 + k, N, g, p);
                                 st3<R, CPLX>(P, 6 * q + k, N, g, pn);

@@ -156,3 +156,32 @@ def test_sphere_three_pole_3d_fp32(ctx):
     p = sphere_three_pole("fp32")
     F, per, _ = ctx.plan(p).run(per_sim=True)
     _compare(per, F, p, "sphere3p32", False)
+
+
+def bloch_slab_3d(prec="fp64"):
+    """A 3D cell periodic in x and y with Bloch phases (complex fields), CPML along z, a
+    three-pole slab under a dielectric block; force along z on the block."""
+    import math
+    p = W._base(3, (12, 10, 24), 8.0, 80)
+    p["bc"] = ["periodic", "periodic", "pml"]
+    p["pml_cells"] = [0, 0, 4]
+    p["objects"] = [
+        {"shape": "box", "lo": [-1, -1, 0.0], "hi": [3, 3, 1.0], "kind": "lorentz", "eps_inf": 1.2,
+         "delta_eps": [0.8, 0.4, 1.1], "omega0": [2.0, 4.0, 7.0]},
+        {"shape": "box", "lo": [0.5, 0.375, 1.5], "hi": [1.0, 0.875, 2.0], "kind": "dielectric", "eps": 3.0, "mu": 1.0},
+    ]
+    lo, hi = [0.375, 0.25, 1.375], [1.125, 1.0, 2.125]
+    p["faces"] = W.box_faces(lo, hi, 3)
+    p["n_harm"] = 1
+    p["polarization"] = "full"
+    p["k_points"] = [{"k": [2 * math.pi / 1.5 * 0.25, 2 * math.pi / 1.25 * 0.5, 0.0], "weight": 1.0}]
+    p["force_axis"] = 2
+    p["precision"] = prec
+    return p
+
+
+@pytest.mark.parametrize("kernel_3d", [1, 2])
+def test_bloch_three_pole_3d_complex(ctx, kernel_3d):
+    p = bloch_slab_3d("fp64")
+    F, per, _ = ctx.plan(p, options={"kernel_3d": kernel_3d}).run(per_sim=True)
+    _compare(per, F, p, "bloch3d", True)
