@@ -399,6 +399,16 @@ def run_profile_case(args):
     for p in profile_case_problems(args.profile_case, args.time_steps):
         plan = ctx.plan(p)
         info = plan.info()
+        if args.plain:
+            # the unbatched comparison path (one run at a time, a launch per kernel and step,
+            # a separate projection kernel): device time from the stats, for ncu launch lists
+            t0 = time.perf_counter()
+            F, _, st = plan.run(plain=True)
+            wall = time.perf_counter() - t0
+            out.append({"case": args.profile_case, "path": "plain", "info": info, "wall_s": wall,
+                        "launches": st["kernel_launches"], "device_ms": st["device_ms"],
+                        "gcell_updates_per_s_wall": info["cell_updates"] / wall / 1e9})
+            continue
         F, _, st = plan.run()
         ms, nl, cu = ctx.kernel_stats(reset=True)
         out.append({"case": args.profile_case, "info": info, "kernel_ms": ms, "launches": nl,
@@ -448,6 +458,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--no-serving-sweep", action="store_true", help="skip the 200-request trace and the load sweep")
     ap.add_argument("--no-autotune", action="store_true", help="default execution options instead of autotuned ones")
+    ap.add_argument("--plain", action="store_true", help="profile cases: run the unbatched comparison path")
     ap.add_argument("--profile-case", choices=["piston", "piston64", "waveguides", "sphere3d", "grating", "grating_silica", "grating_silica_small", "cylinder"], default=None,
                     help="run one mid-size case for kernel profiling instead of the benchmark")
     args = ap.parse_args()
