@@ -30,7 +30,8 @@ sys.path.insert(0, ROOT)
 # the kernel on the piston profiling case (`--profile-case piston`, 17.0 M cells, above L2).  Traffic grows in
 # proportion to the cells (same tiles, same access pattern), so the benchmark's launch scales by its cell count.
 # Valid only for the kernel build that was captured; remove the entry when the kernel changes.
-DRAM_BYTES_PER_CELL_LAUNCH = {"k_step2d_t2<float>": (205.327e6 + 163.056e6) / 16998400}
+DRAM_BYTES_PER_CELL_LAUNCH = {"k_step2d_t2<float>": (205.327e6 + 163.056e6) / 16998400,
+                              "k_step2d_tk<float, 3>": (210.452e6 + 169.787e6) / 16998400}
 
 METRIC = "forces/s and Gcell-updates/s (% HBM roofline), p50/p99 latency vs plain at 1e-4 rel"
 WORKLOAD = "2D piston sweep: 8 h x TE+TM x 40 harmonics, 400x(80..280) cells, 20000 steps"
@@ -530,15 +531,16 @@ def main():
     hbm, peak_kind = peaks()
     b_alg = infos[0]["bytes_per_update"]
     achieved = cups_kernel * b_alg / (step_ms / 1e3) / 1e9 if step_ms > 0 else None
-    two_step = os.environ.get("CASIMIR_STEP2D_K", "2") == "2"
-    kernel = "k_step2d_t2<float>" if two_step else "k_step2d<float>"
-    cells_per_launch = sum(i["n_cells"] for i in infos)
+    # the step kernel the timed plans ran (their execution options, autotuned or default)
+    kmax = max(pl.options()["steps_per_launch"] for pl in plans)
+    kernel = {1: "k_step2d<float>", 2: "k_step2d_t2<float>", 3: "k_step2d_tk<float, 3>"}[kmax]
+    cells_per_launch = sum(i["n_cells"] for i, pl in zip(infos, plans) if pl.options()["steps_per_launch"] == kmax)
     per_cell = DRAM_BYTES_PER_CELL_LAUNCH.get(kernel)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm if achieved else None,
             "traffic": per_cell * cells_per_launch if per_cell else None,
             "traffic_unit": "bytes per launch (ncu dram read + write per cell, scaled to this launch's cells)",
-            "kernel": kernel + (" (two steps per launch)" if two_step else ""), "bytes_per_cell_update": b_alg,
+            "kernel": kernel + f" ({kmax} time step{'s' if kmax > 1 else ''} per launch)", "bytes_per_cell_update": b_alg,
             "cells_per_launch": cells_per_launch,
             "avg_launch_ms": step_ms / max(1, launches), "peak_source": peak_kind}
 

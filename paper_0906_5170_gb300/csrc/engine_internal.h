@@ -102,11 +102,11 @@ struct casimir_plan {
     std::vector<int64_t> coef_off;    // per geo, elements
     std::vector<uint8_t> mat_all;
     std::vector<double> coef_all;
-    std::vector<HostTile2> tiles2;    // two-step kernel tiles (TILE_X2 wide), entries sorted by row
+    std::vector<HostTile2> tiles2;    // multi-step kernel tiles (tile_xk(k2d) wide), entries sorted by row
     std::vector<DevEnt> ents2;
     std::vector<int> rowptr2;
-    int64_t launches = 0;             // launches a request needs (ceil(T/2) for the two-step kernel)
-    int k2d = 1;                      // time steps per launch of the 2D kernel
+    int64_t launches = 0;             // launches a request needs (ceil(T/k2d))
+    int k2d = 1;                      // time steps per launch of the 2D kernel (1, 2 or 3)
     std::vector<HostTile6> tiles6;
     std::vector<HostTile> tilesM;     // march kernel strip tiles (MARCH_W x MARCH_H) with their entries
     std::vector<DevEnt> entsM;
@@ -177,7 +177,8 @@ struct casimir_ctx {
     static constexpr int G_MARCH = 12;
     static constexpr int G_LINE3 = G_MARCH + 4 * MARCH_VARIANTS;
     static constexpr int G_CYL = G_LINE3 + 4;
-    static constexpr int NGROUPS = G_CYL + 2;
+    static constexpr int G_T3 = G_CYL + 2;          // [G_T3 + fp64] the three-step 2D kernel
+    static constexpr int NGROUPS = G_T3 + 2;
     struct Group {
         void *sims = nullptr, *tiles = nullptr;
         size_t sims_cap = 0, tiles_cap = 0;

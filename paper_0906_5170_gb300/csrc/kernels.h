@@ -133,20 +133,27 @@ constexpr int LINES3 = 64;
 void launch_line3(int fp64, int cplx, const DevSim6 *sims, const DevTile *tiles, int ntiles,
                   const int64_t *launch_base, int64_t launch_add, int phase, cudaStream_t st);
 
-// Two-step tiles of the 2D kernel: four warp strips of 28 interior columns; the
-// tile's pixel entries sorted by row, with rowptr[ly] .. rowptr[ly+1] per row.
-constexpr int TILE_X2 = 112;
+// Multi-step tiles of the 2D kernels: four warp strips of 32 - 2K interior columns (K time
+// steps per launch, K halo lanes per side); the tile's pixel entries sorted by row, with
+// rowptr[ly] .. rowptr[ly+1] per row.
+constexpr int WARPS_K = 4;
+constexpr int tile_xk(int k) { return WARPS_K * (32 - 2 * k); }
+constexpr int TILE_X2 = tile_xk(2);   // 112
 struct DevTile2 {
     int sim;
     int i0, j0;
     int ne;
-    const DevEnt *ents;    // loc = ly * TILE_X2 + lx
+    const DevEnt *ents;    // loc = ly * tile_xk(K) + lx
     const int *rowptr;     // TILE_Y + 1 offsets into ents
 };
 
 // Two leapfrog steps per launch: launch number L (from the simulation's start) advances
 // steps 2L-1 and 2L (only 2L-1 when 2L > T), reading buffer (L-1)&1 and writing L&1.
 void launch_step2d_t2(int fp64, const DevSim2D *sims, const DevTile2 *tiles, int ntiles,
+                      const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
+// K = 3 leapfrog steps per launch: launch L advances steps 3L-2 .. 3L (those up to T), reading
+// buffer (L-1)&1 and writing L&1; tiles tile_xk(3) = 104 columns wide.
+void launch_step2d_tk(int fp64, int k, const DevSim2D *sims, const DevTile2 *tiles, int ntiles,
                       const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 
 void launch_step2d(int fp64, const DevSim2D *sims, const DevTile *tiles, int ntiles,

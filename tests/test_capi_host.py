@@ -113,10 +113,12 @@ def test_plan_rejects_invalid_cylindrical_problems(mutate):
 
 def test_plan_options_defaults_and_explicit():
     p = W.piston_small()
-    assert pk.Plan(p).options() == {"steps_per_launch": 2, "march_rows": 32, "kernel_3d": 1}
+    # three fused steps for FP32 runs, two for FP64 runs (bound by FP64 arithmetic)
+    assert pk.Plan(dict(p, precision="fp32")).options() == {"steps_per_launch": 3, "march_rows": 32, "kernel_3d": 1}
+    assert pk.Plan(dict(p, precision="fp64")).options() == {"steps_per_launch": 2, "march_rows": 32, "kernel_3d": 1}
     o = pk.Plan(p, options={"steps_per_launch": 1, "march_rows": 16}).options()
     assert o == {"steps_per_launch": 1, "march_rows": 16, "kernel_3d": 1}
-    for bad in ({"steps_per_launch": 3}, {"march_rows": 65}, {"kernel_3d": 5}):
+    for bad in ({"steps_per_launch": 4}, {"march_rows": 65}, {"kernel_3d": 5}):
         with pytest.raises(pk.CasimirError) as e:
             pk.Plan(p, options=bad)
         assert e.value.code == -1

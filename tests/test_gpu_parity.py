@@ -40,8 +40,8 @@ def _oracle(p, key):
     return _ORACLE_CACHE[key]
 
 
-def _check(ctx, p, key, fp64):
-    F, per, st = ctx.plan(p).run(per_sim=True)
+def _check(ctx, p, key, fp64, options=None):
+    F, per, st = ctx.plan(p, options=options).run(per_sim=True)
     Fo, parts = _oracle(p, key)
     fa = p["force_axis"]
     assert per.shape == parts.shape
@@ -241,6 +241,60 @@ def test_waves_do_not_change_results(ctx):
     ctx.set_wave_bytes(0)
 
 
+# ---- three time steps per launch (2D TM/TE) ----------------------------------------------
+
+K3 = {"steps_per_launch": 3}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n_steps", [300, 301, 302])
+def test_three_steps_per_launch_piston(ctx, prec, n_steps):
+    # J and K sources (sigma on u and on v), and runs whose last launch holds 3, 1 or 2 steps
+    p = W.piston_small(n_steps=n_steps, precision=prec)
+    _check(ctx, p, ("piston", prec, n_steps), prec == "fp64", K3)
+
+
+def test_three_steps_per_launch_ragged_periodic_pmc(ctx):
+    p = W._base(2, (83, 45, 1), 10.0, 500)
+    p["objects"] = [{"shape": "box", "lo": [3.0, 1.0, 0], "hi": [4.5, 2.9, 0], "kind": "pec"},
+                    {"shape": "box", "lo": [5.5, 0.5, 0], "hi": [6.0, 3.5, 0], "kind": "dielectric", "eps": 3.0, "mu": 1.0}]
+    p["faces"] = W.box_faces([2.8, 0.8], [4.8, 3.3], 2)
+    p["n_harm"] = 5
+    p["polarization"] = "TE+TM"
+    p["force_axis"] = 0
+    p["precision"] = "fp64"
+    _check(ctx, p, "ragged", True, K3)
+    q = W.piston_small(n_steps=400, precision="fp64")
+    q["bc"] = ["periodic", "pec", "pec"]
+    _check(ctx, q, "periodic", True, K3)
+    r = W.piston_small(n_steps=400, precision="fp64")
+    L = r["n"][1] / r["resolution"]
+    r["objects"] = r["objects"] + [
+        {"shape": "box", "lo": [0.0, 0.0, 0.0], "hi": [6.0, 0.05, 0.0], "kind": "pmc"},
+        {"shape": "box", "lo": [0.0, L - 0.05, 0.0], "hi": [6.0, L, 0.0], "kind": "pmc"}]
+    _check(ctx, r, "pmc", True, K3)
+
+
+@pytest.mark.parametrize("nx,ny", [(7, 40), (40, 1), (3, 2), (26, 3), (27, 64)])
+def test_three_steps_per_launch_tiny_grids(ctx, nx, ny):
+    p = _tiny_2d(nx, ny, "TE+TM")
+    _check(ctx, p, ("tiny2d", nx, ny), True, K3)
+
+
+def test_three_steps_per_launch_in_a_mixed_batch(ctx):
+    # plans of 1, 2 and 3 steps per launch run side by side in one batch, each as alone
+    probs = [(W.piston_small(h=0.5, n_steps=301), {"steps_per_launch": 3}),
+             (W.piston_small(h=0.7, n_steps=300), {"steps_per_launch": 2}),
+             (W.piston_small(h=0.9, n_steps=299, precision="fp32"), {"steps_per_launch": 3}),
+             (W.piston_small(h=0.6, n_steps=200), {"steps_per_launch": 1})]
+    alone = [ctx.plan(p, options=o).run()[0] for p, o in probs]
+    plans = [ctx.plan(p, options=o) for p, o in probs]
+    tickets = [pl.submit(tag=i) for i, pl in enumerate(plans)]
+    for a, t in zip(alone, tickets):
+        F, err, st = t.force(-1)
+        assert np.allclose(F, a, rtol=1e-12, atol=0)
+
+
 # ---- degenerate grids: narrower than a warp strip, a single row ---------------------------
 
 def _tiny_2d(nx, ny, pol):
@@ -367,7 +421,7 @@ def test_cylindrical_plain_path_and_mixed_batch(ctx):
 
 def test_execution_options_do_not_change_results(ctx):
     cases = [
-        (W.piston_small(n_steps=300, precision="fp64"), [{"steps_per_launch": 1}, {"steps_per_launch": 2}]),
+        (W.piston_small(n_steps=300, precision="fp64"), [{"steps_per_launch": 1}, {"steps_per_launch": 2}, {"steps_per_launch": 3}]),
         (_waveguides_small("fp64", (0.0, 1.3)), [{"march_rows": 16}, {"march_rows": 32}, {"march_rows": 64}]),
         (W.config4_sphere_notch(0.4, seed=3, resolution=6, n_cells=24, pml_cells=4, n_harm=1, n_steps=60,
                                 precision="fp64", substrate_top=1.0), [{"kernel_3d": 1}, {"kernel_3d": 2}]),
@@ -391,7 +445,7 @@ def test_autotune_picks_caches_and_keeps_results(pk, ctx):
         p = W.piston_small(n_steps=300, precision="fp64")
         pl = c.plan(p)
         o = pl.options()
-        assert o["steps_per_launch"] in (1, 2)
+        assert o["steps_per_launch"] in (1, 2, 3)
         # a problem of the same class reuses the choice
         assert c.plan(W.piston_small(h=0.55, n_steps=300, precision="fp64")).options() == o
         F, per, _ = pl.run(per_sim=True)
