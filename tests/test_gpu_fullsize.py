@@ -5,6 +5,8 @@ sampled simulations recomputed one by one by the FP64 oracle.
   * 2D piston sweep: 400 x 80 and 400 x 280 grids, 40 harmonics, TE + TM, 20000 steps;
   * waveguides: 256 x 256 with 1-unit CPML, Lorentz pole, 4 of the 32 k_z points, 3840 steps;
   * rotationally symmetric two-block piston: 60 x 400 (r, z), m, n in {0, 1, 2}, 10314 steps;
+  * silicon/silica grating (one- and three-pole Lorentz media, complex fields): 40 x 160 at
+    resolution 40, 4 k_x x 8 k_z, 8 harmonics, 3200 steps, the three gaps of the benchmark;
   * sphere over an indented substrate: 160^3 with 12-cell CPML, one harmonic per face,
     a shortened run of 100 steps (the oracle's cost per full-length 3D simulation is
     about ten minutes).
@@ -101,3 +103,16 @@ def test_cylinder_blocks_full_size(ctx):
         ref = list(ex.map(one, picks))
     for i, r in zip(picks, ref):
         assert abs(per[i] - r) <= 2e-5 * max(abs(r), 1e-3 * np.max(np.abs(per))), (i, per[i], r)
+
+
+def test_grating_silica_full_size(ctx):
+    # the three gaps the benchmark runs together; sampled simulations of different k-points,
+    # sources and harmonics per gap
+    probs = [W.grating_silica(g, nk_x=4) for g in (0.25, 0.5, 1.0)]
+    per = _run_together(ctx, probs)
+    for p, pp in zip(probs, per):
+        n = len(pp)
+        picks = [5, n // 2 + 7, n - 3]
+        ref = _oracle_sims(p, picks)
+        for i, r in zip(picks, ref):
+            assert abs(pp[i] - r) <= 2e-5 * max(abs(r), 1e-3 * np.max(np.abs(pp))), (i, pp[i], r)
