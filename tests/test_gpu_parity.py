@@ -254,6 +254,13 @@ def test_three_steps_per_launch_piston(ctx, prec, n_steps):
     _check(ctx, p, ("piston", prec, n_steps), prec == "fp64", K3)
 
 
+@pytest.mark.parametrize("n_steps", [1, 2, 4])
+def test_three_steps_per_launch_short_runs(ctx, n_steps):
+    # the first launch itself holds fewer than three steps (the half step at n = 1 included)
+    p = W.piston_small(n_steps=n_steps, precision="fp64")
+    _check(ctx, p, ("piston_short", n_steps), True, K3)
+
+
 def test_three_steps_per_launch_ragged_periodic_pmc(ctx):
     p = W._base(2, (83, 45, 1), 10.0, 500)
     p["objects"] = [{"shape": "box", "lo": [3.0, 1.0, 0], "hi": [4.5, 2.9, 0], "kind": "pec"},
