@@ -398,6 +398,27 @@ def test_complete_cosine_basis_equals_point_basis_on_gpu(ctx):
     assert errs[0] > errs[1] > errs[2] > 1e-10 * scale
 
 
+def test_complete_cosine_basis_equals_point_basis_3d(ctx):
+    # the same completeness in 3D (x-line kernel): every face of the cubic surface carries
+    # a 2D cosine series over its pixels; complete, it spans the same space as the pixels
+    p = W.config4_sphere_notch(0.4, seed=3, resolution=6, n_cells=24, pml_cells=4, n_harm=1, n_steps=60,
+                               precision="fp64", substrate_top=1.0)
+    F_cos, per_cos, _ = ctx.plan(dict(p, n_harm=100000)).run(per_sim=True)
+    F_pt, per_pt, _ = ctx.plan(dict(p, basis="point")).run(per_sim=True)
+    assert len(per_pt) == len(per_cos) > 1000
+    fa = p["force_axis"]
+    scale = max(np.sum(np.abs(per_cos)), np.sum(np.abs(per_pt)))
+    assert abs(F_cos[fa] - F_pt[fa]) <= 1e-10 * scale
+    # and sampled point-basis simulations against the oracle
+    sims = oracle.enumerate_sims(dict(p, basis="point"))
+    w = oracle.g_weights(p)
+    q = dict(p, basis="point")
+    st = oracle.grid_setup(q, q["k_points"][0]["k"])
+    for i in (0, len(sims) // 2, len(sims) - 1):
+        r = float(np.sum(w * oracle.run_sim(q, sims[i], st).real)) * q["k_points"][0]["weight"]
+        assert abs(per_pt[i] - r) <= 1e-10 * abs(r) + 1e-13 * scale
+
+
 # ---- cylindrical (r, z) runs with exp(i m phi) fields (Sec. III C) -------------------------
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
