@@ -408,6 +408,7 @@ static int put_real(const std::vector<double> &v, void *dst, int fp64, cudaStrea
 
 int upload_plan(casimir_plan_t *P, cudaStream_t st)
 {
+    NvtxRange nvtx_("casimir.upload");
     if (P->dev.block) return CASIMIR_OK;
     casimir_ctx *c = P->ctx;
     size_t sz[13] = {align256(P->mat_all.size()), align256(P->coef_all.size() * P->rsize),
@@ -635,6 +636,7 @@ static int grow(casimir_ctx *c, void **p, size_t *cap, size_t need)
 
 static int rebuild(casimir_ctx *c)
 {
+    NvtxRange nvtx_("casimir.rebuild");
     std::vector<DevSim2D> s2[2];
     std::vector<DevTile> t2[2];
     std::vector<DevTile2> tt[4];   // [fp64]: two steps per launch, [2 + fp64]: three
@@ -827,6 +829,7 @@ static void launch_steps(casimir_ctx *c, int k)
 // the launch counter.
 static int run_chunk(casimir_ctx *c, int k)
 {
+    NvtxRange nvtx_("casimir.chunk");
     static const bool no_graphs = std::getenv("CASIMIR_NO_GRAPHS") != nullptr;
     if (no_graphs) {
         CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
@@ -1183,6 +1186,7 @@ static int resolve_options(const casimir_plan_options *in, casimir_plan_options 
 
 static int make_plan(casimir_ctx_t *c, const casimir_problem *p, const casimir_plan_options *opts, casimir_plan_t **out)
 {
+    NvtxRange nvtx_("casimir.plan");
     *out = nullptr;
     auto *P = new casimir_plan_t();
     P->ctx = c;
@@ -1219,6 +1223,7 @@ static std::string tune_key(const casimir_problem &p)
 // Time each candidate on the problem cut to 128 steps; the fastest per cell-update wins.
 static casimir_plan_options autotune(casimir_ctx *c, const casimir_problem &p)
 {
+    NvtxRange nvtx_("casimir.autotune");
     casimir_plan_options dflt{};
     resolve_options(nullptr, &dflt, p.precision == CASIMIR_FP64);
     std::vector<casimir_plan_options> cand;
@@ -1445,6 +1450,7 @@ int casimir_cancel(casimir_ticket r)
 
 int casimir_run(casimir_plan_t *P, double F[3], double *per_sim, casimir_stats *st)
 {
+    NvtxRange nvtx_("casimir.run");
     if (!P) return fail(CASIMIR_EINVAL, "plan is NULL");
     casimir_ctx *c = P->ctx;
     if (!c) return fail(CASIMIR_EINVAL, "host-only plan (created without a context)");

@@ -1,5 +1,6 @@
 // Internal host-side structures shared by the executor translation units.
 #pragma once
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 
 #include <array>
@@ -22,6 +23,15 @@ int fail(int code, const std::string &msg);
 double now_ms();
 size_t align256(size_t b);
 }  // namespace cas
+
+// NVTX ranges around the executor's phases (plan, upload, batch rebuild, chunk, autotune
+// trials, plain runs), visible to profilers; header-only NVTX v3, inert without a tool.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 #define CUDA_TRY(expr)                                                                        \
     do {                                                                                      \

@@ -67,6 +67,7 @@ struct Free {
 
 extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim, casimir_stats *st)
 {
+    NvtxRange nvtx_("casimir.run_plain");
     if (!P) return fail(CASIMIR_EINVAL, "plan is NULL");
     casimir_ctx *c = P->ctx;
     if (!c) return fail(CASIMIR_EINVAL, "host-only plan (created without a context)");
