@@ -311,6 +311,36 @@ static int prepare_plan(casimir_plan_t *P)
                         P->entsM.insert(P->entsM.end(), b.begin(), b.end());
                     }
                 hs.nent = (int)P->entsM.size() - hs.ent0;
+                if (hs.cyl && P->opts.steps_per_launch >= 2) {
+                    // two steps per launch: MARCH_W2-wide strips, entries sorted by row with
+                    // per-row offsets (the sigma group is projected from registers)
+                    const int tx2 = (hs.nx + MARCH_W2 - 1) / MARCH_W2;
+                    std::vector<std::vector<std::pair<int, DevEnt>>> b2((size_t)tx2 * ty);
+                    for (const Entry &e : sm.meas) {
+                        if (inA(e.arr) != inA(sarr)) continue;   // real fields: the source's set only
+                        const int i = (int)(e.idx % hs.nx), j = (int)(e.idx / hs.nx);
+                        const int ti = i / MARCH_W2, tj = j / rows;
+                        const int loc = (j - tj * rows) * MARCH_W2 + (i - ti * MARCH_W2);
+                        b2[(size_t)tj * tx2 + ti].push_back({loc, DevEnt{loc | (e.arr << 16), 0, e.re}});
+                    }
+                    hs.tile2_0 = (int)P->tiles2.size();
+                    for (int tj = 0; tj < ty; ++tj)
+                        for (int ti = 0; ti < tx2; ++ti) {
+                            auto &b = b2[(size_t)tj * tx2 + ti];
+                            std::stable_sort(b.begin(), b.end(), [](const std::pair<int, DevEnt> &x, const std::pair<int, DevEnt> &y) {
+                                return x.first < y.first;
+                            });
+                            HostTile2 ht{(int)s, ti * MARCH_W2, tj * rows, (int)P->ents2.size(), (int)b.size(), (int)P->rowptr2.size()};
+                            int k = 0;
+                            for (int ly = 0; ly <= rows; ++ly) {
+                                while (k < (int)b.size() && b[k].first / MARCH_W2 < ly) ++k;
+                                P->rowptr2.push_back(ly == rows ? (int)b.size() : k);
+                            }
+                            for (auto &pe : b) P->ents2.push_back(pe.second);
+                            P->tiles2.push_back(ht);
+                        }
+                    hs.ntile2 = (int)P->tiles2.size() - hs.tile2_0;
+                }
             }
             hs.line3 = (!hs.march && D.prob.dims == 3 && P->opts.kernel_3d == 1 && planes * N < ((int64_t)1 << 32)) ? 1 : 0;
             if (hs.line3) {
@@ -372,7 +402,8 @@ static int prepare_plan(casimir_plan_t *P)
     P->field_elems = off;
     {
         bool all2d = !P->sims.empty() && !P->sims[0].full;
-        P->k2d = all2d ? P->opts.steps_per_launch : 1;
+        const bool cyl = !P->sims.empty() && P->sims[0].cyl;
+        P->k2d = all2d ? P->opts.steps_per_launch : (cyl && P->opts.steps_per_launch >= 2 ? 2 : 1);
         P->launches = (D.prob.n_steps + P->k2d - 1) / P->k2d;
     }
     P->table_bytes = (int64_t)(align256(P->ents2.size() * sizeof(DevEnt)) + align256(P->rowptr2.size() * sizeof(int)) +
@@ -648,6 +679,8 @@ static int rebuild(casimir_ctx *c)
     std::vector<DevTile> tl3[4];
     std::vector<DevSim6> sc6[2];
     std::vector<DevTile> tc6[2];
+    std::vector<DevSim6> sc2[2];    // cylindrical, two steps per launch
+    std::vector<DevTile2> tc2[2];
     for (auto &aw : c->active_waves) {
         casimir_request *r = aw.first;
         const casimir_request::Wave &w = r->waves[aw.second];
@@ -688,11 +721,20 @@ static int rebuild(casimir_ctx *c)
                 const int gi = P->fp64;
                 DevSim6 d;
                 make_sim6(P, blk, r->acc, r->tail, w.s0, s, &d);
-                const int idx = (int)sc6[gi].size();
-                sc6[gi].push_back(d);
-                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
-                    const HostTile &ht = P->tilesM[t];
-                    tc6[gi].push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.entsM + ht.ent0});
+                if (P->k2d == 2) {
+                    const int idx = (int)sc2[gi].size();
+                    sc2[gi].push_back(d);
+                    for (int t = hs.tile2_0; t < hs.tile2_0 + hs.ntile2; ++t) {
+                        const HostTile2 &ht = P->tiles2[t];
+                        tc2[gi].push_back(DevTile2{idx, ht.i0, ht.j0, ht.ne, P->dev.ents2 + ht.ent0, P->dev.rowptr2 + ht.rp0});
+                    }
+                } else {
+                    const int idx = (int)sc6[gi].size();
+                    sc6[gi].push_back(d);
+                    for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                        const HostTile &ht = P->tilesM[t];
+                        tc6[gi].push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.entsM + ht.ent0});
+                    }
                 }
             } else if (hs.march) {
                 // the simulation's descriptor goes to each variant group that holds one of its tiles
@@ -741,9 +783,12 @@ static int rebuild(casimir_ctx *c)
         } else if (gi < casimir_ctx::G_T3) {
             const int v = gi - casimir_ctx::G_CYL;
             ns = sc6[v].size(); nt = tc6[v].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = sc6[v].data(); tp = tc6[v].data();
-        } else {
+        } else if (gi < casimir_ctx::G_CYL2) {
             const int v = 2 + gi - casimir_ctx::G_T3;
             ns = 0; nt = tt[v].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile2); sp = nullptr; tp = tt[v].data();
+        } else {
+            const int v = gi - casimir_ctx::G_CYL2;
+            ns = sc2[v].size(); nt = tc2[v].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile2); sp = sc2[v].data(); tp = tc2[v].data();
         }
         int rc = grow(c, &G.sims, &G.sims_cap, ns * ss);
         if (rc) return rc;
@@ -789,10 +834,12 @@ static void launch_unit(casimir_ctx *c, int gi, int j, cudaStream_t st)
                          c->d_launch, j, phase, st);
     } else if (gi < casimir_ctx::G_T3) {
         launch_march6_cyl(gi - casimir_ctx::G_CYL, (const DevSim6 *)G.sims, (const DevTile *)G.tiles, G.ntiles, c->d_launch, j, st);
-    } else {
+    } else if (gi < casimir_ctx::G_CYL2) {
         // the 2D simulation tables are those of groups 0 / 1
         const int f = gi - casimir_ctx::G_T3;
         launch_step2d_tk(f, 3, (const DevSim2D *)c->groups[f].sims, (const DevTile2 *)G.tiles, G.ntiles, c->d_launch, j, st);
+    } else {
+        launch_march6_cyl2(gi - casimir_ctx::G_CYL2, (const DevSim6 *)G.sims, (const DevTile2 *)G.tiles, G.ntiles, c->d_launch, j, st);
     }
 }
 
@@ -1235,6 +1282,12 @@ static casimir_plan_options autotune(casimir_ctx *c, const casimir_problem &p)
         for (int rows : {32, 16, 64}) {
             casimir_plan_options o = dflt;
             o.march_rows = rows;
+            cand.push_back(o);
+        }
+        if (p.coords == CASIMIR_COORDS_CYLINDRICAL && dflt.steps_per_launch >= 2) {
+            // the cylindrical march also runs one step per launch
+            casimir_plan_options o = dflt;
+            o.steps_per_launch = 1;
             cand.push_back(o);
         }
     } else {

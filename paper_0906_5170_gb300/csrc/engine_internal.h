@@ -188,7 +188,8 @@ struct casimir_ctx {
     static constexpr int G_LINE3 = G_MARCH + 4 * MARCH_VARIANTS;
     static constexpr int G_CYL = G_LINE3 + 4;
     static constexpr int G_T3 = G_CYL + 2;          // [G_T3 + fp64] the three-step 2D kernel
-    static constexpr int NGROUPS = G_T3 + 2;
+    static constexpr int G_CYL2 = G_T3 + 2;         // [G_CYL2 + fp64] the two-step cylindrical march
+    static constexpr int NGROUPS = G_CYL2 + 2;
     struct Group {
         void *sims = nullptr, *tiles = nullptr;
         size_t sims_cap = 0, tiles_cap = 0;

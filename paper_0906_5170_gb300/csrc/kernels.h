@@ -155,6 +155,13 @@ void launch_step2d_t2(int fp64, const DevSim2D *sims, const DevTile2 *tiles, int
 // buffer (L-1)&1 and writing L&1; tiles tile_xk(3) = 104 columns wide.
 void launch_step2d_tk(int fp64, int k, const DevSim2D *sims, const DevTile2 *tiles, int ntiles,
                       const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
+// Two steps per launch on the cylindrical lattice (fields ~ exp(i m phi), real): launch L
+// advances steps 2L-1 and 2L (2L-1 alone when 2L > T), reading buffer (L-1)&1, writing L&1;
+// strips of MARCH_W2 columns, tiles of S.tile_rows rows with row-sorted entries (loc =
+// ly * MARCH_W2 + lx, the component in bits 16..18) and tile_rows + 1 row offsets.
+constexpr int MARCH_W2 = 28;
+void launch_march6_cyl2(int fp64, const DevSim6 *sims, const DevTile2 *tiles, int ntiles,
+                        const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 
 void launch_step2d(int fp64, const DevSim2D *sims, const DevTile *tiles, int ntiles,
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st);

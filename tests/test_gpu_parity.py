@@ -433,6 +433,23 @@ def test_cylindrical_multi_strip_ragged(ctx):
     _check(ctx, p, "cyl_wide", True)
 
 
+@pytest.mark.parametrize("steps", [1, 2])
+@pytest.mark.parametrize("n_extra", [0, 1])
+def test_cylindrical_steps_per_launch(ctx, steps, n_extra):
+    # one and two steps per launch against the oracle, runs of even and odd length (the last
+    # two-step launch then holds one step), J and K sources, m = 0 .. 2
+    p = W.cylinder_piston(12, [0, 1, 2], t_max=4.0, precision="fp64")
+    p["n_steps"] = p["n_steps"] + n_extra
+    _check(ctx, p, ("cyl_steps", n_extra), True, {"steps_per_launch": steps})
+
+
+@pytest.mark.parametrize("rows", [16, 64])
+def test_cylindrical_two_steps_ragged_tiles(ctx, rows):
+    # 40 radial cells: two 28-column strips (28 + 12), row bands of 16 or 64 along z
+    p = W.cylinder_piston(40, [0, 2], radius=1.0, below=0.4, above=0.7, t_max=1.5, n_harm=6)
+    _check(ctx, p, ("cyl_wide", rows), True, {"steps_per_launch": 2, "march_rows": rows})
+
+
 def test_cylindrical_plain_path_and_mixed_batch(ctx):
     p = W.cylinder_piston(10, [0, 1], t_max=4.0, precision="fp64")
     Fb, pb, _ = ctx.plan(p).run(per_sim=True)
