@@ -214,8 +214,10 @@ int casimir_plan_get_info(const casimir_plan_t *plan, casimir_plan_info *info);
 /* Execution options of a plan (how the leapfrog of Sec. III A is scheduled; the computed
  * force does not depend on them beyond rounding).  0 in a field selects the default. */
 typedef struct {
-    int steps_per_launch;   /* 2D TM/TE runs: time steps fused into one pass over memory, 1, 2 or 3
-                               (default 3 for FP32 runs, 2 for FP64 runs) */
+    int steps_per_launch;   /* time steps fused into one pass over memory: 2D TM/TE runs 1, 2 or 3
+                               (default 3 for FP32 runs, 2 for FP64 runs); cylindrical runs 1 or 2
+                               (any value >= 2 fuses two; the default fuses two); other
+                               six-component runs take one step per launch */
     int march_rows;         /* 2D six-component and cylindrical runs: rows per strip tile, 16, 32 or 64 (default 32) */
     int kernel_3d;          /* 3D runs: 1 = x-line kernel (default), 2 = one-thread-per-cell kernel */
     int reserved;
