@@ -158,7 +158,7 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
             // inputs of iteration r: the buffer's E at row r+1, H at row r, material of row r+1
             R en_c[3], hq_c[3];
             int mn_c;
-            int jr = wrow(j0 - 1);
+            int jr = wrow(j0 - 1), jp = wrow(j0 - 2);   // rows r and r-1, wrapped
             {
                 const int jn = jr + 1 == ny ? 0 : jr + 1;
 #pragma unroll
@@ -183,9 +183,9 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                 if (!two) {
                     if (inA) store(jr, eA, hA);
                 } else if (r == j0) {
-                    updH(wrow(r - 1), m_rm, eAm, eA[0], eA[2], hAm, (R)1, hB0, hBm);   // H_B(j0-1)
+                    updH(jp, m_rm, eAm, eA[0], eA[2], hAm, (R)1, hB0, hBm);   // H_B(j0-1)
                 } else if (r > j0) {
-                    const int jm = wrow(r - 1);
+                    const int jm = jp;
                     R hB[3], eB[3];
                     updH(jm, m_rm, eAm, eA[0], eA[2], hAm, (R)1, hB0, hB);
                     updE(jm, m_rm, hB, hBm[0], hBm[2], eAm, a, bs, eB);
@@ -207,15 +207,16 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                 m_rm = m_r;
                 m_r = mn_c;
                 mn_c = mn_n;
+                jp = jr;
                 jr = jn;
             }
         } else {
             // carried: E_A at row r, the buffer's H at row r, H_A at r-1, E_B at r-1 (+ materials)
             R eAc[3], h0c[3], hAm[3] = {0, 0, 0}, eBm[3] = {0, 0, 0};
             int m_r, m_rm = 0;
-            int jr = wrow(j0 - 1);
+            int jr = wrow(j0 - 1), jp = wrow(j0 - 2);   // rows r and r-1, wrapped
             {
-                const int ja = wrow(j0 - 2);
+                const int ja = jp;
                 const R hb2[3] = {ldr(3, ja), ldr(4, ja), ldr(5, ja)};
                 const R e0[3] = {ldr(0, jr), ldr(1, jr), ldr(2, jr)};
 #pragma unroll
@@ -253,7 +254,7 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                     R eB[3];
                     updE(jr, m_r, hA, hAm[0], hAm[2], eAc, (R)1, hB0, eB);   // E_B(r)
                     if (r > j0) {
-                        const int jm = wrow(r - 1);
+                        const int jm = jp;
                         R hB[3];
                         updH(jm, m_rm, eBm, eB[0], eB[2], hAm, a, bs, hB);    // H_B(r-1)
                         if (r - 1 < j0 + h) {
@@ -275,6 +276,7 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                 m_rm = m_r;
                 m_r = mn_c;
                 mn_c = mn_n;
+                jp = jr;
                 jr = jn;
             }
         }
