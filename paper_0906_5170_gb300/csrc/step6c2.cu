@@ -92,11 +92,12 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
 
     // radial factors of this lane's column i (r_i = i Delta, r_{i+1/2}); on the axis the Stokes
     // form 4 H_phi(Delta/2) / Delta (fa = 4, fb = 0)
-    // (Delta cancels from the ratios: two reciprocals in the run's precision per thread)
-    const R ci = (R)col, rc = col > 0 ? (R)1 / ci : (R)0, rhc = (R)1 / (ci + (R)0.5), ix = (R)S.inv_dx;
-    const R inv_ri = ix * rc, inv_rh = ix * rhc;
-    const R ga = (ci + (R)1) * rhc, gb = ci * rhc;
-    const R fa = col > 0 ? (ci + (R)0.5) * rc : (R)4, fb = col > 0 ? (ci - (R)0.5) * rc : (R)0;
+    // (Delta cancels from the ratios: each factor is one correctly rounded division of exact
+    // operands in the run's precision, so FP32 runs need no FP64 arithmetic per thread)
+    const R ci = (R)col, ch = ci + (R)0.5, ix = (R)S.inv_dx;
+    const R inv_ri = col > 0 ? ix / ci : (R)0, inv_rh = ix / ch;
+    const R ga = (ci + (R)1) / ch, gb = ci / ch;
+    const R fa = col > 0 ? ch / ci : (R)4, fb = col > 0 ? (ci - (R)0.5) / ci : (R)0;
 
     auto right = [&](R f) -> R { const R r = cdn(f); return wrapR ? r * bxr : r; };
     auto left = [&](R f) -> R { const R l = cup(f); return wrapL ? l * bxr : l; };

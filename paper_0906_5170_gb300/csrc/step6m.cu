@@ -189,14 +189,15 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
     //   Stokes over the disk of radius Delta/2: 4 H_phi(Delta/2) / Delta (fa = 4, fb = 0)
     R inv_ri = 0, inv_rh = 0, ga = 0, gb = 0, fa = 0, fb = 0;
     if constexpr (CYL) {
-        // (Delta cancels from the ratios: two reciprocals in the run's precision per thread)
-        const R ci = (R)col, rc = col > 0 ? (R)1 / ci : (R)0, rhc = (R)1 / (ci + (R)0.5), ix = (R)S.inv_dx;
-        inv_ri = ix * rc;
-        inv_rh = ix * rhc;
-        ga = (ci + (R)1) * rhc;
-        gb = ci * rhc;
-        fa = col > 0 ? (ci + (R)0.5) * rc : (R)4;
-        fb = col > 0 ? (ci - (R)0.5) * rc : (R)0;
+        // (Delta cancels from the ratios: each factor is one correctly rounded division of exact
+        // operands in the run's precision, so FP32 runs need no FP64 arithmetic per thread)
+        const R ci = (R)col, ch = ci + (R)0.5, ix = (R)S.inv_dx;
+        inv_ri = col > 0 ? ix / ci : (R)0;
+        inv_rh = ix / ch;
+        ga = (ci + (R)1) / ch;
+        gb = ci / ch;
+        fa = col > 0 ? ch / ci : (R)4;
+        fb = col > 0 ? (ci - (R)0.5) / ci : (R)0;
     }
     auto rowp = [&](int j) { return j < 0 ? j + ny : (j >= ny ? j - ny : j); };
     auto iny = [&](int j) { return PML && dY > 0 && (j < dY || j >= ny - dY); };
