@@ -169,20 +169,24 @@ def test_binding_rejects_malformed_pole_lists():
         pk.Plan(p)
 
 
+@pytest.mark.parametrize("poles", [1, 3])
 @pytest.mark.parametrize("eps_x,stable", [(0.52, True), (0.48, False)])
-def test_stability_bound_matches_the_oracle(eps_x, stable):
-    """The planner admits a uniform one-pole medium exactly when eps(4/dt^2) exceeds the
-    lattice bound (dt/2)^2 k_max^2 = 2 courant^2 = 0.5; the oracle's fields stay bounded
-    just inside it and blow up just outside."""
+def test_stability_bound_matches_the_oracle(eps_x, stable, poles):
+    """The planner admits a uniform Lorentz medium (one pole, or three at frequencies in the
+    ratio 0.3 : 0.6 : 1) exactly when eps(4/dt^2) = eps_inf - sum_j de_j y_j / (4 - y_j),
+    y_j = (w_j dt)^2, exceeds the lattice bound (dt/2)^2 k_max^2 = 2 courant^2 = 0.5; the
+    oracle's fields stay bounded just inside it and blow up just outside."""
     import math
-    res, cour, de, nx = 8.0, 0.5, 10.0, 8
-    r = 1.0 - eps_x                    # eps(X) = 1 - de y / (4 - y), y = (w0 dt)^2
-    y = 4 * r / (de + r)
-    w0 = math.sqrt(y) / (cour / res)
+    from scipy.optimize import brentq
+    res, cour, nx = 8.0, 0.5, 8
+    dt = cour / res
+    de, ratios = ([10.0], [1.0]) if poles == 1 else ([1.0, 2.0, 3.0], [0.3, 0.6, 1.0])
+    eps = lambda s: 1.0 - sum(d * (r * s * dt) ** 2 / (4 - (r * s * dt) ** 2) for d, r in zip(de, ratios))
+    s = brentq(lambda s: eps(s) - eps_x, 1e-3, 1.999 / dt)
     p = W._base(2, (nx, nx, 1), res, 3000, sigma=0.0, courant=cour)
     p["bc"] = ["periodic", "periodic", "pec"]
     p["objects"] = [{"shape": "box", "lo": [-1, -1, 0], "hi": [10, 10, 0], "kind": "lorentz",
-                     "eps_inf": 1.0, "delta_eps": de, "omega0": w0}]
+                     "eps_inf": 1.0, "delta_eps": de, "omega0": [r * s for r in ratios]}]
     q = dict(p, polarization="full", faces=[{"axis": 1, "sign": 1, "pos": 0.5, "lo": [0, 0.5, 0], "hi": [1, 0.5, 0]}])
     if stable:
         pk.Plan(q)
@@ -191,8 +195,8 @@ def test_stability_bound_matches_the_oracle(eps_x, stable):
             pk.Plan(q)
     st = oracle.grid_setup(p)
     with np.errstate(all="ignore"):
-        s = np.abs(oracle.run_vectors(p, st, False, {(2, 3 * nx + 3): 1.0}, {(2, 3 * nx + 3): 1.0}, pol="TM"))
-    late = np.nan_to_num(s[-300:], nan=np.inf).max()
+        v = np.abs(oracle.run_vectors(p, st, False, {(2, 3 * nx + 3): 1.0}, {(2, 3 * nx + 3): 1.0}, pol="TM"))
+    late = np.nan_to_num(v[-300:], nan=np.inf).max()
     assert (late < 10.0) == stable
 
 
