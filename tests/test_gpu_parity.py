@@ -450,6 +450,24 @@ def test_cylindrical_two_steps_ragged_tiles(ctx, rows):
     _check(ctx, p, ("cyl_wide", rows), True, {"steps_per_launch": 2, "march_rows": rows})
 
 
+def test_batch_mixing_fusion_depths(ctx):
+    # a two-step cylindrical plan, three-step and two-step 2D plans and a one-step six-component
+    # plan in one batch: each simulation derives its steps from the shared launch counter and
+    # its plan's depth; every force equals the plan's force alone
+    probs = [W.cylinder_piston(12, [0, 1], t_max=3.0, precision="fp32"),
+             W.piston_small(h=0.6, n_steps=301, precision="fp32"),
+             W.piston_small(h=0.8, n_steps=300, precision="fp64"),
+             W.config3_waveguides(0.5, resolution=8, n_cells=48, pml_units=0.75, n_harm=2, n_steps=150,
+                                  k_points=[{"k": [0, 0, 1.0], "weight": 0.5}], precision="fp32")]
+    alone = [ctx.plan(p).run()[0] for p in probs]
+    plans = [ctx.plan(p) for p in probs]
+    assert [pl.options()["steps_per_launch"] for pl in plans][:3] == [3, 3, 2]
+    tickets = [pl.submit(tag=i) for i, pl in enumerate(plans)]
+    for a, t in zip(alone, tickets):
+        F, err, st = t.force(-1)
+        assert np.allclose(F, a, rtol=1e-12, atol=0)
+
+
 def test_cylindrical_plain_path_and_mixed_batch(ctx):
     p = W.cylinder_piston(10, [0, 1], t_max=4.0, precision="fp64")
     Fb, pb, _ = ctx.plan(p).run(per_sim=True)
