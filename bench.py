@@ -126,7 +126,13 @@ def serving_trial(pk, ctx, n_requests=12, rate=50.0, scale=0.15, seed=0, plain=F
     import workloads as W
     if trace is None:
         trace = W.serving_requests(seed, n_requests=n_requests, rate=rate, scale=scale)
-    plans = [ctx.plan(p) for _, p in trace]
+    # host planning (rasterisation, basis, g(t), simulation list) happens before the trace
+    # starts, as for a prepared query; its time per request is reported beside the latencies
+    plans, plan_ms = [], []
+    for _, p in trace:
+        tp = time.perf_counter()
+        plans.append(ctx.plan(p))
+        plan_ms.append(1e3 * (time.perf_counter() - tp))
     done = [None] * len(trace)
     t0 = time.perf_counter()
     if not plain:
@@ -155,9 +161,11 @@ def serving_trial(pk, ctx, n_requests=12, rate=50.0, scale=0.15, seed=0, plain=F
         kinds[p.get("kind", "?")] = kinds.get(p.get("kind", "?"), 0) + 1
     for pl in plans:
         pl.close()
+    pl = sorted(plan_ms)
     return {"forces_per_s": len(trace) / makespan, "p50_ms": lat[len(lat) // 2],
             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "makespan_s": makespan,
-            "requests": len(trace), "mix": kinds}
+            "requests": len(trace), "mix": kinds,
+            "plan_ms_p50": pl[len(pl) // 2], "plan_ms_max": pl[-1]}
 
 
 def serving_load_sweep(pk, ctx, scale=0.15):
