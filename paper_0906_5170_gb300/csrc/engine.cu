@@ -837,7 +837,7 @@ static void launch_unit(casimir_ctx *c, int gi, int j, cudaStream_t st)
     } else if (gi < casimir_ctx::G_CYL2) {
         // the 2D simulation tables are those of groups 0 / 1
         const int f = gi - casimir_ctx::G_T3;
-        launch_step2d_tk(f, 3, (const DevSim2D *)c->groups[f].sims, (const DevTile2 *)G.tiles, G.ntiles, c->d_launch, j, st);
+        launch_step2d_t3(f, (const DevSim2D *)c->groups[f].sims, (const DevTile2 *)G.tiles, G.ntiles, c->d_launch, j, st);
     } else {
         launch_march6_cyl2(gi - casimir_ctx::G_CYL2, (const DevSim6 *)G.sims, (const DevTile2 *)G.tiles, G.ntiles, c->d_launch, j, st);
     }
@@ -1090,7 +1090,7 @@ int casimir_ctx_create(int device, uint64_t budget, casimir_ctx_t **out)
     CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return fail(CASIMIR_EINVAL, "no such CUDA device");
     CUDA_TRY(cudaSetDevice(device));
-    march6_prepare();
+    CUDA_TRY(march6_prepare());
     auto *c = new casimir_ctx();
     c->device = device;
     size_t fr = 0, tot = 0;

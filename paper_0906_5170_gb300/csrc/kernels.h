@@ -118,7 +118,7 @@ void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const D
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 // Shared-memory limits of the staged march variants; once per device before the first launch
 // (outside any stream capture).
-void march6_prepare();
+cudaError_t march6_prepare();
 // The same march on a cylindrical (r, z) lattice (x = r from the axis, y = z), fields ~ exp(i m phi)
 // in the real-phase form (kzA, kzB = +-m), no CPML, no Lorentz media.
 void launch_march6_cyl(int fp64, const DevSim6 *sims, const DevTile *tiles, int ntiles,
@@ -153,7 +153,7 @@ void launch_step2d_t2(int fp64, const DevSim2D *sims, const DevTile2 *tiles, int
                       const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 // K = 3 leapfrog steps per launch: launch L advances steps 3L-2 .. 3L (those up to T), reading
 // buffer (L-1)&1 and writing L&1; tiles tile_xk(3) = 104 columns wide.
-void launch_step2d_tk(int fp64, int k, const DevSim2D *sims, const DevTile2 *tiles, int ntiles,
+void launch_step2d_t3(int fp64, const DevSim2D *sims, const DevTile2 *tiles, int ntiles,
                       const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 // Two steps per launch on the cylindrical lattice (fields ~ exp(i m phi), real): launch L
 // advances steps 2L-1 and 2L (2L-1 alone when 2L > T), reading buffer (L-1)&1, writing L&1;

@@ -288,10 +288,10 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
 
 }  // namespace
 
-void launch_step2d_tk(int fp64, int k, const DevSim2D *sims, const DevTile2 *tiles, int ntiles,
+void launch_step2d_t3(int fp64, const DevSim2D *sims, const DevTile2 *tiles, int ntiles,
                       const int64_t *launch_base, int64_t launch_add, cudaStream_t st)
 {
-    if (ntiles <= 0 || k != 3) return;
+    if (ntiles <= 0) return;
     if (fp64)
         k_step2d_tk<double, 3, 3, 4><<<ntiles, WARPS_K * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
     else

@@ -718,11 +718,11 @@ template <typename R, bool CPLX, bool PML, int NPL, int MINB, int PF>
 struct Variant {
     static constexpr int STG = stage_depth<R, CPLX, PML, NPL>();
     static constexpr size_t SMEM = STG > 0 ? (STG + 1) * slot_bytes<R, CPLX, PML, NPL>() : 0;
-    static void prepare()
+    static cudaError_t prepare()
     {
-        if (SMEM > 48 * 1024)
-            cudaFuncSetAttribute(k_march6<R, CPLX, PML, NPL, MINB, false, PF, STG>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        if (SMEM <= 48 * 1024) return cudaSuccess;
+        return cudaFuncSetAttribute(k_march6<R, CPLX, PML, NPL, MINB, false, PF, STG>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     }
     static void launch(int grid, const DevSim6 *sims, const DevTile *tiles, int ntiles, const int64_t *lb, int64_t la,
                        cudaStream_t st)
@@ -741,9 +741,11 @@ struct Variants {
     using V3 = Variant<R, CPLX, true, 1, M3, 1>;
     using V4 = Variant<R, CPLX, false, 3, M4, 1>;
     using V5 = Variant<R, CPLX, true, 3, M5, 1>;
-    static void prepare()
+    static cudaError_t prepare()
     {
-        V0::prepare(); V1::prepare(); V2::prepare(); V3::prepare(); V4::prepare(); V5::prepare();
+        for (cudaError_t e : {V0::prepare(), V1::prepare(), V2::prepare(), V3::prepare(), V4::prepare(), V5::prepare()})
+            if (e != cudaSuccess) return e;
+        return cudaSuccess;
     }
     static void launch(int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles, const int64_t *lb,
                        int64_t la, cudaStream_t st)
@@ -794,12 +796,11 @@ void launch_march6(int fp64, int cplx, int variant, const DevSim6 *sims, const D
     }
 }
 
-void march6_prepare()
+cudaError_t march6_prepare()
 {
-    VarD1::prepare();
-    VarD0::prepare();
-    VarF1::prepare();
-    VarF0::prepare();
+    for (cudaError_t e : {VarD1::prepare(), VarD0::prepare(), VarF1::prepare(), VarF0::prepare()})
+        if (e != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 }  // namespace cas
