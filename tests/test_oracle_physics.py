@@ -63,10 +63,15 @@ def pressure_3d(a, width, pol):
 
 
 def test_analytic_plate_sums_limits():
-    # wide sidewalls recover the textbook infinite-plate values
+    # wide sidewalls recover the infinite-plate values the paper prints (tests/golden/paper_values.txt):
+    # zeta(3)/(8 pi a^3) per polarisation in the two-dimensional world (the PFA normalisation of the
+    # double-block figure) and pi^2/(240 a^4) for TE + TM in three dimensions
+    from conftest import PAPER_VALUES as G
+    assert G["pfa_2d_pressure"] == pytest.approx(ZETA3 / (8 * math.pi), rel=1e-15)
+    assert G["plate_pressure_3d"] == pytest.approx(math.pi ** 2 / 240, rel=1e-15)
     for pol in ("TM", "TE"):
-        assert pressure_2d(1.0, 400.0, pol) == pytest.approx(-ZETA3 / (8 * math.pi), rel=5e-3)
-        assert pressure_3d(1.0, 400.0, pol) == pytest.approx(-math.pi**2 / 480, rel=5e-3)
+        assert pressure_2d(1.0, 400.0, pol) == pytest.approx(-G["pfa_2d_pressure"], rel=5e-3)
+        assert pressure_3d(1.0, 400.0, pol) == pytest.approx(-G["plate_pressure_3d"] / 2, rel=5e-3)
 
 
 def _upper_plate_force(res, pol, g_variant="plain", **kw):

@@ -113,16 +113,21 @@ def test_pole_lists_are_validated():
 
 
 def test_material_models_of_the_paper():
+    # the constants the paper prints (tests/golden/paper_values.txt)
+    from conftest import PAPER_VALUES as G
     si, sio2 = W.silicon(), W.silica()
     c = W.C_UM_PER_S
     eps_si = lambda w: si["eps_inf"] + si["delta_eps"] * si["omega0"] ** 2 / (si["omega0"] ** 2 - w * w)
-    assert eps_si(0.0) == pytest.approx(11.87)
-    assert eps_si(1e9) == pytest.approx(1.035, abs=1e-9)
-    assert si["omega0"] * c == pytest.approx(6.6e15)
+    assert eps_si(0.0) == pytest.approx(G["silicon_eps_f"])              # static: eps_f
+    assert eps_si(1e9) == pytest.approx(G["silicon_eps_0"], abs=1e-9)   # high frequency: eps_0
+    assert si["omega0"] * c == pytest.approx(G["silicon_omega0_rad_s"])
     eps_s = lambda w: sio2["eps_inf"] + sum(C * w0 * w0 / (w0 * w0 - w * w)
                                            for C, w0 in zip(sio2["delta_eps"], sio2["omega0"]))
-    assert eps_s(0.0) == pytest.approx(1 + 0.829 + 0.095 + 1.098)
-    assert np.allclose(np.array(sio2["omega0"]) * c, [0.867e14, 1.508e14, 203.4e14])
+    Cs = [G["silica_C1"], G["silica_C2"], G["silica_C3"]]
+    assert np.allclose(sio2["delta_eps"], Cs, rtol=0, atol=0)
+    assert eps_s(0.0) == pytest.approx(1 + sum(Cs))
+    assert np.allclose(np.array(sio2["omega0"]) * c,
+                       [G["silica_omega1_rad_s"], G["silica_omega2_rad_s"], G["silica_omega3_rad_s"]])
     # on the imaginary axis both are real, above 1 and falling
     xi = np.array([0.1, 1.0, 10.0])
     e = np.array([eps_s(1j * x).real for x in xi])
