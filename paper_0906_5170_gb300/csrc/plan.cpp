@@ -186,7 +186,10 @@ int find_array(int family, int field, int comp, const ArraySpec *arrs, int narr)
     return -1;
 }
 
-int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err)
+// `same` (or null): a lattice of the same family (and, cylindrical, the same m) built for
+// another k-point.  Materials, CPML and the Lorentz table do not depend on k, so they are
+// copied from it instead of being rasterised again.
+int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err, const Geo *same)
 {
     const casimir_problem &p = P.prob;
     ArraySpec arrs[6];
@@ -219,6 +222,20 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err)
     g->complex_fields = cplxf;
     if ((cplxf || g->kz != 0.0) && family != FAM_FULL) { *err = "k_z or a complex Bloch phase needs polarization FULL"; return CASIMIR_EINVAL; }
 
+    if (same) {
+        g->mat = same->mat;
+        g->table = same->table;
+        g->nmat = same->nmat;
+        g->lorentz = same->lorentz;
+        g->npoles = same->npoles;
+        g->has_lorentz = same->has_lorentz;
+        for (int a = 0; a < 3; ++a) {
+            g->has_pml[a] = same->has_pml[a];
+            for (int h = 0; h < 2; ++h)
+                for (int q = 0; q < 3; ++q) g->pml[a][h][q] = same->pml[a][h][q];
+        }
+        return CASIMIR_OK;
+    }
     int64_t ncell = (int64_t)p.n[0] * p.n[1] * p.n[2];
     g->mat.assign(ncell, 0);
     std::map<std::vector<double>, int> ids;
@@ -293,19 +310,6 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err)
     return CASIMIR_OK;
 }
 
-void add_entry(std::vector<Entry> &v, std::map<std::pair<int, int64_t>, size_t> &at, int arr, int64_t idx, cplx val)
-{
-    auto key = std::make_pair(arr, idx);
-    auto it = at.find(key);
-    if (it == at.end()) {
-        at.emplace(key, v.size());
-        v.push_back(Entry{arr, idx, val.real(), val.imag()});
-    } else {
-        v[it->second].re += val.real();
-        v[it->second].im += val.imag();
-    }
-}
-
 }  // namespace
 
 int family_arrays(int family, ArraySpec out[6])
@@ -334,28 +338,41 @@ int family_arrays(int family, ArraySpec out[6])
 // Im g(-t) of Appendix A.  Rotating g(-t) = (1/2pi) int_0^inf g(xi) e^{i xi t} dxi
 // onto xi = i eta gives the Laplace integral
 //   Im g(-t) = (1/2pi) int_0^inf sqrt(1 + sigma/eta) (eta + sigma/2) e^{-eta t} d eta,
-// evaluated with eta = exp(pi/2 sinh(tau)) (exp-sinh quadrature, which absorbs
-// the eta^{-1/2} end point and the exponential tail).
+// evaluated with eta = e(tau) / t, e(tau) = exp(pi/2 sinh(tau)) (exp-sinh quadrature,
+// which absorbs the eta^{-1/2} end point and the exponential tail; scaling by 1/t puts the
+// integrand's peak near tau = 0).  With that scaling e^{-eta t} = e^{-e(tau)} does not depend
+// on t, so the nodes e_k and the t-free part of their weights, e_k (pi/2) cosh(tau_k) e^{-e_k},
+// are computed once and every t costs one square root per node.
+namespace {
+struct ExpSinhNodes {
+    static constexpr double h = 1.0 / 64.0;
+    std::vector<double> e, a;
+    ExpSinhNodes()
+    {
+        for (int k = -6 * 64; k <= 6 * 64; ++k) {
+            const double tau = k * h;
+            const double ek = std::exp(0.5 * kPi * std::sinh(tau));
+            const double ak = ek * 0.5 * kPi * std::cosh(tau) * std::exp(-ek);
+            if (!(ek > 0.0) || !std::isfinite(ek) || !std::isfinite(ak)) continue;
+            e.push_back(ek);
+            a.push_back(ak);
+        }
+    }
+};
+}  // namespace
+
 double img_plain(double t, double sigma)
 {
     if (sigma == 0.0) return 1.0 / (2.0 * kPi * t * t);
-    auto f = [&](double eta) {
-        return std::sqrt(1.0 + sigma / eta) * (eta + 0.5 * sigma) * std::exp(-eta * t);
-    };
-    // scale the variable so that the integrand's peak sits near eta ~ 1/t
-    double scale = 1.0 / t;
-    double h = 1.0 / 64.0;
+    static const ExpSinhNodes nodes;
+    const double st = sigma * t, hs = 0.5 * sigma, it = 1.0 / t;
     double sum = 0.0;
-    for (int k = -6 * 64; k <= 6 * 64; ++k) {
-        double tau = k * h;
-        double e = std::exp(0.5 * kPi * std::sinh(tau));
-        double eta = scale * e;
-        if (!(eta > 0.0) || !std::isfinite(eta)) continue;
-        double w = scale * e * 0.5 * kPi * std::cosh(tau);
-        double v = f(eta) * w;
+    for (size_t k = 0; k < nodes.e.size(); ++k) {
+        const double ek = nodes.e[k];
+        const double v = nodes.a[k] * std::sqrt(1.0 + st / ek) * (ek * it + hs);
         if (std::isfinite(v)) sum += v;
     }
-    return sum * h / (2.0 * kPi);
+    return sum * it * ExpSinhNodes::h / (2.0 * kPi);
 }
 
 int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
@@ -496,10 +513,15 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
 
     // lattices
     std::map<std::pair<int, int>, int> geo_of;
+    std::map<std::pair<int, int>, int> lattice_of;   // (family, m if cylindrical) -> first geo built
+    const bool cyl_coords = p.coords == CASIMIR_COORDS_CYLINDRICAL;
     for (int k = 0; k < p.n_kpoints; ++k)
         for (int fam : fams) {
             Geo g;
-            int rc = build_geo(*P, fam, k, &g, err);
+            const std::pair<int, int> lk{fam, cyl_coords ? P->kpoints[k].m : 0};
+            auto li = lattice_of.find(lk);
+            int rc = build_geo(*P, fam, k, &g, err, li == lattice_of.end() ? nullptr : &P->geos[li->second]);
+            if (li == lattice_of.end()) lattice_of[lk] = (int)P->geos.size();
             if (rc) return rc;
             geo_of[{k, fam}] = (int)P->geos.size();
             P->geos.push_back(std::move(g));
@@ -515,7 +537,7 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
             for (int kind = 0; kind < 2; ++kind)
                 for (int c = 0; c < 3; ++c) srcs.push_back({fam, kind, c});
     }
-    std::vector<std::pair<int64_t, cplx>> st;
+    using Stencil = std::vector<std::pair<int64_t, cplx>>;
     for (int k = 0; k < p.n_kpoints; ++k)
         for (int fi = 0; fi < p.n_faces; ++fi) {
             const casimir_face &f = P->faces[fi];
@@ -536,7 +558,49 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
                 epsS[q] = m.eps;
                 muS[q] = m.mu;
             }
-            for (auto hm : harms)
+            // interpolation stencils of every pixel onto the sites of one array of one family's
+            // lattice at this k-point, shared by every harmonic and source of the face; each
+            // stencil site also carries its index among the distinct sites the face touches
+            struct Stencils {
+                std::vector<Stencil> st;
+                std::vector<std::vector<int>> uid;
+                int nu = 0;
+            };
+            std::map<std::pair<int, int>, Stencils> stc;
+            auto stencils = [&](int fam, const Geo &g, const ArraySpec &as, int arr) -> const Stencils & {
+                auto it = stc.find({fam, arr});
+                if (it != stc.end()) return it->second;
+                Stencils &v = stc[{fam, arr}];
+                v.st.resize(px.x.size());
+                v.uid.resize(px.x.size());
+                std::map<int64_t, int> sites;
+                for (size_t q = 0; q < px.x.size(); ++q) {
+                    stencil(*P, g, as, px.x[q].data(), v.st[q]);
+                    for (auto &e : v.st[q]) v.uid[q].push_back(sites.emplace(e.first, (int)sites.size()).first->second);
+                }
+                v.nu = (int)sites.size();
+                return v;
+            };
+            // entries of one simulation, summed per (array, site) and kept in first-touch order
+            std::vector<int> slot[6];
+            auto add = [&](std::vector<Entry> &v, int arr, int nu, int u, int64_t idx, cplx val) {
+                std::vector<int> &sl = slot[arr];
+                if ((int)sl.size() < nu) sl.resize(nu, -1);
+                if (sl[u] < 0) {
+                    sl[u] = (int)v.size();
+                    v.push_back(Entry{arr, idx, val.real(), val.imag()});
+                } else {
+                    v[sl[u]].re += val.real();
+                    v[sl[u]].im += val.imag();
+                }
+            };
+            auto clear_slots = [&](const std::vector<Entry> &v, const std::vector<int> &u_of) {
+                for (size_t e = 0; e < v.size(); ++e) slot[v[e].arr][u_of[e]] = -1;
+            };
+            std::vector<int> u_of;
+            std::vector<double> fv(px.x.size());
+            for (auto hm : harms) {
+                for (size_t q = 0; q < px.x.size(); ++q) fv[q] = basis_value(*P, px, (int)q, hm.first, hm.second);
                 for (auto s : srcs) {
                     // exact pruning: for force axis i and a face with normal a != i only c == a contributes
                     if (!(f.axis == p.force_axis || s.comp == f.axis)) continue;
@@ -554,14 +618,13 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
                     int narr = family_arrays(s.fam, arrs);
                     int sa = find_array(s.fam, s.kind, s.comp, arrs, narr);
                     sim.second_u = (sa == 0) ? 1 : 0;
-                    std::vector<double> fv(px.x.size());
-                    for (size_t q = 0; q < px.x.size(); ++q) fv[q] = basis_value(*P, px, (int)q, hm.first, hm.second);
                     // source: flux after the impulse D_c = -(dA/dV) W_c^H f, stored as E = D/eps (masked)
-                    std::map<std::pair<int, int64_t>, size_t> at;
+                    const Stencils &ss = stencils(s.fam, g, arrs[sa], sa);
+                    u_of.clear();
                     for (size_t q = 0; q < px.x.size(); ++q) {
                         if (fv[q] == 0.0) continue;
-                        stencil(*P, g, arrs[sa], px.x[q].data(), st);
-                        for (auto &e : st) {
+                        for (size_t j = 0; j < ss.st[q].size(); ++j) {
+                            const auto &e = ss.st[q][j];
                             // cylindrical: the surface current on the surface of revolution averaged over
                             // the site's ring carries r(pixel) / w(site), w = r_site (Delta/8 on the axis)
                             double scale = 1.0;
@@ -569,9 +632,12 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
                                 double rs = ((double)(e.first % p.n[0]) + arrs[sa].off[0]) * P->dx;
                                 scale = px.x[q][0] / (rs > 0.5 * kTol * P->dx ? rs : 0.125 * P->dx);
                             }
-                            add_entry(sim.src, at, sa, e.first, -std::conj(e.second) * fv[q] * scale / P->dx);
+                            const size_t before = sim.src.size();
+                            add(sim.src, sa, ss.nu, ss.uid[q][j], e.first, -std::conj(e.second) * fv[q] * scale / P->dx);
+                            if (sim.src.size() > before) u_of.push_back(ss.uid[q][j]);
                         }
                     }
+                    clear_slots(sim.src, u_of);
                     for (auto &e : sim.src) {
                         double c = g.table[(size_t)g.mat[e.idx] * narr + sa] * arrs[sa].sign;
                         e.re *= c;
@@ -581,7 +647,7 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
                     double nv[3] = {0, 0, 0};
                     nv[f.axis] = f.sign;
                     int i = p.force_axis;
-                    std::map<std::pair<int, int64_t>, size_t> am;
+                    u_of.clear();
                     for (size_t q = 0; q < px.x.size(); ++q) {
                         if (fv[q] == 0.0) continue;
                         double base = px.dA * (s.kind == 0 ? epsS[q] : muS[q]) * fv[q];
@@ -591,13 +657,19 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
                             if (coefs[t] == 0.0) continue;
                             int ma = find_array(s.fam, s.kind, comps[t], arrs, narr);
                             if (ma < 0) continue;   // component absent in this family: identically zero
-                            stencil(*P, g, arrs[ma], px.x[q].data(), st);
-                            for (auto &e : st)
-                                add_entry(sim.meas, am, ma, e.first, e.second * (base * coefs[t] * arrs[ma].sign));
+                            const Stencils &sm = stencils(s.fam, g, arrs[ma], ma);
+                            for (size_t j = 0; j < sm.st[q].size(); ++j) {
+                                const size_t before = sim.meas.size();
+                                add(sim.meas, ma, sm.nu, sm.uid[q][j], sm.st[q][j].first,
+                                    sm.st[q][j].second * (base * coefs[t] * arrs[ma].sign));
+                                if (sim.meas.size() > before) u_of.push_back(sm.uid[q][j]);
+                            }
                         }
                     }
+                    clear_slots(sim.meas, u_of);
                     P->sims.push_back(std::move(sim));
                 }
+            }
         }
     if (P->sims.empty()) { *err = "no contributing simulations"; return CASIMIR_EINVAL; }
     return CASIMIR_OK;
