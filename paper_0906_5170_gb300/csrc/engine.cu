@@ -886,6 +886,7 @@ static int run_chunk(casimir_ctx *c, int k)
     }
     auto it = c->graphs.find(k);
     if (!no_graphs && it == c->graphs.end()) {
+        std::lock_guard<std::mutex> cg(c->capture_mu);
         cudaGraph_t g;
         CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         launch_steps(c, k);
@@ -1003,13 +1004,17 @@ static int engine_iterate(casimir_ctx *c)
             if (!done) r->status = r->cancel ? CASIMIR_ECANCELED : CASIMIR_ETIMEOUT;
         }
     }
-    for (size_t q = 0; q < c->active.size();) {
-        casimir_request *r = c->active[q];
-        if (r->copy_issued && cudaEventQuery(r->done_ev) == cudaSuccess) {
-            c->active.erase(c->active.begin() + q);
-            finish_request(c, r, r->status.load());
-        } else {
-            ++q;
+    {
+        // the active list and the memory accounting are read by other threads under the lock
+        std::lock_guard<std::mutex> lk(c->mu);
+        for (size_t q = 0; q < c->active.size();) {
+            casimir_request *r = c->active[q];
+            if (r->copy_issued && cudaEventQuery(r->done_ev) == cudaSuccess) {
+                c->active.erase(c->active.begin() + q);
+                finish_request(c, r, r->status.load());
+            } else {
+                ++q;
+            }
         }
     }
     activate_waves(c);
@@ -1042,6 +1047,7 @@ static void worker_main(casimir_ctx *c)
             c->queue.pop_front();
             int rc = admit(c, r);
             if (rc) {
+                r->msg = g_err;
                 r->status = rc;
                 r->plan->inflight--;
                 r->state = 3;
@@ -1056,10 +1062,11 @@ static void worker_main(casimir_ctx *c)
         int rc = engine_iterate(c);
         lk.lock();
         if (rc) {
-            std::string msg = g_err;
+            const std::string msg = g_err;
             for (casimir_request *r : c->active) {
                 dev_free(c, r->block);
                 r->block = nullptr;
+                r->msg = msg;
                 r->status = rc;
                 r->plan->inflight--;
                 r->state = 3;
@@ -1427,6 +1434,7 @@ void casimir_plan_destroy(casimir_plan_t *P)
     }
     if (c && P->dev.block) {
         std::lock_guard<std::mutex> lk(c->mu);
+        std::lock_guard<std::mutex> cg(c->capture_mu);
         cudaStreamSynchronize(c->stream);
         dev_free(c, P->dev.block);
         c->used -= P->dev.bytes;
@@ -1485,9 +1493,15 @@ int casimir_force(casimir_ticket r, int wait_ms, double F[3], double *err_est, c
         st->cell_updates = r->plan->cells * (int64_t)r->plan->data.prob.n_steps;
         st->kernel_launches = r->launches;
     }
+    const std::string msg = r->msg;
     lk.unlock();
-    release(r);
-    if (status != CASIMIR_OK) return fail(status, status == CASIMIR_ETIMEOUT ? "watchdog stopped the run" : "request failed");
+    {
+        std::lock_guard<std::mutex> cg(c->capture_mu);
+        release(r);
+    }
+    if (status == CASIMIR_ETIMEOUT) return fail(status, "watchdog stopped the run");
+    if (status == CASIMIR_ECANCELED) return fail(status, "request cancelled");
+    if (status != CASIMIR_OK) return fail(status, msg.empty() ? "request failed" : msg);
     return CASIMIR_OK;
 }
 

@@ -154,6 +154,7 @@ struct casimir_request {
     cudaEvent_t done_ev = nullptr;
     bool copy_issued = false;
     std::vector<double> per_sim;
+    std::string msg;          // why the request failed (the worker's error message)
     // the request's simulations run in waves (contiguous ranges in plan order)
     struct Wave {
         size_t s_begin, s_end;
@@ -215,6 +216,10 @@ struct casimir_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join[NAUX] = {};
     // worker
     std::mutex mu;
+    // Held while the worker captures a chunk graph on `stream`, and by calls from other
+    // threads that synchronise that stream or free device or pinned memory: an operation on
+    // a stream under capture is not permitted and would invalidate the capture.
+    std::mutex capture_mu;
     std::condition_variable cv;
     std::deque<casimir_request *> queue;
     std::thread worker;

@@ -156,6 +156,31 @@ def test_watchdog_and_cancel_leave_context_usable(ctx, pk):
     _check(ctx, q, "after", True)
 
 
+def test_plan_teardown_overlapping_graph_capture(ctx, pk):
+    """Destroying a plan from the caller's thread (its tables are freed after a synchronisation of
+    the context stream) while the worker admits the next request and captures its first chunk
+    graph on that stream: the capture and the request are unaffected; a cancelled request ends
+    cancelled, never failed."""
+    p = W.piston_small(n_steps=120)
+    ref = ctx.plan(p).run()[0]
+    prev = ctx.plan(p)
+    prev.run()                                  # its tables are on the device
+    for it in range(12):
+        pl = ctx.plan(p)
+        t = pl.submit()
+        if it % 2:
+            t.cancel()
+        prev.close()                            # overlaps the worker's admission and capture
+        prev = pl
+        try:
+            F = t.force(-1)[0]
+        except pk.CasimirError as e:
+            assert it % 2 and e.code == -6, (it, e)
+            continue
+        assert F == pytest.approx(ref, rel=1e-9, abs=0)
+    prev.close()
+
+
 def test_budget_rejects_oversized_plan(pk):
     c = pk.Context(0, hbm_budget_bytes=1 << 20)
     with pytest.raises(pk.CasimirError) as e:
