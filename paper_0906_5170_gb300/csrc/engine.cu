@@ -520,13 +520,14 @@ static int admit(casimir_ctx *c, casimir_request *r)
     r->waves.clear();
     r->waves_done = 0;
     const size_t ns = P->sims.size();
+    const int64_t wave_bytes = c->wave_bytes.load();
     for (size_t q = 0; q < ns;) {
         casimir_request::Wave w{q, q, 0, 0, 0, 0};
         while (w.s_end < ns) {
             size_t e = w.s_end;
             int64_t next = e + 1 < ns ? P->sims[e + 1].field_off : P->field_elems;
             int64_t b = (next - P->sims[e].field_off) * (int64_t)P->rsize;
-            if (w.s_end > w.s_begin && c->wave_bytes > 0 && w.bytes + b > c->wave_bytes) break;
+            if (w.s_end > w.s_begin && wave_bytes > 0 && w.bytes + b > wave_bytes) break;
             w.bytes += b;
             w.cells += (int64_t)P->sims[e].nx * P->sims[e].ny * P->sims[e].nz;
             ++w.s_end;
@@ -546,10 +547,11 @@ static int admit(casimir_ctx *c, casimir_request *r)
 // within the wave budget; a wave always starts when nothing else is active.
 static void activate_waves(casimir_ctx *c)
 {
+    const int64_t wave_bytes = c->wave_bytes.load();
     while (!c->pending_waves.empty()) {
         auto pw = c->pending_waves.front();
         casimir_request::Wave &w = pw.first->waves[pw.second];
-        if (!c->active_waves.empty() && c->wave_bytes > 0 && c->active_bytes + w.bytes > c->wave_bytes) break;
+        if (!c->active_waves.empty() && wave_bytes > 0 && c->active_bytes + w.bytes > wave_bytes) break;
         c->pending_waves.pop_front();
         w.s0 = c->h_launch - 1;
         w.state = 1;
@@ -963,6 +965,7 @@ static int engine_iterate(casimir_ctx *c)
             CUDA_TRY(cudaEventSynchronize(c->ev1));
             float ms = 0;
             cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+            std::lock_guard<std::mutex> lk(c->mu);   // the statistics are read under the lock
             c->step_ms += ms;
             c->step_launches += k;
             for (auto &aw : c->active_waves) {
@@ -992,7 +995,8 @@ static int engine_iterate(casimir_ctx *c)
     for (casimir_request *r : c->active) {
         if (r->copy_issued) continue;
         bool done = r->waves_done == r->waves.size();
-        bool timed_out = c->watchdog_ms > 0 && now_ms() - r->t_admit > c->watchdog_ms;
+        const double wd = c->watchdog_ms.load();
+        bool timed_out = wd > 0 && now_ms() - r->t_admit > wd;
         if (done || timed_out || r->cancel) {
             if (!done) drop_waves(c, r);
             size_t ns = r->plan->sims.size();

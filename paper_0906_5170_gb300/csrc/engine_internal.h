@@ -175,7 +175,7 @@ struct casimir_ctx {
     casimir_alloc_fn alloc = nullptr;
     casimir_free_fn freef = nullptr;
     void *user = nullptr;
-    double watchdog_ms = 0;
+    std::atomic<double> watchdog_ms{0};   // set by callers, read by the worker
     int64_t *d_launch = nullptr;
     int64_t h_launch = 1;            // index of the next launch
     // active set
@@ -199,7 +199,7 @@ struct casimir_ctx {
     int ntiles = 0;                   // over all groups
     // waves: simulations are activated in groups whose field bytes fit `wave_bytes`
     // (0: a whole request at once), so that the active working set can stay in L2
-    int64_t wave_bytes = 0;
+    std::atomic<int64_t> wave_bytes{0};
     int64_t active_bytes = 0;
     std::vector<std::pair<casimir_request *, size_t>> active_waves;
     std::deque<std::pair<casimir_request *, size_t>> pending_waves;
