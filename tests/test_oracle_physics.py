@@ -172,3 +172,31 @@ def test_p14_mirror_symmetry():
               faces=box_faces([2.5 - d, 0.5 - d], [3.5 + d, 1.5 + d], 2))
     f0, parts0, _ = oracle.force(pc, return_parts=True)
     assert abs(f0) < 1e-11 * sum(abs(x) for x in parts0)
+
+
+def test_p13_harmonic_contributions_fall_as_n_to_the_minus_4():
+    # Sec. III A: on a rectangular contour the fields, seen as functions along a face, have
+    # nonzero slopes at the corners while every cosine has zero slope there, so their cosine
+    # coefficients fall as n^-2 and each harmonic's force contribution as n^-4.  Contour 0.25
+    # away from the right block of a 2D TM piston (away from the block's own edge fields), 45
+    # pixels per face at resolution 30; contributions summed over faces and sources per n; the
+    # log-log slope over n = 8..24 (below half the face's pixel count, where the lattice takes
+    # over), for even and odd n separately (the mirror symmetry about the block's mid-plane
+    # splits them) and together.
+    res = 30
+    p = piston_small(0.5, resolution=res, n_harm=1000, n_steps=int(20 / (0.5 / res)),
+                     polarization="TM", precision="fp64")
+    p["faces"] = box_faces([3.25, 0.25], [4.75, 1.75], 2)
+    F, parts, sims = oracle.force(p, return_parts=True)
+    c = {}
+    for v, s in zip(parts, sims):
+        c[s["harm"][0]] = c.get(s["harm"][0], 0.0) + v
+    n = np.array(sorted(c))
+    v = np.array([c[k] for k in n])
+    assert len(n) == 45
+    assert F < 0 and abs(v[0]) > 0.5 * abs(F)          # attraction; n = 0 carries most of it
+    tail = (n >= 8) & (n <= 24)
+    assert np.all(v[tail] > 0)                          # one sign over the fitted range
+    for sel in (tail & (n % 2 == 0), tail & (n % 2 == 1), tail):
+        slope = np.polyfit(np.log(n[sel]), np.log(v[sel]), 1)[0]
+        assert -4.5 < slope < -3.5, slope
