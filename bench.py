@@ -346,6 +346,29 @@ def oracle_reference(probs):
     return out
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu names Arm cores too; /proc/cpuinfo as a fallback)."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and v.strip():
+                return v.strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() == "model name" and v.strip():
+                    return v.strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(budget_s=15.0):
     """The FP64 oracle on a bounded sample of the workload: simulations of the
     h = 0.5 geometry for a shortened number of steps, one per host core."""
@@ -365,7 +388,7 @@ def cpu_baseline(budget_s=15.0):
     dt = time.perf_counter() - t0
     cells = p["n"][0] * p["n"][1]
     cups = len(sims) * cells * T / dt
-    return {"value": cups / 1e9, "unit": "Gcell-updates/s", "cores": cores, "kind": "oracle",
+    return {"value": cups / 1e9, "unit": "Gcell-updates/s", "cores": cores, "cpu": cpu_model(), "kind": "oracle",
             "sample": f"{len(sims)} sims of the h=0.5 geometry (400x80) x {T} steps, FP64, {dt:.2f} s"}, dt
 
 
