@@ -247,8 +247,11 @@ int casimir_submit(casimir_plan_t *plan, uint64_t user_tag, casimir_ticket *out)
 /* Wait up to `wait_ms` (0: poll, < 0: forever) for the result.  On success F[3]
  * holds the force (only F[force_axis] is non-zero), *err_est (may be NULL) an
  * estimate of the truncation error of the time integral, *st (may be NULL)
- * timings.  Returns CASIMIR_NOTREADY while running.  After a return other than
- * CASIMIR_NOTREADY the ticket is released. */
+ * timings.  Returns CASIMIR_NOTREADY while running; CASIMIR_ETIMEOUT or
+ * CASIMIR_ECANCELED for a request the watchdog stopped or the caller cancelled; for
+ * a request that failed on the device, the failing call's code (CASIMIR_ECUDA,
+ * CASIMIR_ENOMEM), with that call's message in casimir_last_error() of the calling
+ * thread.  After a return other than CASIMIR_NOTREADY the ticket is released. */
 int casimir_force(casimir_ticket ticket, int wait_ms, double F[3], double *err_est, casimir_stats *st);
 
 /* Cancel a queued or running request (its ticket is still released by casimir_force). */
