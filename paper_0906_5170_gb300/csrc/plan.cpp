@@ -66,6 +66,7 @@ Mat material_at(const PlanData &P, const double x[3])
 // Canonical coordinate of a site along axis a in [0, L).
 double canon(double x, double L)
 {
+    if (x >= 0.0 && x <= L - 1e-9 * L) return x;   // already canonical (fmod would return x)
     double y = std::fmod(x, L);
     if (y < 0) y += L;
     if (y > L - 1e-9 * L) y = 0.0;
@@ -240,7 +241,8 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err, 
     g->mat.assign(ncell, 0);
     std::map<std::vector<double>, int> ids;
     constexpr int NPK = 6 * CASIMIR_MAX_POLES;   // (delta_eps, omega0) per pole and E component
-    std::vector<double> key(narr + NPK);
+    std::vector<double> key(narr + NPK), prev_key;
+    int prev_id = -1;
     double L[3] = {p.n[0] * P.dx, p.n[1] * P.dx, p.n[2] * P.dx};
     for (int kk = 0; kk < p.n[2]; ++kk)
         for (int j = 0; j < p.n[1]; ++j)
@@ -277,14 +279,21 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err, 
                     }
                     key[a] = c;
                 }
-                auto it = ids.find(key);
+                // neighbouring cells mostly share their key: try the previous cell's first
                 int id;
-                if (it == ids.end()) {
-                    id = (int)ids.size();
-                    if (id > 255) { *err = "more than 256 distinct material sites"; return CASIMIR_EINVAL; }
-                    ids.emplace(key, id);
+                if (prev_id >= 0 && key == prev_key) {
+                    id = prev_id;
                 } else {
-                    id = it->second;
+                    auto it = ids.find(key);
+                    if (it == ids.end()) {
+                        id = (int)ids.size();
+                        if (id > 255) { *err = "more than 256 distinct material sites"; return CASIMIR_EINVAL; }
+                        ids.emplace(key, id);
+                    } else {
+                        id = it->second;
+                    }
+                    prev_key = key;
+                    prev_id = id;
                 }
                 g->mat[((int64_t)kk * p.n[1] + j) * p.n[0] + i] = (uint8_t)id;
             }
