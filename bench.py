@@ -34,7 +34,8 @@ DRAM_BYTES_PER_CELL_LAUNCH = {"k_step2d_t2<float>": (205.327e6 + 163.056e6) / 16
                               "k_step2d_tk<float, 3>": (210.452e6 + 169.787e6) / 16998400}
 
 METRIC = "forces/s and Gcell-updates/s (% HBM roofline), p50/p99 latency vs plain at 1e-4 rel"
-WORKLOAD = "2D piston sweep: 8 h x TE+TM x 40 harmonics, 400x(80..280) cells, 20000 steps"
+def workload_name(time_steps=20000):
+    return f"2D piston sweep: 8 h x TE+TM x 40 harmonics, 400x(80..280) cells, {time_steps} steps"
 
 
 def peaks():
@@ -470,7 +471,7 @@ def run_reference(args):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000 * total_dt / max(1, args.steps), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "sample": cb["sample"]},
+           "config": {"workload": workload_name(args.time_steps), "sample": cb["sample"]},
            "cpu_baseline": dict(cb, value=v),
            "e2e": {"value": v, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -657,7 +658,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "forces_per_step": n_forces,
+            "config": {"workload": workload_name(args.time_steps), "forces_per_step": n_forces,
                        "sims_per_step": sum(i["n_sims"] for i in infos),
                        "cell_updates_per_step": cells_per_step, "time_steps": args.time_steps,
                        "l2": "inputs larger than L2 (%.1f GB of fields)" % (sum(i["device_bytes"] for i in infos) / 1e9),
