@@ -50,7 +50,8 @@ extern "C" {
 
 /* ---- problem description (Sec. II and III) ---------------------------------- */
 enum { CASIMIR_BC_PEC = 0, CASIMIR_BC_PML = 1, CASIMIR_BC_PERIODIC = 2 };
-enum { CASIMIR_SHAPE_BOX = 0, CASIMIR_SHAPE_SPHERE = 1 };
+enum { CASIMIR_SHAPE_BOX = 0, CASIMIR_SHAPE_SPHERE = 1,
+       CASIMIR_SHAPE_GRID = 2 };   /* a voxel mask over the box [lo, hi] (arbitrary geometry) */
 enum { CASIMIR_MAT_PEC = 0,        /* eps = -inf (Sec. III A): tangential E vanishes */
        CASIMIR_MAT_PMC = 1,        /* mu = -inf (Sec. III A): tangential H vanishes */
        CASIMIR_MAT_DIELECTRIC = 2, /* constant eps, mu */
@@ -79,7 +80,16 @@ enum { CASIMIR_COORDS_CARTESIAN = 0,
                                              m = 0, 2 for m > 0: the +m and -m terms). */
 
 /* One geometric object; later objects override earlier ones where they overlap.
- * Membership is closed (boundary points belong to the object). */
+ * Membership is closed (boundary points belong to the object).
+ *
+ * CASIMIR_SHAPE_GRID: `mask` holds mask_n[0] x mask_n[1] x mask_n[2] bytes, x fastest
+ * (index (k * mask_n[1] + j) * mask_n[0] + i); voxel (i, j, k) spans the box [lo, hi] cut
+ * into mask_n[a] equal slabs along each axis a, and the object is the union of the closed
+ * voxels whose byte is non-zero (so a mask of voxels aligned with a box reproduces that box).
+ * Two-dimensional problems need mask_n[2] == 1 and ignore lo[2], hi[2].  Every used axis
+ * needs hi[a] > lo[a] and mask_n[a] >= 1 (CASIMIR_EINVAL otherwise).  The planner copies
+ * the mask; the caller may free it once casimir_plan returns.  Several materials: one
+ * object per material, each with its own mask. */
 typedef struct {
     int shape;           /* CASIMIR_SHAPE_* */
     int kind;            /* CASIMIR_MAT_* */
@@ -92,6 +102,9 @@ typedef struct {
     double omega0[CASIMIR_MAX_POLES];     /* Lorentz pole frequencies (> 0 where delta_eps > 0); every
                                              pole needs omega0 dt < 2, and the medium eps(4/dt^2) above
                                              the lattice's (dt/2)^2 k_max^2 (CASIMIR_EINVAL otherwise) */
+    const uint8_t *mask; /* CASIMIR_SHAPE_GRID: the voxel mask (NULL for other shapes) */
+    int mask_n[3];       /* CASIMIR_SHAPE_GRID: voxels per axis */
+    int reserved;
 } casimir_object;
 
 /* One axis-aligned face of the stress surface S: normal along `axis`, outward

@@ -195,6 +195,31 @@ def _inside(obj, pts, dims, d):
         for a in range(dims):
             r2 += (pts[a] - obj["center"][a]) ** 2
         return r2 <= (obj["radius"] + tol) ** 2
+    if obj["shape"] == "grid":
+        # voxel (i, j, k) of mask[i, j(, k)] is the closed box lo + [i, i+1] h along each axis,
+        # h = (hi - lo) / (voxels along that axis); the object is the union of the filled ones.
+        # A point is in it when a filled voxel lies within the tolerance of it.
+        mask = np.asarray(obj["mask"]) != 0
+        if mask.ndim == 2:
+            mask = mask[:, :, None]
+        inbox = np.ones(pts[0].shape, dtype=bool)
+        near = []                                   # per axis: the voxel indices within tol
+        for a in range(3):
+            if a >= dims:
+                near.append([np.zeros(pts[0].shape, dtype=int)])
+                continue
+            lo, hi, n = obj["lo"][a], obj["hi"][a], mask.shape[a]
+            inbox &= (pts[a] >= lo - tol) & (pts[a] <= hi + tol)
+            h = (hi - lo) / n
+            u = (pts[a] - lo) / h
+            near.append([np.clip(np.floor(u - tol / h), 0, n - 1).astype(int),
+                         np.clip(np.floor(u + tol / h), 0, n - 1).astype(int)])
+        out = np.zeros(pts[0].shape, dtype=bool)
+        for i in near[0]:
+            for j in near[1]:
+                for k in near[2]:
+                    out |= mask[i, j, k]
+        return out & inbox
     raise ValueError(obj["shape"])
 
 

@@ -19,7 +19,7 @@ OK, NOTREADY = 0, 1
 EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ECANCELED = -1, -2, -3, -4, -5, -6
 
 BC = {"pec": 0, "pml": 1, "periodic": 2}
-SHAPE = {"box": 0, "sphere": 1}
+SHAPE = {"box": 0, "sphere": 1, "grid": 2}
 KIND = {"pec": 0, "pmc": 1, "dielectric": 2, "lorentz": 3}
 POL = {"TM": 1, "TE": 2, "TE+TM": 3, "full": 4}
 GVAR = {"plain": 0, "zinv": 1}
@@ -37,7 +37,8 @@ class Object(ctypes.Structure):
     _fields_ = [("shape", ctypes.c_int), ("kind", ctypes.c_int), ("lo", D3), ("hi", D3),
                 ("center", D3), ("radius", ctypes.c_double), ("eps", ctypes.c_double),
                 ("mu", ctypes.c_double), ("eps_inf", ctypes.c_double), ("delta_eps", DP3),
-                ("omega0", DP3)]
+                ("omega0", DP3), ("mask", ctypes.POINTER(ctypes.c_uint8)), ("mask_n", I3),
+                ("reserved", ctypes.c_int)]
 
 
 def _poles(o: dict):
@@ -49,6 +50,17 @@ def _poles(o: dict):
         raise ValueError(f"lorentz: delta_eps and omega0 need 1..{MAX_POLES} entries each")
     pad = [0.0] * (MAX_POLES - len(de))
     return DP3(*[float(x) for x in de], *pad), DP3(*[float(x) for x in w0], *pad)
+
+
+def _mask_bytes(mask):
+    """A grid object's mask, indexed mask[i, j] or mask[i, j, k], as C-ordered (k, j, i) bytes."""
+    import numpy as np
+    m = np.asarray(mask)
+    if m.ndim == 2:
+        m = m[:, :, None]
+    if m.ndim != 3:
+        raise ValueError("grid mask: 2 or 3 dimensions")
+    return np.ascontiguousarray((m != 0).transpose(2, 1, 0), dtype=np.uint8)
 
 
 class Face(ctypes.Structure):
@@ -165,6 +177,7 @@ class MarshalledProblem:
 
     def __init__(self, p: dict):
         objs = p.get("objects", [])
+        self.masks = []                      # voxel masks of grid objects, kept alive with the struct
         self.objects = (Object * max(1, len(objs)))()
         for i, o in enumerate(objs):
             ob = self.objects[i]
@@ -178,6 +191,11 @@ class MarshalledProblem:
             ob.mu = float(o.get("mu", 1.0))
             ob.eps_inf = float(o.get("eps_inf", 1.0))
             ob.delta_eps, ob.omega0 = _poles(o)
+            if o["shape"] == "grid":
+                m = _mask_bytes(o["mask"])
+                self.masks.append(m)
+                ob.mask = m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+                ob.mask_n = I3(*[int(x) for x in m.shape[::-1]])
         faces = p["faces"]
         self.faces = (Face * max(1, len(faces)))()
         for i, f in enumerate(faces):

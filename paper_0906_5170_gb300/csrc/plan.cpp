@@ -33,6 +33,24 @@ bool inside(const casimir_object &o, const double x[3], int dims, double d)
             if (x[a] < o.lo[a] - tol || x[a] > o.hi[a] + tol) return false;
         return true;
     }
+    if (o.shape == CASIMIR_SHAPE_GRID) {
+        // the union of the closed filled voxels: test the voxels within the tolerance of x
+        // along each axis (one, or two when x lies on a voxel face)
+        int c[3][2];
+        for (int a = 0; a < 3; ++a) {
+            if (a >= dims) { c[a][0] = c[a][1] = 0; continue; }
+            if (x[a] < o.lo[a] - tol || x[a] > o.hi[a] + tol) return false;
+            const double h = (o.hi[a] - o.lo[a]) / o.mask_n[a];
+            const double u = (x[a] - o.lo[a]) / h, t = tol / h;
+            c[a][0] = std::max(0, (int)std::floor(u - t));
+            c[a][1] = std::min(o.mask_n[a] - 1, (int)std::floor(u + t));
+        }
+        for (int k = c[2][0]; k <= c[2][1]; ++k)
+            for (int j = c[1][0]; j <= c[1][1]; ++j)
+                for (int i = c[0][0]; i <= c[0][1]; ++i)
+                    if (o.mask[((size_t)k * o.mask_n[1] + j) * o.mask_n[0] + i]) return true;
+        return false;
+    }
     double r2 = 0;
     for (int a = 0; a < dims; ++a) r2 += (x[a] - o.center[a]) * (x[a] - o.center[a]);
     return r2 <= (o.radius + tol) * (o.radius + tol);
@@ -423,7 +441,20 @@ int build_plan(const casimir_problem *pin, PlanData *P, std::string *err)
     P->dx = 1.0 / p.resolution;
     P->dt = p.courant * P->dx;
     for (auto &o : P->objects) {
-        if (o.kind < 0 || o.kind > 3 || o.shape < 0 || o.shape > 1) { *err = "object kind/shape"; return CASIMIR_EINVAL; }
+        if (o.kind < 0 || o.kind > 3 || o.shape < 0 || o.shape > 2) { *err = "object kind/shape"; return CASIMIR_EINVAL; }
+        if (o.shape == CASIMIR_SHAPE_GRID) {
+            if (!o.mask) { *err = "grid object without a mask"; return CASIMIR_EINVAL; }
+            for (int a = 0; a < 3; ++a)
+                if (o.mask_n[a] < 1 || (a < p.dims && !(o.hi[a] > o.lo[a])) || (a >= p.dims && o.mask_n[a] != 1)) {
+                    *err = "grid object: mask_n >= 1 and hi > lo on every used axis (mask_n[2] == 1 in 2D)";
+                    return CASIMIR_EINVAL;
+                }
+            // the plan keeps its own copy of the mask
+            P->masks.emplace_back(o.mask, o.mask + (size_t)o.mask_n[0] * o.mask_n[1] * o.mask_n[2]);
+            o.mask = P->masks.back().data();
+        } else {
+            o.mask = nullptr;
+        }
         if (o.kind == CASIMIR_MAT_DIELECTRIC && !(o.eps > 0 && o.mu > 0)) { *err = "dielectric eps, mu must be > 0"; return CASIMIR_EINVAL; }
         if (o.kind == CASIMIR_MAT_LORENTZ) {
             if (!(o.eps_inf > 0)) { *err = "lorentz eps_inf must be > 0"; return CASIMIR_EINVAL; }

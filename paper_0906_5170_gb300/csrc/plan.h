@@ -1,6 +1,7 @@
 // Internal plan representation shared by the host planner and the executor.
 #pragma once
 #include <cstdint>
+#include <deque>
 #include <string>
 #include <vector>
 
@@ -70,8 +71,12 @@ struct Sim {
 };
 
 struct PlanData {
+    PlanData() = default;
+    PlanData(const PlanData &) = delete;              // objects point into `masks`
+    PlanData &operator=(const PlanData &) = delete;
     casimir_problem prob{};
     std::vector<casimir_object> objects;
+    std::deque<std::vector<uint8_t>> masks;   // copies of the grid objects' masks (stable addresses)
     std::vector<casimir_face> faces;
     std::vector<casimir_kpoint> kpoints;
     double dx = 0, dt = 0;

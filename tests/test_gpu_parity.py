@@ -181,6 +181,21 @@ def test_plan_teardown_overlapping_graph_capture(ctx, pk):
     prev.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_voxel_mask_objects(ctx, prec):
+    """Arbitrary geometry as voxel masks: an L-shaped PEC block (voxels on the Yee lattice) and a
+    seeded random dielectric pattern of 0.07-wide voxels in the gap (sites anywhere in a voxel,
+    some on voxel faces); the planner's mask rasterisation against the oracle's."""
+    p = W.piston_small(n_steps=400, precision=prec, g_variant="plain")   # plain g: any medium
+    m = np.zeros((10, 10), np.uint8)
+    m[:, :5] = 1
+    m[:5, 5:] = 1
+    r = (np.random.default_rng(3).random((10, 7)) < 0.4).astype(np.uint8)
+    p["objects"] = [p["objects"][0], W.grid_object(m, [3.5, 0.5], [4.5, 1.5], kind="pec"),
+                    W.grid_object(r, [2.6, 0.75], [3.3, 1.24], kind="dielectric", eps=2.5, mu=1.0)]
+    _check(ctx, p, ("mask", prec), prec == "fp64")
+
+
 def test_budget_rejects_oversized_plan(pk):
     c = pk.Context(0, hbm_budget_bytes=1 << 20)
     with pytest.raises(pk.CasimirError) as e:

@@ -59,6 +59,15 @@ def box_faces(lo, hi, dims):
     return faces
 
 
+def grid_object(mask, lo, hi, **material):
+    """An arbitrary shape as a voxel mask over the box [lo, hi]: mask[i, j] (2D) or mask[i, j, k]
+    (3D), non-zero where the voxel belongs to the object; `material` as for any object
+    (kind="pec", or kind="dielectric", eps=..., and so on)."""
+    lo = [float(v) for v in lo] + [0.0] * (3 - len(lo))
+    hi = [float(v) for v in hi] + [0.0] * (3 - len(hi))
+    return dict(shape="grid", lo=lo, hi=hi, mask=np.asarray(mask, dtype=np.uint8), **material)
+
+
 def _base(dims, n, resolution, n_steps, sigma=1.0, courant=0.5):
     return {
         "dims": dims, "n": list(n), "resolution": float(resolution),
