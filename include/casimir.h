@@ -224,6 +224,20 @@ int casimir_ctx_kernel_stats(casimir_ctx_t *ctx, double *step_ms, int64_t *launc
 int casimir_plan(casimir_ctx_t *ctx, const casimir_problem *problem, casimir_plan_t **out);
 int casimir_plan_get_info(const casimir_plan_t *plan, casimir_plan_info *info);
 
+/* Introspection of the rasterised geometry (step a0 of the method, Sec. III): for k-point
+ * `kpoint` and the field array storing component `comp` (0..2) of E (field 0) or H
+ * (field 1), out[(k * n[1] + j) * n[0] + i] receives the coefficient at that array's
+ * site of cell (i, j, k): 1/eps (E; 1/eps_inf in a Lorentz medium) or 1/mu (H), and 0
+ * where the site is masked (E on PEC, on a closed wall or, in cylindrical runs, on the
+ * axis where the component vanishes; H on PMC or the axis).  off[3] receives the site's
+ * position within the cell in units of Delta ((i + off[0]) Delta, ...); the TE family of
+ * two-dimensional runs lives on the lattice shifted by half a cell, so its offsets differ
+ * from the standard Yee ones.  `out` holds n[0] n[1] n[2] doubles; works on host-only
+ * plans.  CASIMIR_EINVAL if the plan's polarisation has no such array or kpoint is out of
+ * range. */
+int casimir_plan_site_coefs(const casimir_plan_t *plan, int kpoint, int field, int comp,
+                            double off[3], double *out);
+
 /* Execution options of a plan (how the leapfrog of Sec. III A is scheduled; the computed
  * force does not depend on them beyond rounding).  0 in a field selects the default. */
 typedef struct {

@@ -117,6 +117,8 @@ SIGNATURES = {
                                                 ctypes.c_int]),
     "casimir_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_void_p)]),
     "casimir_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
+    "casimir_plan_site_coefs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "casimir_plan_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.POINTER(PlanOptions),
                                        ctypes.POINTER(ctypes.c_void_p)]),
     "casimir_plan_get_options": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanOptions)]),
@@ -316,6 +318,17 @@ class Plan:
         i = PlanInfo()
         check(lib().casimir_plan_get_info(self.h, ctypes.byref(i)))
         return {f: getattr(i, f) for f, _ in PlanInfo._fields_}
+
+    def site_coefs(self, kpoint, field, comp):
+        """The rasterised coefficient (1/eps or 1/mu, 0 where masked) of the array storing
+        component `comp` of E (field 0) or H (field 1) at k-point `kpoint`, as an array
+        indexed [i, j, k], and the sites' offsets within a cell (in cells)."""
+        nx, ny, nz = (int(v) for v in self.problem["n"])
+        out = np.zeros(nx * ny * nz)
+        off = (ctypes.c_double * 3)()
+        check(lib().casimir_plan_site_coefs(self.h, int(kpoint), int(field), int(comp), off,
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out.reshape(nz, ny, nx).transpose(2, 1, 0), tuple(off)
 
     def sims(self):
         n = self.info()["n_sims"]

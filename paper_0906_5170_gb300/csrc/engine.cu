@@ -1381,6 +1381,25 @@ int casimir_ctx_set_autotune(casimir_ctx_t *c, int on)
     return CASIMIR_OK;
 }
 
+int casimir_plan_site_coefs(const casimir_plan_t *P, int kpoint, int field, int comp, double off[3], double *out)
+{
+    if (!P || !off || !out) return fail(CASIMIR_EINVAL, "NULL argument");
+    const PlanData &D = P->data;
+    if (kpoint < 0 || kpoint >= D.prob.n_kpoints) return fail(CASIMIR_EINVAL, "kpoint out of range");
+    for (const Geo &g : D.geos) {
+        if (g.kpt != kpoint) continue;
+        ArraySpec arrs[6];
+        const int narr = family_arrays(g.family, arrs);
+        for (int a = 0; a < narr; ++a) {
+            if (arrs[a].field != field || arrs[a].comp != comp) continue;
+            for (int q = 0; q < 3; ++q) off[q] = arrs[a].off[q];
+            for (size_t c = 0; c < g.mat.size(); ++c) out[c] = g.table[(size_t)g.mat[c] * narr + a];
+            return CASIMIR_OK;
+        }
+    }
+    return fail(CASIMIR_EINVAL, "no such field array in this plan");
+}
+
 int casimir_plan_get_info(const casimir_plan_t *P, casimir_plan_info *info)
 {
     if (!P || !info) return fail(CASIMIR_EINVAL, "NULL argument");

@@ -1,0 +1,81 @@
+"""The planner's rasterisation (step a0: materials, PEC/PMC masks, closed walls, cylindrical
+axis masks, Lorentz eps_inf) against the oracle's own lattice, site by site, bit for bit.
+
+casimir_plan_site_coefs returns, for one field array of a host-only plan, the coefficient the
+step kernels read at every site (1/eps or 1/mu, 0 where masked); the oracle's lattice set-up
+holds the same coefficients for its leapfrog.  The TE family of two-dimensional runs sits on
+the lattice shifted by half a cell, so its arrays are compared after the integer shift between
+the two site positions (periodic in the canonical cell).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_0906_5170_gb300 as pk
+import workloads as W
+
+
+def _mask_problem():
+    p = W.piston_small(n_steps=50, precision="fp64", g_variant="plain")
+    m = np.zeros((10, 10), np.uint8)
+    m[:, :5] = 1
+    m[:5, 5:] = 1
+    r = (np.random.default_rng(3).random((10, 7)) < 0.4).astype(np.uint8)
+    p["objects"] = [p["objects"][0], W.grid_object(m, [3.5, 0.5], [4.5, 1.5], kind="pec"),
+                    W.grid_object(r, [2.6, 0.75], [3.3, 1.24], kind="dielectric", eps=2.5, mu=1.0)]
+    return p
+
+
+def _pmc_problem():
+    p = W.piston_small(n_steps=50, precision="fp64")
+    p["objects"].append({"shape": "box", "lo": [0.0, 0.0, 0], "hi": [0.3, 2.0, 0], "kind": "pmc"})
+    p["objects"].append({"shape": "sphere", "center": [3.0, 1.0, 0], "radius": 0.3, "kind": "dielectric",
+                         "eps": 4.0, "mu": 2.0})
+    return p
+
+
+PROBLEMS = {
+    "piston_te_tm": lambda: W.piston_small(n_steps=50),
+    "pmc_and_disk": _pmc_problem,
+    "voxel_masks": _mask_problem,
+    "plates_filled": lambda: W.plates_box_2d(10, 1.0, polarization="TE+TM", n_steps=50, fill_eps=2.0),
+    "waveguides_kz": lambda: W.config3_waveguides(0.5, resolution=8, n_cells=48, pml_units=0.75, n_harm=2,
+                                                  n_steps=50, k_points=[{"k": [0, 0, 1.3], "weight": 1.0}]),
+    "grating_silica": lambda: W.grating_silica(0.5, nk_x=2, nk_z=1, n_harm=2, t_max=1.0),
+    "sphere_3d": lambda: W.config4_sphere_notch(0.55, n_cells=24, pml_cells=4, resolution=16),
+    "cylinder": lambda: W.cylinder_piston(12, (0, 1, 2)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PROBLEMS))
+def test_site_coefficients_match_the_oracle(name):
+    p = PROBLEMS[name]()
+    plan = pk.Plan(p)
+    nx, ny, nz = p["n"]
+    checked = 0
+    for k, kp in enumerate(p["k_points"]):
+        st = oracle.grid_setup(p, kp["k"], kp.get("m", 0))
+        for field, offs, ref in ((0, oracle.E_OFF, st.ce), (1, oracle.H_OFF, st.ch)):
+            for c in range(3):
+                try:
+                    got, off = plan.site_coefs(k, field, c)
+                except pk.CasimirError:
+                    continue                      # this polarisation has no such array
+                want = np.asarray(ref[c]).reshape(nz, ny, nx).transpose(2, 1, 0)
+                shift = [off[a] - offs[c][a] for a in range(3)]
+                for a in range(p["dims"]):
+                    assert shift[a] == round(shift[a]), (name, field, c, off)
+                    want = np.roll(want, -int(round(shift[a])), axis=a)
+                assert np.array_equal(got, want), (name, k, field, c, np.argwhere(got != want)[:5])
+                checked += 1
+    assert checked >= (6 if p["polarization"] in ("TE+TM", "full") else 3) * len(p["k_points"])
+
+
+def test_site_coefficients_reject_absent_arrays():
+    plan = pk.Plan(W.plates_box_2d(10, 1.0, polarization="TM", n_steps=50))
+    with pytest.raises(pk.CasimirError):
+        plan.site_coefs(0, 1, 2)                  # no H_z in a TM run
+    with pytest.raises(pk.CasimirError):
+        plan.site_coefs(1, 0, 2)                  # one k-point only
+    got, off = plan.site_coefs(0, 0, 2)
+    assert off == (0.0, 0.0, 0.5) and got.shape == (10, 20, 1)
