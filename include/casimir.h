@@ -301,6 +301,19 @@ int casimir_run_plain(casimir_plan_t *plan, double F[3], double *per_sim, casimi
  * source component. */
 int casimir_plan_sims(const casimir_plan_t *plan, int32_t *desc, int64_t n);
 
+/* Introspection of simulation `sim` (plan order) of a plan, steps a2 and a8 of the method
+ * (Sec. II, Eqs. (3)-(6); Sec. III A): which = 0 gives its source, the stored field values
+ * right after the impulse (E = D/eps or H = B/mu at each site, masked sites dropped to 0);
+ * which = 1 its measurement functional, s(n) = sum_e weight_e * field_e (the stress-tensor
+ * projection of the harmonic f_n with dA and eps_S or mu_S).  Entry e: comp[e] = 3 * field +
+ * component (field 0 E, 1 H), idx[e] = the site's cell index (k * n[1] + j) * n[0] + i on
+ * that array's lattice (casimir_plan_site_coefs gives the offsets), val[2e], val[2e + 1] =
+ * real and imaginary part, with the sign of the stored array (the TE family stores -E).
+ * Returns the number of entries (writes at most cap of them; cap 0 only counts), or
+ * CASIMIR_EINVAL for a bad simulation index, `which` or buffer.  Works on host-only plans. */
+int64_t casimir_plan_sim_entries(const casimir_plan_t *plan, int64_t sim, int which, int32_t *comp,
+                                 int64_t *idx, double *val, int64_t cap);
+
 /* The time weights w_n = 2 Delta_t Im g(-n Delta_t), n = 1..n_steps, of Eq. (1)
  * (rectangle rule); w must hold n_steps doubles. */
 int casimir_plan_weights(const casimir_plan_t *plan, double *w, int64_t n);

@@ -117,6 +117,9 @@ SIGNATURES = {
                                                 ctypes.c_int]),
     "casimir_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.POINTER(ctypes.c_void_p)]),
     "casimir_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]),
+    "casimir_plan_sim_entries": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                                 ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
     "casimir_plan_site_coefs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "casimir_plan_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.POINTER(PlanOptions),
@@ -329,6 +332,20 @@ class Plan:
         check(lib().casimir_plan_site_coefs(self.h, int(kpoint), int(field), int(comp), off,
                                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out.reshape(nz, ny, nx).transpose(2, 1, 0), tuple(off)
+
+    def sim_entries(self, sim, which):
+        """Source (which 0) or measurement (which 1) entries of simulation `sim`: arrays of
+        3 * field + component, cell index on that array's lattice, and complex value."""
+        L = lib()
+        n = check(L.casimir_plan_sim_entries(self.h, int(sim), int(which), None, None, None, 0))
+        comp = np.zeros(n, np.int32)
+        idx = np.zeros(n, np.int64)
+        val = np.zeros(2 * n)
+        check(L.casimir_plan_sim_entries(self.h, int(sim), int(which),
+                                         comp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                         idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         val.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n))
+        return comp, idx, val[0::2] + 1j * val[1::2]
 
     def sims(self):
         n = self.info()["n_sims"]

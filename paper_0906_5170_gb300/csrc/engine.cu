@@ -1439,6 +1439,25 @@ int casimir_plan_sims(const casimir_plan_t *P, int32_t *desc, int64_t n)
     return CASIMIR_OK;
 }
 
+int64_t casimir_plan_sim_entries(const casimir_plan_t *P, int64_t sim, int which, int32_t *comp, int64_t *idx,
+                                 double *val, int64_t cap)
+{
+    if (!P || sim < 0 || sim >= (int64_t)P->data.sims.size() || (which != 0 && which != 1) || cap < 0 ||
+        (cap > 0 && (!comp || !idx || !val)))
+        return fail(CASIMIR_EINVAL, "simulation index, which or buffers");
+    const Sim &m = P->data.sims[sim];
+    ArraySpec arrs[6];
+    family_arrays(m.family, arrs);
+    const std::vector<Entry> &v = which == 0 ? m.src : m.meas;
+    for (size_t e = 0; e < v.size() && (int64_t)e < cap; ++e) {
+        comp[e] = 3 * arrs[v[e].arr].field + arrs[v[e].arr].comp;
+        idx[e] = v[e].idx;
+        val[2 * e] = v[e].re;
+        val[2 * e + 1] = v[e].im;
+    }
+    return (int64_t)v.size();
+}
+
 int casimir_plan_weights(const casimir_plan_t *P, double *w, int64_t n)
 {
     if (!P || !w || n < (int64_t)P->data.gw.size()) return fail(CASIMIR_EINVAL, "w too small");

@@ -79,3 +79,58 @@ def test_site_coefficients_reject_absent_arrays():
         plan.site_coefs(1, 0, 2)                  # one k-point only
     got, off = plan.site_coefs(0, 0, 2)
     assert off == (0.0, 0.0, 0.5) and got.shape == (10, 20, 1)
+
+
+def _shift(plan, field, c, dims):
+    """Integer site shift of the planner's array against the standard Yee site of (field, c)."""
+    _, off = plan.site_coefs(0, field, c)
+    std = (oracle.H_OFF if field else oracle.E_OFF)[c]
+    return [int(round(off[a] - std[a])) if a < dims else 0 for a in range(3)]
+
+
+@pytest.mark.parametrize("name", sorted(PROBLEMS))
+def test_sources_and_measurements_match_the_oracle(name):
+    # steps a2 and a8: the impulse source (stored as E = D/eps or H = B/mu, masked) and the
+    # stress-tensor measurement functional of every simulation, entry by entry
+    from oracle.casimir_oracle import _sim_vectors
+    p = PROBLEMS[name]()
+    plan = pk.Plan(p)
+    nx, ny, nz = p["n"]
+    dims = p["dims"]
+    sims = oracle.enumerate_sims(p)
+    setups = [oracle.grid_setup(p, kp["k"], kp.get("m", 0)) for kp in p["k_points"]]
+    te = p["polarization"] == "TE+TM"
+    step = max(1, len(sims) // 40)
+    for s in range(0, len(sims), step):
+        sim = sims[s]
+        st = setups[sim["k"]]
+        src_o, meas_o = _sim_vectors(p, st, sim)
+
+        def to_oracle(field, c, idx):
+            sh = _shift(plan, field, c, dims)
+            i, j, k = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+            return (((k + sh[2]) % nz) * ny + (j + sh[1]) % ny) * nx + (i + sh[0]) % nx
+
+        def sign(field, c):
+            return -1.0 if te and sim["pol"] == "TE" and field == 0 else 1.0
+
+        field = 1 if sim["kind"] == "K" else 0
+        c = sim["comp"]
+        coef = (st.ch if field else st.ce)[c]
+        comp, idx, val = plan.sim_entries(s, 0)
+        assert np.all(comp == 3 * field + c)
+        got = {to_oracle(field, c, int(q)): v * sign(field, c) for q, v in zip(idx, val)}
+        want = {q: v * coef[q] for q, v in src_o.items()}
+        assert set(got) == set(want), (name, s)
+        scale = max(abs(v) for v in want.values())
+        assert max(abs(got[q] - want[q]) for q in want) <= 1e-13 * scale, (name, s)
+
+        comp, idx, val = plan.sim_entries(s, 1)
+        got = {}
+        for cc, q, v in zip(comp, idx, val):
+            fq, cq = divmod(int(cc), 3)
+            assert fq == field
+            got[(cq, to_oracle(fq, cq, int(q)))] = v * sign(fq, cq)
+        assert set(got) == set(meas_o), (name, s)
+        scale = max(abs(v) for v in meas_o.values())
+        assert max(abs(got[q] - meas_o[q]) for q in meas_o) <= 1e-13 * scale, (name, s)
