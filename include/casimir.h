@@ -238,6 +238,15 @@ int casimir_plan_get_info(const casimir_plan_t *plan, casimir_plan_info *info);
 int casimir_plan_site_coefs(const casimir_plan_t *plan, int kpoint, int field, int comp,
                             double off[3], double *out);
 
+/* Introspection of the rasterised Lorentz media (Eq. (9), the silica model of Sec. III D):
+ * for k-point `kpoint`, E component `comp` and pole slot `pole` (0 .. CASIMIR_MAX_POLES - 1),
+ * de[cell] and w0[cell] receive that slot's strength and frequency at the component's site of
+ * every cell (same indexing as casimir_plan_site_coefs).  The poles present at a site fill
+ * the first slots; empty slots and masked sites (PEC, closed walls) hold 0.  Six-component
+ * plans only (CASIMIR_EINVAL otherwise, or for an index out of range). */
+int casimir_plan_site_poles(const casimir_plan_t *plan, int kpoint, int comp, int pole,
+                            double *de, double *w0);
+
 /* Execution options of a plan (how the leapfrog of Sec. III A is scheduled; the computed
  * force does not depend on them beyond rounding).  0 in a field selects the default. */
 typedef struct {

@@ -120,6 +120,8 @@ SIGNATURES = {
     "casimir_plan_sim_entries": (ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
+    "casimir_plan_site_poles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "casimir_plan_site_coefs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "casimir_plan_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.POINTER(PlanOptions),
@@ -332,6 +334,16 @@ class Plan:
         check(lib().casimir_plan_site_coefs(self.h, int(kpoint), int(field), int(comp), off,
                                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out.reshape(nz, ny, nx).transpose(2, 1, 0), tuple(off)
+
+    def site_poles(self, kpoint, comp, pole):
+        """Strength and frequency of Lorentz pole slot `pole` at the sites of E component
+        `comp` (arrays indexed [i, j, k]; present poles fill the first slots, 0 elsewhere)."""
+        nx, ny, nz = (int(v) for v in self.problem["n"])
+        de, w0 = np.zeros(nx * ny * nz), np.zeros(nx * ny * nz)
+        check(lib().casimir_plan_site_poles(self.h, int(kpoint), int(comp), int(pole),
+                                            de.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            w0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return (de.reshape(nz, ny, nx).transpose(2, 1, 0), w0.reshape(nz, ny, nx).transpose(2, 1, 0))
 
     def sim_entries(self, sim, which):
         """Source (which 0) or measurement (which 1) entries of simulation `sim`: arrays of

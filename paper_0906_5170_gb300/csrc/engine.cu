@@ -1381,6 +1381,27 @@ int casimir_ctx_set_autotune(casimir_ctx_t *c, int on)
     return CASIMIR_OK;
 }
 
+int casimir_plan_site_poles(const casimir_plan_t *P, int kpoint, int comp, int pole, double *de, double *w0)
+{
+    if (!P || !de || !w0) return fail(CASIMIR_EINVAL, "NULL argument");
+    const PlanData &D = P->data;
+    if (kpoint < 0 || kpoint >= D.prob.n_kpoints || comp < 0 || comp > 2 || pole < 0 || pole >= CASIMIR_MAX_POLES)
+        return fail(CASIMIR_EINVAL, "kpoint, comp or pole out of range");
+    for (const Geo &g : D.geos) {
+        if (g.kpt != kpoint || g.family != FAM_FULL) continue;
+        for (size_t c = 0; c < g.mat.size(); ++c) {
+            de[c] = w0[c] = 0.0;
+            if (pole < g.npoles) {
+                const size_t at = ((size_t)g.mat[c] * g.npoles + pole) * 6 + 2 * comp;
+                de[c] = g.lorentz[at];
+                w0[c] = g.lorentz[at + 1];
+            }
+        }
+        return CASIMIR_OK;
+    }
+    return fail(CASIMIR_EINVAL, "Lorentz tables exist for six-component plans only");
+}
+
 int casimir_plan_site_coefs(const casimir_plan_t *P, int kpoint, int field, int comp, double off[3], double *out)
 {
     if (!P || !off || !out) return fail(CASIMIR_EINVAL, "NULL argument");

@@ -5,7 +5,9 @@ casimir_plan_site_coefs returns, for one field array of a host-only plan, the co
 step kernels read at every site (1/eps or 1/mu, 0 where masked); the oracle's lattice set-up
 holds the same coefficients for its leapfrog.  The TE family of two-dimensional runs sits on
 the lattice shifted by half a cell, so its arrays are compared after the integer shift between
-the two site positions (periodic in the canonical cell).
+the two site positions (periodic in the canonical cell).  casimir_plan_sim_entries and
+casimir_plan_site_poles extend the same check to every simulation's source and measurement
+entries (steps a2, a8) and to the per-site Lorentz pole tables.
 """
 import numpy as np
 import pytest
@@ -134,3 +136,43 @@ def test_sources_and_measurements_match_the_oracle(name):
         assert set(got) == set(meas_o), (name, s)
         scale = max(abs(v) for v in meas_o.values())
         assert max(abs(got[q] - meas_o[q]) for q in meas_o) <= 1e-13 * scale, (name, s)
+
+
+def _poles_problem():
+    # a three-pole slab written with an empty first pole, a one-pole block inside it, a PEC
+    # box cutting both, CPML around: packing, overrides and masks of the pole tables
+    p = W.config3_waveguides(0.5, resolution=8, n_cells=48, pml_units=0.75, n_harm=2, n_steps=50,
+                             k_points=[{"k": [0, 0, 0.7], "weight": 1.0}])
+    p["objects"] = [
+        {"shape": "box", "lo": [1.0, 1.0, 0], "hi": [5.0, 3.0, 0], "kind": "lorentz", "eps_inf": 1.5,
+         "delta_eps": [0.0, 0.8, 1.1, ], "omega0": [2.0, 1.5, 3.0]},
+        {"shape": "box", "lo": [2.0, 1.5, 0], "hi": [3.0, 2.5, 0], "kind": "lorentz", "eps_inf": 2.0,
+         "delta_eps": 3.0, "omega0": 2.5},
+        {"shape": "box", "lo": [3.5, 1.25, 0], "hi": [4.0, 2.75, 0], "kind": "pec"},
+    ]
+    return p
+
+
+@pytest.mark.parametrize("name", ["waveguides_kz", "grating_silica", "poles"])
+def test_site_poles_match_the_oracle(name):
+    # the (delta_eps, omega0) pairs present at every E site, as sets (the planner packs the
+    # present poles first; the oracle keeps each pole at the index it was given)
+    p = _poles_problem() if name == "poles" else PROBLEMS[name]()
+    plan = pk.Plan(p)
+    nx, ny, nz = p["n"]
+    for k, kp in enumerate(p["k_points"]):
+        st = oracle.grid_setup(p, kp["k"], kp.get("m", 0))
+        for c in range(3):
+            got = np.stack([np.stack(plan.site_poles(k, c, q), -1) for q in range(oracle.MAX_POLES)], -2)
+            want = np.zeros_like(got)
+            for q in range(len(st.lde[c])):
+                de = np.asarray(st.lde[c][q]).reshape(nz, ny, nx).transpose(2, 1, 0)
+                w0 = np.asarray(st.lw0[c][q]).reshape(nz, ny, nx).transpose(2, 1, 0)
+                want[..., q, 0] = de
+                want[..., q, 1] = np.where(de != 0.0, w0, 0.0)
+            key = lambda a: np.sort(a[..., 0] + 1j * a[..., 1], axis=-1)
+            assert np.array_equal(key(got), key(want)), (name, k, c)
+            assert np.any(got[..., 0] != 0.0)
+    if name == "poles":
+        de0, _ = plan.site_poles(0, 2, 0)
+        assert np.count_nonzero(np.unique(de0)) == 2           # 0.8 (packed first) and 3.0
