@@ -2,6 +2,7 @@
 function include/casimir.h declares, and its planner agrees with the oracle on
 the simulation list and on the time weights of Eq. (1)."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -237,3 +238,27 @@ def test_serving_mix_is_stable(scale):
         q = dict(wg, n_steps=2000, k_points=[kp])
         s = np.abs(oracle.run_sim(q, oracle.enumerate_sims(q)[0], oracle.grid_setup(q, kp["k"])))
         assert np.all(np.isfinite(s)) and s[-200:].max() < s[:200].max()
+
+
+def test_header_is_plain_c(tmp_path):
+    # the boundary is a C ABI: its header compiles as C99 with every warning on, and the
+    # structs a C caller fills have the sizes the binding marshals
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "c.c"
+    src.write_text('#include <stdio.h>\n#include "casimir.h"\n'
+                   'int main(void) { printf("%zu %zu %zu %zu\\n", sizeof(casimir_object), sizeof(casimir_face),'
+                   ' sizeof(casimir_kpoint), sizeof(casimir_problem));\n'
+                   '  printf("%zu %zu %zu\\n", sizeof(casimir_plan_info), sizeof(casimir_plan_options), sizeof(casimir_stats));'
+                   ' return 0; }\n')
+    exe = tmp_path / "c"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, str(src), "-o", str(exe)],
+                   check=True)
+    sizes = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    from paper_0906_5170_gb300 import capi
+    assert sizes == [ctypes.sizeof(capi.Object), ctypes.sizeof(capi.Face), ctypes.sizeof(capi.KPoint),
+                     ctypes.sizeof(capi.Problem), ctypes.sizeof(capi.PlanInfo), ctypes.sizeof(capi.PlanOptions),
+                     ctypes.sizeof(capi.Stats)]
