@@ -247,6 +247,15 @@ int casimir_plan_site_coefs(const casimir_plan_t *plan, int kpoint, int field, i
 int casimir_plan_site_poles(const casimir_plan_t *plan, int kpoint, int comp, int pole,
                             double *de, double *w0);
 
+/* Introspection of the CPML coefficients (Sec. III B; polynomial grading of order 3,
+ * reflection 1e-8, kappa = 1, frequency shift falling linearly from 0.05 to 0 at the wall):
+ * for PML axis `axis` and sites on integer (half = 0) or half-integer (half = 1) positions
+ * along it, b[i], c[i] and inv_kappa[i] for i < n[axis], in the update psi <- b psi + c dF
+ * and the stretched derivative inv_kappa dF + psi.  CASIMIR_EINVAL if the axis is not a PML
+ * axis of the plan. */
+int casimir_plan_pml(const casimir_plan_t *plan, int axis, int half, double *b, double *c,
+                     double *inv_kappa);
+
 /* Execution options of a plan (how the leapfrog of Sec. III A is scheduled; the computed
  * force does not depend on them beyond rounding).  0 in a field selects the default. */
 typedef struct {

@@ -122,6 +122,8 @@ SIGNATURES = {
                                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
     "casimir_plan_site_poles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "casimir_plan_pml": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "casimir_plan_site_coefs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "casimir_plan_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Problem), ctypes.POINTER(PlanOptions),
@@ -334,6 +336,15 @@ class Plan:
         check(lib().casimir_plan_site_coefs(self.h, int(kpoint), int(field), int(comp), off,
                                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return out.reshape(nz, ny, nx).transpose(2, 1, 0), tuple(off)
+
+    def pml(self, axis, half):
+        """CPML b, c, 1/kappa along PML axis `axis` at integer (half 0) or half-integer sites."""
+        n = int(self.problem["n"][axis]) if 0 <= axis < 3 else 1   # the library rejects a bad axis
+        b, c, ik = np.zeros(n), np.zeros(n), np.zeros(n)
+        P = ctypes.POINTER(ctypes.c_double)
+        check(lib().casimir_plan_pml(self.h, int(axis), int(half), b.ctypes.data_as(P), c.ctypes.data_as(P),
+                                     ik.ctypes.data_as(P)))
+        return b, c, ik
 
     def site_poles(self, kpoint, comp, pole):
         """Strength and frequency of Lorentz pole slot `pole` at the sites of E component

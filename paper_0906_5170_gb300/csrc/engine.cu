@@ -1381,6 +1381,18 @@ int casimir_ctx_set_autotune(casimir_ctx_t *c, int on)
     return CASIMIR_OK;
 }
 
+int casimir_plan_pml(const casimir_plan_t *P, int axis, int half, double *b, double *c, double *inv_kappa)
+{
+    if (!P || !b || !c || !inv_kappa || axis < 0 || axis > 2 || half < 0 || half > 1)
+        return fail(CASIMIR_EINVAL, "NULL argument, axis or half");
+    if (P->data.geos.empty() || !P->data.geos[0].has_pml[axis]) return fail(CASIMIR_EINVAL, "not a PML axis of this plan");
+    const auto &pr = P->data.geos[0].pml[axis][half];
+    std::copy(pr[0].begin(), pr[0].end(), b);
+    std::copy(pr[1].begin(), pr[1].end(), c);
+    std::copy(pr[2].begin(), pr[2].end(), inv_kappa);
+    return CASIMIR_OK;
+}
+
 int casimir_plan_site_poles(const casimir_plan_t *P, int kpoint, int comp, int pole, double *de, double *w0)
 {
     if (!P || !de || !w0) return fail(CASIMIR_EINVAL, "NULL argument");

@@ -176,3 +176,29 @@ def test_site_poles_match_the_oracle(name):
     if name == "poles":
         de0, _ = plan.site_poles(0, 2, 0)
         assert np.count_nonzero(np.unique(de0)) == 2           # 0.8 (packed first) and 3.0
+
+
+@pytest.mark.parametrize("name", ["waveguides_kz", "grating_silica", "sphere_3d"])
+def test_pml_profiles_match_the_oracle(name):
+    # step a5: the CPML coefficients of every PML axis, integer and half-integer sites
+    from oracle.casimir_oracle import _pml_profile
+    p = PROBLEMS[name]()
+    plan = pk.Plan(p)
+    dt = p["courant"] / p["resolution"]
+    axes = [a for a in range(p["dims"]) if p["bc"][a] == "pml"]
+    assert axes
+    for a in axes:
+        for half in (0, 1):
+            got = plan.pml(a, half)
+            want = _pml_profile(p["n"][a], p["pml_cells"][a], p["resolution"], dt, half)
+            # b and 1/kappa to rounding; c = s/(s k + k^2 a) (b - 1) inherits the rounding of b
+            # (the two sides' exp may differ by an ulp) amplified by the cancellation in b - 1
+            assert np.allclose(got[0], want[0], rtol=1e-15, atol=0), (name, a, half)
+            assert np.array_equal(got[2], want[2]), (name, a, half)
+            bm1 = np.where(want[0] != 1.0, want[0] - 1.0, 1.0)
+            tol = 1e-14 * np.abs(want[1]) + 4e-16 * np.abs(want[1] / bm1)
+            assert np.all(np.abs(got[1] - want[1]) <= tol), (name, a, half)
+            assert np.any(got[1] != 0) and np.all(got[0] <= 1)
+    for a in [a for a in range(3) if a not in axes] + [3]:
+        with pytest.raises(pk.CasimirError):
+            plan.pml(a, 0)                        # not a PML axis (or no axis at all)
