@@ -14,6 +14,12 @@ import paper_0906_5170_gb300 as pk
 import workloads as W
 
 
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_0906_5170_gb300 import build as pkbuild
+    pkbuild.build()                  # the host planner of the C ABI (incremental)
+
+
 def _box_mask(box, vox, pad, dims):
     n = [int(round((box["hi"][a] - box["lo"][a]) / vox)) + 2 * pad for a in range(dims)]
     m = np.zeros(n, np.uint8)

@@ -17,6 +17,12 @@ import paper_0906_5170_gb300 as pk
 import workloads as W
 
 
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_0906_5170_gb300 import build as pkbuild
+    pkbuild.build()                  # the host planner of the C ABI (incremental)
+
+
 def _mask_problem():
     p = W.piston_small(n_steps=50, precision="fp64", g_variant="plain")
     m = np.zeros((10, 10), np.uint8)
