@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for f in CXX:
         o = os.path.join(OUT_DIR, f + ".o")
         objs.append(o)
-        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", *inc, "-I", "/usr/local/cuda/include",
+        jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", *inc, "-I", "/usr/local/cuda/include",
                      "-c", os.path.join(CSRC, f), "-o", o])
     procs = [subprocess.Popen(j, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for j in jobs]
     failed = []

@@ -9,6 +9,7 @@
 #include <map>
 #include <array>
 #include <complex>
+#include <thread>
 
 #include "plan.h"
 
@@ -257,64 +258,101 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err, 
     }
     int64_t ncell = (int64_t)p.n[0] * p.n[1] * p.n[2];
     g->mat.assign(ncell, 0);
-    std::map<std::vector<double>, int> ids;
     constexpr int NPK = 6 * CASIMIR_MAX_POLES;   // (delta_eps, omega0) per pole and E component
-    std::vector<double> key(narr + NPK), prev_key;
-    int prev_id = -1;
     double L[3] = {p.n[0] * P.dx, p.n[1] * P.dx, p.n[2] * P.dx};
-    for (int kk = 0; kk < p.n[2]; ++kk)
-        for (int j = 0; j < p.n[1]; ++j)
+    // key of cell (i, j, kk): every array's coefficient, then every E component's poles
+    auto cell_key = [&](int i, int j, int kk, std::vector<double> &key) {
+        std::fill(key.begin(), key.end(), 0.0);
+        for (int a = 0; a < narr; ++a) {
+            const ArraySpec &as = arrs[a];
+            double x[3] = {(i + as.off[0]) * P.dx, (j + as.off[1]) * P.dx, (kk + as.off[2]) * P.dx};
+            bool wall = false;
+            for (int ax = 0; ax < p.dims; ++ax) {
+                x[ax] = canon(x[ax], L[ax]);
+                if (cyl && ax == 0) continue;   // r = 0 is the axis, the wall r = R lies beyond the grid
+                if (as.field == 0 && (p.bc[ax] == CASIMIR_BC_PEC || p.bc[ax] == CASIMIR_BC_PML) &&
+                    std::fabs(x[ax]) < kTol * P.dx)
+                    wall = true;
+            }
+            // on the axis: E_phi and H_r carry no weight (r = 0); E_z ~ r^|m| vanishes for m != 0
+            bool axis_mask = cyl && i == 0 && as.off[0] == 0.0 &&
+                             ((as.field == 0 && as.comp == 2) || (as.field == 1 && as.comp == 0) ||
+                              (as.field == 0 && as.comp == 1 && g->mphi != 0));
+            Mat m = material_at(P, x);
+            double c;
+            if (axis_mask) {
+                c = 0.0;
+            } else if (as.field == 0) {
+                c = (m.pec || wall) ? 0.0 : 1.0 / m.eps;
+                if (!(m.pec || wall))
+                    for (int q = 0; q < CASIMIR_MAX_POLES && m.de[q] != 0.0; ++q) {
+                        key[narr + 6 * q + 2 * as.comp] = m.de[q];
+                        key[narr + 6 * q + 2 * as.comp + 1] = m.w0[q];
+                    }
+            } else {
+                c = m.pmc ? 0.0 : 1.0 / m.mu;
+            }
+            key[a] = c;
+        }
+    };
+    // Material ids in order of first occurrence in the scan (x fastest).  Ranges of rows are
+    // numbered in parallel, each in its own first-seen order; merging the ranges in scan order
+    // then gives every key the id a single pass would give it.
+    const int64_t rows = (int64_t)p.n[1] * p.n[2];
+    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    const int nchunk = (int)std::min<int64_t>(ncell >= (1 << 16) ? hw : 1, rows);
+    std::vector<std::vector<std::vector<double>>> chunk_keys(nchunk);
+    std::vector<char> overflow(nchunk, 0);
+    auto number_rows = [&](int s) {
+        std::map<std::vector<double>, int> local;
+        std::vector<double> key(narr + NPK), prev_key;
+        int prev_id = -1;
+        for (int64_t r = rows * s / nchunk; r < rows * (s + 1) / nchunk; ++r) {
+            const int kk = (int)(r / p.n[1]), j = (int)(r % p.n[1]);
             for (int i = 0; i < p.n[0]; ++i) {
-                std::fill(key.begin(), key.end(), 0.0);
-                for (int a = 0; a < narr; ++a) {
-                    const ArraySpec &as = arrs[a];
-                    double x[3] = {(i + as.off[0]) * P.dx, (j + as.off[1]) * P.dx, (kk + as.off[2]) * P.dx};
-                    bool wall = false;
-                    for (int ax = 0; ax < p.dims; ++ax) {
-                        x[ax] = canon(x[ax], L[ax]);
-                        if (cyl && ax == 0) continue;   // r = 0 is the axis, the wall r = R lies beyond the grid
-                        if (as.field == 0 && (p.bc[ax] == CASIMIR_BC_PEC || p.bc[ax] == CASIMIR_BC_PML) &&
-                            std::fabs(x[ax]) < kTol * P.dx)
-                            wall = true;
-                    }
-                    // on the axis: E_phi and H_r carry no weight (r = 0); E_z ~ r^|m| vanishes for m != 0
-                    bool axis_mask = cyl && i == 0 && as.off[0] == 0.0 &&
-                                     ((as.field == 0 && as.comp == 2) || (as.field == 1 && as.comp == 0) ||
-                                      (as.field == 0 && as.comp == 1 && g->mphi != 0));
-                    Mat m = material_at(P, x);
-                    double c;
-                    if (axis_mask) {
-                        c = 0.0;
-                    } else if (as.field == 0) {
-                        c = (m.pec || wall) ? 0.0 : 1.0 / m.eps;
-                        if (!(m.pec || wall))
-                            for (int q = 0; q < CASIMIR_MAX_POLES && m.de[q] != 0.0; ++q) {
-                                key[narr + 6 * q + 2 * as.comp] = m.de[q];
-                                key[narr + 6 * q + 2 * as.comp + 1] = m.w0[q];
-                            }
-                    } else {
-                        c = m.pmc ? 0.0 : 1.0 / m.mu;
-                    }
-                    key[a] = c;
-                }
+                cell_key(i, j, kk, key);
                 // neighbouring cells mostly share their key: try the previous cell's first
                 int id;
                 if (prev_id >= 0 && key == prev_key) {
                     id = prev_id;
                 } else {
-                    auto it = ids.find(key);
-                    if (it == ids.end()) {
-                        id = (int)ids.size();
-                        if (id > 255) { *err = "more than 256 distinct material sites"; return CASIMIR_EINVAL; }
-                        ids.emplace(key, id);
+                    auto it = local.find(key);
+                    if (it == local.end()) {
+                        id = (int)local.size();
+                        if (id > 255) { overflow[s] = 1; return; }   // the whole grid has more too
+                        local.emplace(key, id);
+                        chunk_keys[s].push_back(key);
                     } else {
                         id = it->second;
                     }
                     prev_key = key;
                     prev_id = id;
                 }
-                g->mat[((int64_t)kk * p.n[1] + j) * p.n[0] + i] = (uint8_t)id;
+                g->mat[r * p.n[0] + i] = (uint8_t)id;
             }
+        }
+    };
+    {
+        std::vector<std::thread> pool;
+        for (int s = 1; s < nchunk; ++s) pool.emplace_back(number_rows, s);
+        number_rows(0);
+        for (auto &t : pool) t.join();
+    }
+    std::map<std::vector<double>, int> ids;
+    for (int s = 0; s < nchunk; ++s) {
+        if (overflow[s]) { *err = "more than 256 distinct material sites"; return CASIMIR_EINVAL; }
+        uint8_t remap[256];
+        for (size_t q = 0; q < chunk_keys[s].size(); ++q) {
+            auto it = ids.find(chunk_keys[s][q]);
+            if (it == ids.end()) {
+                const int id = (int)ids.size();
+                if (id > 255) { *err = "more than 256 distinct material sites"; return CASIMIR_EINVAL; }
+                it = ids.emplace(chunk_keys[s][q], id).first;
+            }
+            remap[q] = (uint8_t)it->second;
+        }
+        for (int64_t c = rows * s / nchunk * p.n[0]; c < rows * (s + 1) / nchunk * p.n[0]; ++c) g->mat[c] = remap[g->mat[c]];
+    }
     g->nmat = (int)ids.size();
     g->table.assign((size_t)g->nmat * narr, 0.0);
     // poles in use: the highest pole present at any site
