@@ -262,3 +262,27 @@ def test_header_is_plain_c(tmp_path):
     assert sizes == [ctypes.sizeof(capi.Object), ctypes.sizeof(capi.Face), ctypes.sizeof(capi.KPoint),
                      ctypes.sizeof(capi.Problem), ctypes.sizeof(capi.PlanInfo), ctypes.sizeof(capi.PlanOptions),
                      ctypes.sizeof(capi.Stats)]
+
+
+@pytest.mark.parametrize("layout", ["rows", "columns"])
+def test_plan_rejects_more_than_256_materials(layout):
+    # material ids are bytes: 300 distinct dielectrics are refused, whether one range of rows of
+    # the threaded rasterisation already sees them all ("rows": stripes across x, every row of
+    # cells crosses all of them) or only the merge of the ranges does ("columns": stripes across
+    # y, each row lies in one of them)
+    res, n = 10.0, 300
+    p = W.plates_box_2d(10, 1.0, polarization="TM", n_steps=10)
+    p["n"] = [n, n, 1]
+    d = 1.0 / res
+    objs = []
+    for q in range(n):
+        lo = [q * d, 0.0, 0.0] if layout == "rows" else [0.0, q * d, 0.0]
+        hi = [(q + 0.5) * d, n * d, 0.0] if layout == "rows" else [n * d, (q + 0.5) * d, 0.0]
+        objs.append({"shape": "box", "lo": lo, "hi": hi, "kind": "dielectric", "eps": 1.5 + 0.01 * q, "mu": 1.0})
+    p["objects"] = objs
+    p["faces"] = [{"axis": 1, "sign": 1, "pos": 1.0, "lo": [0.0, 1.0, 0.0], "hi": [1.0, 1.0, 0.0]}]
+    with pytest.raises(pk.CasimirError) as e:
+        pk.Plan(p)
+    assert e.value.code == -1 and "256" in str(e.value)
+    p["objects"] = objs[:200]                     # 201 ids with the background: accepted
+    assert pk.Plan(p).info()["n_sims"] > 0
