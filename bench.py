@@ -634,12 +634,20 @@ def main():
             for name, p in probs.items():
                 F = ctx.plan(p).run()[0][p["force_axis"]]
                 Fo, scale = ref[name]
-                check[name] = {"precision": p.get("precision", "fp64"), "force": float(F), "oracle": Fo,
-                               "rel_err": abs(F - Fo) / abs(Fo), "err_over_sum_abs": abs(F - Fo) / scale}
+                prec = p.get("precision", "fp64")
+                # FP32 fields: 1e-4 of the force; FP64: 1e-10 of the force plus the rounding floor
+                # 16 u sqrt(T) sum |c_i| of a sum whose per-simulation terms cancel
+                bound = 1e-4 * abs(Fo) if prec == "fp32" else \
+                    1e-10 * abs(Fo) + 16 * 2.0 ** -53 * math.sqrt(p["n_steps"]) * scale
+                check[name] = {"precision": prec, "force": float(F), "oracle": Fo,
+                               "rel_err": abs(F - Fo) / abs(Fo), "err_over_sum_abs": abs(F - Fo) / scale,
+                               "sum_abs_over_force": scale / abs(Fo), "bound": bound,
+                               "within_bound": bool(abs(F - Fo) <= bound)}
             cases = list(check.values())
             for prec in ("fp32", "fp64"):
                 errs = [v["rel_err"] for v in cases if v["precision"] == prec]
                 check[f"max_rel_err_{prec}"] = max(errs) if errs else None
+            check["all_within_bound"] = all(v["within_bound"] for v in cases)
         except Exception as e:  # the oracle is test infrastructure; report, do not fail the bench
             check = {"error": repr(e)}
 

@@ -336,15 +336,16 @@ int64_t casimir_plan_sim_entries(const casimir_plan_t *plan, int64_t sim, int wh
  * (rectangle rule); w must hold n_steps doubles. */
 int casimir_plan_weights(const casimir_plan_t *plan, double *w, int64_t n);
 
-/* Allocation-free run of a plan, for callers that cannot allocate device memory
- * (no counterpart in the paper; this is a library-integration entry point).
- * Such callers include code that runs while a CUDA graph is being captured, a
- * host that gives the library only a fixed memory reservation, and embedders
- * whose allocator must not be re-entered.  The call performs no cudaMalloc,
- * cudaFree or other allocating routine: every intermediate (fields, simulation
- * and tile tables, the plan's copied tables) lives in one static device array of
- * 64 MiB per device, which every GPU that loads the library holds until the
- * process exits.
+/* Allocation-free run of a plan (no counterpart in the paper; an entry point for
+ * embedding the library).  Some callers cannot let a library allocate device memory:
+ * a host that has already handed nearly all of the GPU's memory to its own pool, so
+ * that a cudaMalloc would fail or fragment that pool; an embedder whose memory
+ * manager must not be re-entered from inside one of its own callbacks; and
+ * latency-bound loops that cannot absorb the device-wide synchronisation that
+ * cudaFree implies.  This call performs no cudaMalloc, cudaFree or other allocating
+ * routine: every intermediate (fields, simulation and tile tables, the plan's copied
+ * tables, the launch counter) lives in one static device array of 64 MiB per device,
+ * which every GPU that loads the library holds until the process exits.
  *   plan       any plan of two-dimensional (TM/TE) simulations, including a
  *              host-only plan built with ctx == NULL;
  *   d_per_sim  DEVICE pointer to n_sims doubles; receives every simulation's
@@ -352,13 +353,16 @@ int casimir_plan_weights(const casimir_plan_t *plan, double *w, int64_t n);
  *              weight (all work is queued on `cuda_stream`; synchronise it
  *              before reading);
  *   cuda_stream a cudaStream_t, or NULL for the default stream.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture begins.
- * Every call reuses the same array, which keeps the previous call's contents
- * (the call clears what must start at zero); calls whose work overlaps on the
- * GPU race on the array and must be serialised by the caller.  Returns
- * CASIMIR_ENOMEM, with the required size in casimir_last_error(), when the plan
- * does not fit in the array, and CASIMIR_EINVAL for non-2D plans. */
+ * The first call on a device does the set-up: with that device current it looks up
+ * the array's device address (and, under lazy module loading, its first launches
+ * load the kernels); make that first call, and let it complete, before any stream
+ * capture begins.  Every call reuses the same array, which keeps the previous
+ * call's contents (the call clears what must start at zero); calls whose work
+ * overlaps on the GPU race on the array and must be serialised by the caller.
+ * The tables reach the device through ordinary asynchronous copies from host
+ * memory owned by the call.  Returns CASIMIR_ENOMEM, with the required size in
+ * casimir_last_error(), when the plan does not fit in the array, and
+ * CASIMIR_EINVAL for non-2D plans. */
 int casimir_run_noalloc(const casimir_plan_t *plan, double *d_per_sim, void *cuda_stream);
 
 /* Thread-local message describing the last error of the calling thread. */

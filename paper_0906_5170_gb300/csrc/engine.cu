@@ -18,6 +18,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <new>
+#include <stdexcept>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -1353,17 +1355,30 @@ static casimir_plan_options autotune(casimir_ctx *c, const casimir_problem &p)
 int casimir_plan_ex(casimir_ctx_t *c, const casimir_problem *p, const casimir_plan_options *opts, casimir_plan_t **out)
 {
     if (!p || !out) return fail(CASIMIR_EINVAL, "NULL argument");
-    return make_plan(c, p, opts, out);
+    try {
+        return make_plan(c, p, opts, out);
+    } catch (const std::bad_alloc &) {
+        return fail(CASIMIR_ENOMEM, "out of host memory while planning");
+    } catch (const std::exception &e) {
+        return fail(CASIMIR_EINVAL, std::string("planning failed: ") + e.what());
+    }
 }
 
 int casimir_plan(casimir_ctx_t *c, const casimir_problem *p, casimir_plan_t **out)
 {
     if (!p || !out) return fail(CASIMIR_EINVAL, "NULL argument");
-    if (c && c->autotune) {
-        const casimir_plan_options o = autotune(c, *p);
-        return make_plan(c, p, &o, out);
+    // nothing thrown by the planner (host allocation, thread creation) crosses the C ABI
+    try {
+        if (c && c->autotune) {
+            const casimir_plan_options o = autotune(c, *p);
+            return make_plan(c, p, &o, out);
+        }
+        return make_plan(c, p, nullptr, out);
+    } catch (const std::bad_alloc &) {
+        return fail(CASIMIR_ENOMEM, "out of host memory while planning");
+    } catch (const std::exception &e) {
+        return fail(CASIMIR_EINVAL, std::string("planning failed: ") + e.what());
     }
-    return make_plan(c, p, nullptr, out);
 }
 
 int casimir_plan_get_options(const casimir_plan_t *P, casimir_plan_options *opts)
@@ -1640,14 +1655,14 @@ int casimir_run(casimir_plan_t *P, double F[3], double *per_sim, casimir_stats *
 // ---------------------------------------------------------------------------------
 // Allocation-free run of a two-dimensional plan.
 //
-// Some callers may not allocate device memory at all: code running while a
-// CUDA graph is being captured (cudaMalloc is not permitted inside a capture),
-// hosts that hand the library a fixed memory reservation, or embedders whose
-// allocator must not be re-entered from a library.  casimir_run_noalloc lets
-// them run a plan without any device allocation: the fields, the simulation
-// and tile tables, the copied plan tables and the launch counter all live in
-// the file-scope array below, allocated once per device when the library is
-// loaded and held until the process exits.
+// Some callers cannot let a library allocate device memory: hosts that have
+// handed nearly all of the GPU's memory to their own pool, embedders whose memory
+// manager must not be re-entered from one of its own callbacks, and loops that
+// cannot absorb the device-wide synchronisation of cudaFree.  casimir_run_noalloc
+// lets them run a plan without any device allocation: the fields, the simulation
+// and tile tables, the copied plan tables and the launch counter all live in the
+// file-scope array below, which every device that loads the library holds until
+// the process exits.
 // ---------------------------------------------------------------------------------
 
 static constexpr size_t kNoallocBytes = size_t(64) << 20;   // 64 MiB per device

@@ -6,6 +6,7 @@
 // face, Eq. (7); sources spread onto the Yee grid), Appendix A (g(t)).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <map>
 #include <array>
 #include <complex>
@@ -16,6 +17,16 @@
 namespace cas {
 
 namespace {
+// Host threads for rasterising a lattice: the hardware's, at most 16; the environment
+// variable CASIMIR_PLAN_THREADS (1..64) overrides the count.
+int plan_threads()
+{
+    if (const char *e = std::getenv("CASIMIR_PLAN_THREADS")) {
+        const int v = std::atoi(e);
+        if (v >= 1 && v <= 64) return v;
+    }
+    return (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+}
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTol = 1e-6;   // geometric tolerance, in cells
@@ -299,11 +310,10 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err, 
     // numbered in parallel, each in its own first-seen order; merging the ranges in scan order
     // then gives every key the id a single pass would give it.
     const int64_t rows = (int64_t)p.n[1] * p.n[2];
-    const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    const int nchunk = (int)std::min<int64_t>(ncell >= (1 << 16) ? hw : 1, rows);
+    const int nchunk = (int)std::min<int64_t>(ncell >= (1 << 16) ? plan_threads() : 1, rows);
     std::vector<std::vector<std::vector<double>>> chunk_keys(nchunk);
-    std::vector<char> overflow(nchunk, 0);
-    auto number_rows = [&](int s) {
+    std::vector<char> overflow(nchunk, 0), failed(nchunk, 0);
+    auto number_rows_range = [&](int s) {
         std::map<std::vector<double>, int> local;
         std::vector<double> key(narr + NPK), prev_key;
         int prev_id = -1;
@@ -332,12 +342,31 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err, 
             }
         }
     };
+    auto number_rows = [&](int s) {
+        // runs on a worker thread: nothing may escape it (an exception leaving a thread's
+        // function terminates the process), so an allocation failure is flagged per range
+        try {
+            number_rows_range(s);
+        } catch (...) {
+            failed[s] = 1;
+        }
+    };
     {
+        // ranges whose thread cannot be started are numbered on the calling thread
         std::vector<std::thread> pool;
-        for (int s = 1; s < nchunk; ++s) pool.emplace_back(number_rows, s);
-        number_rows(0);
+        std::vector<int> inline_ranges{0};
+        for (int s = 1; s < nchunk; ++s) {
+            try {
+                pool.emplace_back(number_rows, s);
+            } catch (...) {
+                inline_ranges.push_back(s);
+            }
+        }
+        for (int s : inline_ranges) number_rows(s);
         for (auto &t : pool) t.join();
     }
+    for (int s = 0; s < nchunk; ++s)
+        if (failed[s]) { *err = "out of host memory while numbering material sites"; return CASIMIR_ENOMEM; }
     std::map<std::vector<double>, int> ids;
     for (int s = 0; s < nchunk; ++s) {
         if (overflow[s]) { *err = "more than 256 distinct material sites"; return CASIMIR_EINVAL; }
@@ -346,7 +375,10 @@ int build_geo(const PlanData &P, int family, int kpt, Geo *g, std::string *err, 
             auto it = ids.find(chunk_keys[s][q]);
             if (it == ids.end()) {
                 const int id = (int)ids.size();
-                if (id > 255) { *err = "more than 256 distinct material sites"; return CASIMIR_EINVAL; }
+                if (id > 255) {
+                    *err = "more than 256 distinct material sites (found when merging the row ranges)";
+                    return CASIMIR_EINVAL;
+                }
                 it = ids.emplace(chunk_keys[s][q], id).first;
             }
             remap[q] = (uint8_t)it->second;

@@ -265,11 +265,13 @@ def test_header_is_plain_c(tmp_path):
 
 
 @pytest.mark.parametrize("layout", ["rows", "columns"])
-def test_plan_rejects_more_than_256_materials(layout):
+def test_plan_rejects_more_than_256_materials(layout, monkeypatch):
     # material ids are bytes: 300 distinct dielectrics are refused, whether one range of rows of
     # the threaded rasterisation already sees them all ("rows": stripes across x, every row of
     # cells crosses all of them) or only the merge of the ranges does ("columns": stripes across
-    # y, each row lies in one of them)
+    # y, each row lies in one of them).  Eight row ranges whatever the host's core count, so that
+    # the merge is reached on a one-core machine too.
+    monkeypatch.setenv("CASIMIR_PLAN_THREADS", "8")
     res, n = 10.0, 300
     p = W.plates_box_2d(10, 1.0, polarization="TM", n_steps=10)
     p["n"] = [n, n, 1]
@@ -284,5 +286,6 @@ def test_plan_rejects_more_than_256_materials(layout):
     with pytest.raises(pk.CasimirError) as e:
         pk.Plan(p)
     assert e.value.code == -1 and "256" in str(e.value)
+    assert ("merging" in str(e.value)) == (layout == "columns")   # which of the two checks fired
     p["objects"] = objs[:200]                     # 201 ids with the background: accepted
     assert pk.Plan(p).info()["n_sims"] > 0

@@ -3,9 +3,9 @@ Sec. III D): every kernel that carries the auxiliary equations (the two-dimensio
 the two-phase one-thread-per-cell kernel, the three-dimensional x-line kernel, the plain
 path) against the FP64 oracle, simulation by simulation.
 
-Tolerances as in the other parity tests: FP64 1e-10 relative; FP32 fields with FP64
-accumulation 2e-5 of the largest simulation per simulation and 1e-4 of the sum of
-|contributions| for the force."""
+Tolerances as in the other parity tests (tests/parity_bounds.py): FP64 1e-10 relative per
+simulation and for the force (plus the rounding floor of a cancelling sum); FP32 fields with
+FP64 accumulation 2e-5 of the largest simulation per simulation and 1e-4 of the force itself."""
 import json
 import os
 import subprocess
@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 import workloads as W
+from parity_bounds import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -50,14 +51,7 @@ def _oracle(p, key):
 def _compare(per, F, p, key, fp64):
     Fo, parts = _oracle(p, key)
     fa = p["force_axis"]
-    assert per.shape == parts.shape
-    scale = np.sum(np.abs(parts))
-    if fp64:
-        assert np.all(np.abs(per - parts) <= 1e-10 * np.abs(parts) + 1e-13 * scale)
-        assert abs(F[fa] - Fo) <= 1e-10 * abs(Fo) + 1e-13 * scale
-    else:
-        assert np.max(np.abs(per - parts)) <= 2e-5 * np.max(np.abs(parts))
-        assert abs(F[fa] - Fo) <= 1e-4 * scale
+    assert_parity(per, F[fa], parts, Fo, p["n_steps"], fp64, str(key))
 
 
 def small_grating(prec="fp64", **kw):
