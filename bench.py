@@ -243,7 +243,7 @@ def measure_basis(pk, ctx):
         return F[fa], n, wall, ms
 
     Fp, n_p, w_p, ms_p = one(dict(base, basis="point"))
-    out = {"workload": "config-2 geometry h = 1.225 (400 x 138), TE + TM, 4000 steps, FP32 fields",
+    out = {"workload": "config-2 geometry h = 1.575 (400 x 166), TE + TM, 4000 steps, FP32 fields",
            "point": {"sims": n_p, "wall_s": w_p, "kernel_ms": ms_p, "force": Fp}, "cosine": []}
     for k in (5, 10, 20, 40):
         F, n, w, ms = one(dict(base, n_harm=k))
