@@ -22,6 +22,7 @@ import subprocess
 import sys
 import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -121,27 +122,28 @@ def workload_problems(n_steps=20000, n_harm=40):
 
 def serving_trial(pk, ctx, n_requests=12, rate=50.0, scale=0.15, seed=0, plain=False, trace=None):
     """Poisson arrivals of the seeded serving mix (2D pistons/waveguides, Bloch gratings, 3D
-    spheres, grid sides scaled by `scale`), or the given trace of (arrival s, problem).  Batched:
-    every request is submitted at its arrival time and joins the running batch.  Plain: requests
-    run one after another through the unbatched path.  Latency = completion - arrival."""
+    spheres, grid sides scaled by `scale`), or the given trace of (arrival s, problem).  Every
+    request is planned on the host when it arrives (rasterisation, basis, g(t), simulation list:
+    the autotuner's trials for the first request of a problem class included), so its latency,
+    completion - arrival, includes its planning; plan_ms reports that part on its own.  Batched:
+    the request is submitted once planned and joins the running batch.  Plain: requests run one
+    after another through the unbatched path."""
     import workloads as W
     if trace is None:
         trace = W.serving_requests(seed, n_requests=n_requests, rate=rate, scale=scale)
-    # host planning (rasterisation, basis, g(t), simulation list) happens before the trace
-    # starts, as for a prepared query; its time per request is reported beside the latencies
-    plans, plan_ms = [], []
-    for _, p in trace:
-        tp = time.perf_counter()
-        plans.append(ctx.plan(p))
-        plan_ms.append(1e3 * (time.perf_counter() - tp))
-    done = [None] * len(trace)
+    n = len(trace)
+    done = [None] * n
+    plan_ms = [0.0] * n
+    plans = [None] * n
     t0 = time.perf_counter()
     if not plain:
-        tickets = [None] * len(trace)
+        tickets = [None] * n
         nxt = 0
         while any(d is None for d in done):
-            now = time.perf_counter() - t0
-            while nxt < len(trace) and trace[nxt][0] <= now:
+            while nxt < n and trace[nxt][0] <= time.perf_counter() - t0:
+                tp = time.perf_counter()
+                plans[nxt] = ctx.plan(trace[nxt][1])
+                plan_ms[nxt] = 1e3 * (time.perf_counter() - tp)
                 tickets[nxt] = plans[nxt].submit(tag=nxt)
                 nxt += 1
             for i, t in enumerate(tickets):
@@ -149,10 +151,13 @@ def serving_trial(pk, ctx, n_requests=12, rate=50.0, scale=0.15, seed=0, plain=F
                     done[i] = time.perf_counter() - t0
             time.sleep(0.0005)
     else:
-        for i, (arr, _) in enumerate(trace):
+        for i, (arr, p) in enumerate(trace):
             wait = arr - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(wait)
+            tp = time.perf_counter()
+            plans[i] = ctx.plan(p)
+            plan_ms[i] = 1e3 * (time.perf_counter() - tp)
             plans[i].run(plain=True)
             done[i] = time.perf_counter() - t0
     lat = sorted(1e3 * (d - a) for d, (a, _) in zip(done, trace))
@@ -160,13 +165,17 @@ def serving_trial(pk, ctx, n_requests=12, rate=50.0, scale=0.15, seed=0, plain=F
     kinds = {}
     for _, p in trace:
         kinds[p.get("kind", "?")] = kinds.get(p.get("kind", "?"), 0) + 1
+    cu = sum(pl.info()["cell_updates"] for pl in plans)
     for pl in plans:
         pl.close()
-    pl = sorted(plan_ms)
-    return {"forces_per_s": len(trace) / makespan, "p50_ms": lat[len(lat) // 2],
-            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "makespan_s": makespan,
-            "requests": len(trace), "mix": kinds,
-            "plan_ms_p50": pl[len(pl) // 2], "plan_ms_max": pl[-1]}
+    pm = sorted(plan_ms)
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(q * len(v)))]
+    return {"forces_per_s": n / makespan, "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "makespan_s": makespan,
+            "requests": n, "mix": kinds, "latency_includes_planning": True,
+            "plan_ms_p50": pct(pm, 0.5), "plan_ms_p99": pct(pm, 0.99), "plan_ms_max": pm[-1],
+            "gcell_updates_per_s": cu / makespan / 1e9}
 
 
 def serving_load_sweep(pk, ctx, scale=0.15):
@@ -186,40 +195,73 @@ def serving_load_sweep(pk, ctx, scale=0.15):
             "capacity_forces_per_s": cap, "load_sweep": sweep}
 
 
-def measure_configs(pk, ctx, peak):
-    """The other configurations, each timed once after a warm-up run (device-resident
-    tables): Gcell-updates/s of the step kernels and the fraction of the HBM roofline on
-    algorithmic bytes.  Bounded subsets where the full configuration would take minutes."""
+def measure_configs(pk, ctx, peak, local=0, stream=None):
+    """The other configurations: Gcell-updates/s of the step kernels, the fraction of the HBM
+    roofline on algorithmic bytes and forces/s.  Config 1 in full, timed after a warm-up run;
+    config 3 (one gap: all 32 k_z x 30 harmonics) and config 4 (one height: 6 faces x 36
+    harmonics, every contributing source) as whole forces, timed once from submission to result
+    (host planning excluded, table upload included).  Config 4 needs 184 GB of fields and runs
+    in a context with a 150 GB budget: its force is the sum over three plans by face (the two
+    faces normal to the force, the four others), which the executor admits as memory frees up.
+    Returns the measurements and, for the oracle leg, three sampled simulations of config 3."""
+    import numpy as np
     import workloads as W
     out = {}
-    kp = W.config3_kz_points(0.5, medium=W.waveguide_material())
-    cases = {
-        "plates_2d_tm_fp64_full": ([W.config1_plates()], "full configuration (24 sims, 60x40, 4000 steps, FP64)"),
-        "waveguides_kz_cpml_lorentz": ([W.config3_waveguides(0.5, k_points=[kp[i] for i in (0, 8, 16, 24)])],
-                                       "gap 0.5, 4 of 32 k_z points, 30 harmonics, 256x256, 3840 steps"),
-        "sphere_notch_3d": ([W.config4_sphere_notch(0.55, seed=1, n_harm=1)],
-                            "height 0.55, 1 harmonic per face (20 sims), 160^3, 3200 steps"),
-    }
-    for name, (probs, desc) in cases.items():
-        plans = [ctx.plan(p) for p in probs]
-        for pl in plans:
-            pl.run()
-        ctx.kernel_stats(reset=True)
+
+    def timed(plans, c, per_sim=False):
+        c.kernel_stats(reset=True)
         t0 = time.perf_counter()
-        for pl in plans:
-            pl.run()
+        if per_sim:
+            res = [pl.run(per_sim=True) for pl in plans]
+        else:
+            tickets = [pl.submit(tag=i) for i, pl in enumerate(plans)]
+            res = [t.force(-1) for t in tickets]
         wall = time.perf_counter() - t0
-        ms, nl, cu = ctx.kernel_stats()
-        info = plans[0].info()
-        b = info["bytes_per_step"] / info["n_cells"]     # fields, CPML psi and Lorentz planes
+        ms, nl, cu = c.kernel_stats(reset=True)
+        infos = [pl.info() for pl in plans]
+        b = sum(i["bytes_per_step"] for i in infos) / sum(i["n_cells"] for i in infos)
         gcu = cu / (ms / 1e3) / 1e9
-        out[name] = {"workload": desc, "gcell_updates_per_s": gcu, "bytes_per_cell_update": b,
-                     "bytes_per_cell_update_fields_only": info["bytes_per_update"],
-                     "hbm_frac": gcu * b / peak, "forces_per_s": len(plans) / wall,
-                     "kernel_ms": ms, "launches": nl}
+        return res, {"gcell_updates_per_s": gcu, "bytes_per_cell_update": b,
+                     "bytes_per_cell_update_fields_only": infos[0]["bytes_per_update"], "hbm_frac": gcu * b / peak,
+                     "forces_per_s": 1.0 / wall, "wall_s": wall, "kernel_ms": ms, "launches": nl,
+                     "sims": sum(i["n_sims"] for i in infos), "cell_updates": sum(i["cell_updates"] for i in infos)}
+
+    # config 1: the full configuration, warm
+    pl = ctx.plan(W.config1_plates())
+    pl.run()
+    _, m = timed([pl], ctx)
+    out["plates_2d_tm_fp64_full"] = dict(m, workload="full configuration (24 sims, 60x40, 4000 steps, FP64)")
+    pl.close()
+    # config 3: one whole force (gap 0.5)
+    p3 = W.config3_waveguides(0.5)
+    pl = ctx.plan(p3)
+    res, m = timed([pl], ctx, per_sim=True)
+    F3, per3, _ = res[0]
+    out["waveguides_kz_cpml_lorentz_full"] = dict(
+        m, workload="gap 0.5, all 32 k_z points x 30 harmonics, 256x256 with 1-unit CPML, 3840 steps (one whole force)",
+        F_x=float(F3[0]))
+    picks = [0, len(per3) // 2, len(per3) - 1]
+    sample3 = {"problem": p3, "picks": picks, "gpu": [float(per3[i]) for i in picks],
+               "scale": float(np.max(np.abs(per3)))}
+    pl.close()
+    # config 4: one whole force (height 0.55), three plans by face under a 150 GB budget
+    p4 = W.config4_sphere_notch(0.55, seed=1)
+    zf = [f for f in p4["faces"] if f["axis"] == p4["force_axis"]]
+    rest = [f for f in p4["faces"] if f["axis"] != p4["force_axis"]]
+    c4 = pk.Context(local, hbm_budget_bytes=150 * 10**9, stream=stream)
+    try:
+        plans = [c4.plan(dict(p4, faces=fs)) for fs in ([zf[0]], [zf[1]], rest)]
+        res, m = timed(plans, c4)
+        out["sphere_notch_3d_full"] = dict(
+            m, workload="height 0.55, 6 faces x 6x6 harmonics (720 sims), 160^3 with 12-cell CPML, 3200 steps "
+                        "(one whole force: three plans by face under a 150 GB budget)",
+            F_z=float(sum(r[0][2] for r in res)), device_gb=sum(pl.info()["device_bytes"] for pl in plans) / 1e9,
+            kernel_3d=plans[0].options()["kernel_3d"])
         for pl in plans:
             pl.close()
-    return out
+    finally:
+        c4.close()
+    return out, sample3
 
 
 def measure_basis(pk, ctx):
@@ -375,7 +417,6 @@ def cpu_baseline(budget_s=15.0):
     h = 0.5 geometry for a shortened number of steps, one per host core."""
     import numpy as np
     import oracle
-    from concurrent.futures import ThreadPoolExecutor
     import workloads as W
     cores = os.cpu_count() or 1
     T = 1000
@@ -405,6 +446,10 @@ def profile_case_problems(case, steps):
         return [W.config3_waveguides(0.5, n_harm=6, n_steps=steps, k_points=[kp[3], kp[12]])]
     if case == "sphere3d":     # 160^3 CPML cell, 1 harmonic per face: 20 simulations
         return [W.config4_sphere_notch(0.55, seed=1, n_harm=1, n_steps=steps)]
+    if case == "sphere3d_face":   # the same cell, one face normal to the force: 6 simulations (1.5 GB)
+        p = W.config4_sphere_notch(0.55, seed=1, n_harm=1, n_steps=steps)
+        p["faces"] = [f for f in p["faces"] if f["axis"] == p["force_axis"]][:1]
+        return [p]
     if case == "cylinder":     # rotationally symmetric two-block piston, h = 1: 60 x 400 (r, z), m, n <= 2
         p = W.cylinder_blocks(1.0)
         p["n_steps"] = steps
@@ -452,6 +497,74 @@ def run_profile_case(args):
     ctx.close()
 
 
+def run_serving_full(args):
+    """The serving mix at its stated size (grid sides x 1.0): the first N requests of the seed-0
+    trace (Poisson, 50 requests/s), batched then plain on the same trace, in a context with a
+    150 GB HBM budget and autotuning; each request class's first request re-run synchronously
+    and two of its simulations recomputed by the FP64 oracle.  One JSON line."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_0906_5170_gb300 import build as pkbuild
+    pkbuild.build()
+    import paper_0906_5170_gb300 as pk
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    sctx = pk.Context(0, hbm_budget_bytes=150 * 10**9, stream=stream.cuda_stream)
+    sctx.set_autotune(True)
+    trace = W.serving_requests(0, n_requests=args.serving_full, rate=50.0, scale=1.0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    batched = serving_trial(pk, sctx, trace=trace)
+    plain = serving_trial(pk, sctx, trace=trace, plain=True)
+    clk = clocks.stop()
+    # one request of each class: its simulations on the GPU against the oracle, two sampled ones
+    firsts = {}
+    for _, p in trace:
+        firsts.setdefault(p["kind"], p)
+    picks_gpu = {}
+    for kind, p in firsts.items():
+        pl = sctx.plan(p)
+        _, per, _ = pl.run(per_sim=True)
+        rng = np.random.default_rng(1)
+        picks = sorted(int(i) for i in rng.choice(len(per), size=2, replace=False))
+        picks_gpu[kind] = (p, picks, [float(per[i]) for i in picks], float(np.max(np.abs(per))))
+        pl.close()
+    sctx.close()
+    check = {}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build_all()
+        jobs = [(kind, i, j) for kind, v in picks_gpu.items() for j, i in enumerate(v[1])]
+
+        def one(job):
+            kind, i, _ = job
+            p = picks_gpu[kind][0]
+            s_ = oracle.enumerate_sims(p)[i]
+            st_ = oracle.grid_setup(p, p["k_points"][s_["k"]]["k"])
+            w = oracle.g_weights(p)
+            return float(np.sum(w * oracle.run_sim(p, s_, st_).real)) * p["k_points"][s_["k"]]["weight"]
+        with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+            refs = list(ex.map(one, jobs))
+        for (kind, i, j), r in zip(jobs, refs):
+            g = picks_gpu[kind][2][j]
+            e = abs(g - r) / max(abs(r), 1e-3 * picks_gpu[kind][3])
+            c = check.setdefault(kind, {"sims": [], "gpu": [], "oracle": [], "rel_err": []})
+            c["sims"].append(i)
+            c["gpu"].append(g)
+            c["oracle"].append(r)
+            c["rel_err"].append(e)
+        for c in check.values():
+            c["within_2e-5"] = bool(max(c["rel_err"]) <= 2e-5)
+    out = {"serving_full": {"trace": f"seed 0, Poisson 50 req/s, serving mix at its stated size (x1.0), "
+                                     f"first {len(trace)} requests", "hbm_budget_bytes": 150 * 10**9,
+                            "batched": batched, "plain": plain,
+                            "forces_per_s_ratio": batched["forces_per_s"] / plain["forces_per_s"],
+                            "oracle_check_sampled_sims": check},
+           "clocks": clk}
+    print(json.dumps(out))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -488,17 +601,21 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=12)
+    ap.add_argument("--serving-full", type=int, default=0, metavar="N",
+                    help="run only the serving mix at its stated size: N requests, batched and plain")
     ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--no-serving-sweep", action="store_true", help="skip the 200-request trace and the load sweep")
     ap.add_argument("--no-autotune", action="store_true", help="default execution options instead of autotuned ones")
     ap.add_argument("--plain", action="store_true", help="profile cases: run the unbatched comparison path")
-    ap.add_argument("--profile-case", choices=["piston", "piston64", "waveguides", "sphere3d", "grating", "grating_silica", "grating_silica_small", "cylinder"], default=None,
+    ap.add_argument("--profile-case", choices=["piston", "piston64", "waveguides", "sphere3d", "sphere3d_face", "grating", "grating_silica", "grating_silica_small", "cylinder"], default=None,
                     help="run one mid-size case for kernel profiling instead of the benchmark")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_case:
         return run_profile_case(args)
+    if args.serving_full:
+        return run_serving_full(args)
 
     import numpy as np
     import torch
@@ -618,8 +735,9 @@ def main():
         sctx.close()
 
     others = None
+    sample3 = None
     if not args.no_configs:
-        others = measure_configs(pk, ctx, peaks()[0])
+        others, sample3 = measure_configs(pk, ctx, peaks()[0], local, stream.cuda_stream)
         others["basis_point_vs_cosine"] = measure_basis(pk, ctx)
         others["cylinder_piston"] = measure_cylinder(pk, ctx)
         others["grating_silica"] = measure_grating_silica(pk, ctx, peaks()[0])
@@ -643,11 +761,27 @@ def main():
                                "rel_err": abs(F - Fo) / abs(Fo), "err_over_sum_abs": abs(F - Fo) / scale,
                                "sum_abs_over_force": scale / abs(Fo), "bound": bound,
                                "within_bound": bool(abs(F - Fo) <= bound)}
-            cases = list(check.values())
+            if sample3 is not None:
+                # sampled simulations of the whole config-3 force against the oracle, one by one
+                p3 = sample3["problem"]
+                sims = oracle.enumerate_sims(p3)
+                w = oracle.g_weights(p3)
+
+                def one(i):
+                    s_ = sims[i]
+                    st_ = oracle.grid_setup(p3, p3["k_points"][s_["k"]]["k"])
+                    return float(np.sum(w * oracle.run_sim(p3, s_, st_).real)) * p3["k_points"][s_["k"]]["weight"]
+                with ThreadPoolExecutor(max_workers=len(sample3["picks"])) as ex:
+                    ref = list(ex.map(one, sample3["picks"]))
+                errs = [abs(g - r) / max(abs(r), 1e-3 * sample3["scale"]) for g, r in zip(sample3["gpu"], ref)]
+                check["config3_full_sampled_sims"] = {
+                    "precision": "fp32", "sims": sample3["picks"], "gpu": sample3["gpu"], "oracle": ref,
+                    "max_rel_err": max(errs), "bound": 2e-5, "within_bound": bool(max(errs) <= 2e-5)}
+            cases = [v for v in check.values() if "rel_err" in v]
             for prec in ("fp32", "fp64"):
                 errs = [v["rel_err"] for v in cases if v["precision"] == prec]
                 check[f"max_rel_err_{prec}"] = max(errs) if errs else None
-            check["all_within_bound"] = all(v["within_bound"] for v in cases)
+            check["all_within_bound"] = all(v["within_bound"] for v in check.values() if isinstance(v, dict))
         except Exception as e:  # the oracle is test infrastructure; report, do not fail the bench
             check = {"error": repr(e)}
 

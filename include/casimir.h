@@ -264,7 +264,9 @@ typedef struct {
                                (any value >= 2 fuses two; the default fuses two); other
                                six-component runs take one step per launch */
     int march_rows;         /* 2D six-component and cylindrical runs: rows per strip tile, 16, 32 or 64 (default 32) */
-    int kernel_3d;          /* 3D runs: 1 = x-line kernel (default), 2 = one-thread-per-cell kernel */
+    int kernel_3d;          /* 3D runs: 3 = column march, both half steps per pass (the default without
+                               CPML); 1 = x-line kernel, one half step per pass (the default with
+                               CPML); 2 = one-thread-per-cell kernel */
     int reserved;
 } casimir_plan_options;
 

@@ -16,7 +16,8 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcasimir.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU = ["step2d.cu", "step2d_t2.cu", "step2d_tk.cu", "step6.cu", "step6m.cu", "step6x.cu", "step6c2.cu", "engine.cu", "plain.cu"]
+CU = ["step2d.cu", "step2d_t2.cu", "step2d_tk.cu", "step6.cu", "step6m.cu", "step6x.cu", "step6c2.cu", "step3c.cu",
+      "engine.cu", "plain.cu"]
 CXX = ["plan.cpp"]
 
 
@@ -39,8 +40,10 @@ def up_to_date():
     return all(os.path.getmtime(s) <= t for s in sources())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, defines=()) -> str:
+    """defines: extra -D macros for the CUDA sources (tuning constants); a build with them is
+    always fresh."""
+    if not force and not defines and up_to_date():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -51,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(OUT_DIR, f + ".o")
         objs.append(o)
         cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *inc,
-               "-c", os.path.join(CSRC, f), "-o", o]
+               *["-D" + d for d in defines], "-c", os.path.join(CSRC, f), "-o", o]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         jobs.append(cmd)

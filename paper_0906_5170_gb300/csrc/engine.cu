@@ -234,7 +234,10 @@ static int prepare_plan(casimir_plan_t *P)
             hs.march = (D.prob.dims == 2 && g.n[2] == 1 && march_env && planes * N < ((int64_t)1 << 32)) ? 1 : 0;
             if (g.cyl && !hs.march)   // only the march kernel has the cylindrical form
                 return fail(CASIMIR_EINVAL, "cylindrical runs need the march kernel (12 N < 2^32 cells)");
-            const int nbuf = hs.march ? 2 : 1;
+            // three-dimensional runs: the column march (both half steps per launch, ping-pong
+            // buffers) by default, the x-line or per-cell kernels (in place) on request
+            hs.col3 = (!hs.march && D.prob.dims == 3 && P->opts.kernel_3d == 3 && planes * N < ((int64_t)1 << 32)) ? 1 : 0;
+            const int nbuf = (hs.march || hs.col3) ? 2 : 1;
             hs.fhalf = 6 * cf * N;
             off += nbuf * hs.fhalf;
             hs.psi_half = 0;
@@ -344,7 +347,89 @@ static int prepare_plan(casimir_plan_t *P)
                     hs.ntile2 = (int)P->tiles2.size() - hs.tile2_0;
                 }
             }
-            hs.line3 = (!hs.march && D.prob.dims == 3 && P->opts.kernel_3d == 1 && planes * N < ((int64_t)1 << 32)) ? 1 : 0;
+            if (hs.col3) {
+                // one warp per tile of COL3_W x COL3_H cells in (x, y) over a chunk of at most COL3_ZMAX
+                // planes; kernel variant of each tile from the CPML slabs and Lorentz poles of its
+                // halo-extended box [i0-1, i0+COL3_W] x [j0-1, j0+COL3_H] x [z0-1, z1] (cached per geometry)
+                const int tx = (hs.nx + COL3_W - 1) / COL3_W, ty = (hs.ny + COL3_H - 1) / COL3_H;
+                const int ncz = (hs.nz + COL3_ZMAX - 1) / COL3_ZMAX, zc = (hs.nz + ncz - 1) / ncz;
+                const int tz = (hs.nz + zc - 1) / zc;
+                auto vit = march_variants.find(sm.geo);
+                if (vit == march_variants.end()) {
+                    std::vector<int> dmat(g.nmat, 0);
+                    for (int id = 0; id < g.nmat; ++id)
+                        for (int q = 0; q < g.npoles; ++q)
+                            for (int c = 0; c < 3; ++c)
+                                if (g.lorentz[((size_t)id * g.npoles + q) * 6 + 2 * c] != 0.0) dmat[id] = std::max(dmat[id], q + 1);
+                    const int dX = g.has_pml[0] ? D.prob.pml_cells[0] : 0, dY = g.has_pml[1] ? D.prob.pml_cells[1] : 0;
+                    const int dZ = g.has_pml[2] ? D.prob.pml_cells[2] : 0;
+                    auto wrapc = [](int i, int n) { return ((i % n) + n) % n; };
+                    std::vector<int> vs((size_t)tx * ty * tz, 0);
+                    std::vector<int> colp((size_t)hs.nx * hs.ny);
+                    for (int tk = 0; tk < tz; ++tk) {
+                        const int z0 = tk * zc, z1 = std::min(hs.nz, z0 + zc);
+                        // the most poles of each (x, y) column over the chunk's planes and its halo planes
+                        std::fill(colp.begin(), colp.end(), 0);
+                        bool zp = false;
+                        for (int kk = z0 - 1; kk <= z1; ++kk) {
+                            const int k = wrapc(kk, hs.nz);
+                            if (dZ > 0 && (k < dZ || k >= hs.nz - dZ)) zp = true;
+                            if (g.npoles == 0) continue;
+                            for (int j = 0; j < hs.ny; ++j)
+                                for (int i = 0; i < hs.nx; ++i) {
+                                    int &cp = colp[(size_t)j * hs.nx + i];
+                                    cp = std::max(cp, dmat[g.mat[((size_t)k * hs.ny + j) * hs.nx + i]]);
+                                }
+                        }
+                        for (int tj = 0; tj < ty; ++tj)
+                            for (int ti = 0; ti < tx; ++ti) {
+                                const int i0 = ti * COL3_W, j0 = tj * COL3_H;
+                                bool pml = zp;
+                                int poles = 0;
+                                for (int jj = j0 - 1; jj <= j0 + COL3_H; ++jj) {
+                                    const int j = wrapc(jj, hs.ny);
+                                    if (dY > 0 && (j < dY || j >= hs.ny - dY)) pml = true;
+                                    for (int ii = i0 - 1; ii <= i0 + COL3_W; ++ii) {
+                                        const int i = wrapc(ii, hs.nx);
+                                        if (dX > 0 && (i < dX || i >= hs.nx - dX)) pml = true;
+                                        poles = std::max(poles, colp[(size_t)j * hs.nx + i]);
+                                    }
+                                }
+                                vs[((size_t)tk * ty + tj) * tx + ti] = (pml ? 1 : 0) + (poles == 0 ? 0 : poles == 1 ? 2 : 4);
+                            }
+                    }
+                    vit = march_variants.emplace(sm.geo, std::move(vs)).first;
+                }
+                std::vector<std::vector<DevEnt>> bucket((size_t)tx * ty * tz);
+                const int64_t sxy = (int64_t)hs.nx * hs.ny;
+                for (const Entry &e : sm.meas) {
+                    const int z = (int)(e.idx / sxy);
+                    const int64_t r = e.idx - (int64_t)z * sxy;
+                    const int j = (int)(r / hs.nx), i = (int)(r - (int64_t)j * hs.nx);
+                    const int ti = i / COL3_W, tj = j / COL3_H, tk = z / zc;
+                    const int loc = (j - tj * COL3_H) * 32 + (i - ti * COL3_W);
+                    auto &b = bucket[((size_t)tk * ty + tj) * tx + ti];
+                    if (e.re != 0.0 || !hs.cplx) b.push_back(DevEnt{loc | (e.arr << 16), z, e.re});
+                    if (hs.cplx && e.im != 0.0) b.push_back(DevEnt{loc | ((e.arr | 8) << 16), z, e.im});
+                }
+                hs.tile0 = (int)P->tilesM.size();
+                hs.ntile = tx * ty * tz;
+                hs.ent0 = (int)P->entsM.size();
+                for (int tk = 0; tk < tz; ++tk)
+                    for (int tj = 0; tj < ty; ++tj)
+                        for (int ti = 0; ti < tx; ++ti) {
+                            const size_t tt = ((size_t)tk * ty + tj) * tx + ti;
+                            auto &b = bucket[tt];
+                            HostTile ht{(int)s, ti * COL3_W, tj * COL3_H, (int)P->entsM.size(), (int)b.size(),
+                                        vit->second[tt] + (hs.magnetic ? MARCH_VARIANTS : 0)};
+                            ht.z0 = tk * zc;
+                            ht.z1 = std::min(hs.nz, ht.z0 + zc);
+                            P->tilesM.push_back(ht);
+                            P->entsM.insert(P->entsM.end(), b.begin(), b.end());
+                        }
+                hs.nent = (int)P->entsM.size() - hs.ent0;
+            }
+            hs.line3 = (!hs.march && !hs.col3 && D.prob.dims == 3 && P->opts.kernel_3d == 1 && planes * N < ((int64_t)1 << 32)) ? 1 : 0;
             if (hs.line3) {
                 // tiles of 32 x cells by LINES3 (y, z) lines; entries bucketed per tile
                 const int64_t nl = (int64_t)hs.ny * hs.nz;
@@ -370,7 +455,7 @@ static int prepare_plan(casimir_plan_t *P)
                     }
                 hs.nent = (int)P->entsM.size() - hs.ent0;
             }
-            if (!hs.march && !hs.line3) {
+            if (!hs.march && !hs.line3 && !hs.col3) {
                 int ntile = (int)((N + TILE6 - 1) / TILE6);
                 hs.tile0 = (int)P->tiles6.size();
                 hs.ntile = ntile;
@@ -650,11 +735,12 @@ void make_sim6(const casimir_plan_t *P, char *blk, double *acc, double *tail, in
     d->kz = g.kz;
     d->kzA = hs.kzA;
     d->kzB = hs.kzB;
-    d->fhalf = hs.march ? hs.fhalf : 0;
+    const bool pp = hs.march || hs.col3;   // ping-pong buffers
+    d->fhalf = pp ? hs.fhalf : 0;
     d->tile_rows = P->opts.march_rows;
     d->npoles = hs.npoles;
-    d->psi_half = hs.march ? hs.psi_half : 0;
-    d->lor_half = hs.march ? hs.lor_half : 0;
+    d->psi_half = pp ? hs.psi_half : 0;
+    d->lor_half = pp ? hs.lor_half : 0;
 }
 
 static int grow(casimir_ctx *c, void **p, size_t *cap, size_t need)
@@ -681,6 +767,8 @@ static int rebuild(casimir_ctx *c)
     std::vector<DevTile> tm6[4 * MARCH_VARIANTS];
     std::vector<DevSim6> sl3[4];
     std::vector<DevTile> tl3[4];
+    std::vector<DevSim6> scol[4 * COL3_VARIANTS];
+    std::vector<DevTile> tcol[4 * COL3_VARIANTS];
     std::vector<DevSim6> sc6[2];
     std::vector<DevTile> tc6[2];
     std::vector<DevSim6> sc2[2];    // cylindrical, two steps per launch
@@ -710,6 +798,21 @@ static int rebuild(casimir_ctx *c)
                         const HostTile &ht = P->tiles[t];
                         tv.push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.ents + ht.ent0});
                     }
+                }
+            } else if (hs.col3) {
+                // the simulation's descriptor goes to each variant group that holds one of its tiles
+                DevSim6 d;
+                make_sim6(P, blk, r->acc, r->tail, w.s0, s, &d);
+                int idx[COL3_VARIANTS];
+                std::fill(idx, idx + COL3_VARIANTS, -1);
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile &ht = P->tilesM[t];
+                    const int gi = COL3_VARIANTS * (2 * P->fp64 + hs.cplx) + ht.variant;
+                    if (idx[ht.variant] < 0) {
+                        idx[ht.variant] = (int)scol[gi].size();
+                        scol[gi].push_back(d);
+                    }
+                    tcol[gi].push_back(DevTile{idx[ht.variant], ht.i0, ht.j0, ht.ne, P->dev.entsM + ht.ent0, ht.z0, ht.z1});
                 }
             } else if (hs.line3) {
                 const int gi = 2 * P->fp64 + hs.cplx;
@@ -790,9 +893,12 @@ static int rebuild(casimir_ctx *c)
         } else if (gi < casimir_ctx::G_CYL2) {
             const int v = 2 + gi - casimir_ctx::G_T3;
             ns = 0; nt = tt[v].size(); ss = sizeof(DevSim2D); ts = sizeof(DevTile2); sp = nullptr; tp = tt[v].data();
-        } else {
+        } else if (gi < casimir_ctx::G_COL3) {
             const int v = gi - casimir_ctx::G_CYL2;
             ns = sc2[v].size(); nt = tc2[v].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile2); sp = sc2[v].data(); tp = tc2[v].data();
+        } else {
+            const int v = gi - casimir_ctx::G_COL3;
+            ns = scol[v].size(); nt = tcol[v].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = scol[v].data(); tp = tcol[v].data();
         }
         int rc = grow(c, &G.sims, &G.sims_cap, ns * ss);
         if (rc) return rc;
@@ -842,8 +948,12 @@ static void launch_unit(casimir_ctx *c, int gi, int j, cudaStream_t st)
         // the 2D simulation tables are those of groups 0 / 1
         const int f = gi - casimir_ctx::G_T3;
         launch_step2d_t3(f, (const DevSim2D *)c->groups[f].sims, (const DevTile2 *)G.tiles, G.ntiles, c->d_launch, j, st);
-    } else {
+    } else if (gi < casimir_ctx::G_COL3) {
         launch_march6_cyl2(gi - casimir_ctx::G_CYL2, (const DevSim6 *)G.sims, (const DevTile2 *)G.tiles, G.ntiles, c->d_launch, j, st);
+    } else {
+        const int v = gi - casimir_ctx::G_COL3, fc = v / COL3_VARIANTS;   // 2 * fp64 + cplx
+        launch_col3(fc >> 1, fc & 1, v % COL3_VARIANTS, (const DevSim6 *)G.sims, (const DevTile *)G.tiles, G.ntiles,
+                    c->d_launch, j, st);
     }
 }
 
@@ -1216,28 +1326,44 @@ int casimir_ctx_kernel_stats(casimir_ctx_t *c, double *step_ms, int64_t *launche
     return CASIMIR_OK;
 }
 
-// Options with defaults filled in (the environment variables CASIMIR_STEP2D_K and
-// CASIMIR_LINE3 set the defaults of steps_per_launch and kernel_3d, for A/B runs).
+// Options with defaults filled in (the environment variables CASIMIR_STEP2D_K, CASIMIR_LINE3
+// and CASIMIR_COL3 set the defaults of steps_per_launch and kernel_3d, for A/B runs).
 // The default of steps_per_launch is 3 for FP32 runs (fewer passes over memory; measured 25%
 // faster than 2 on the piston sweep) and 2 for FP64 runs (bound by FP64 arithmetic, where the
-// third step's extra halo work costs more than the memory it saves).
-static int resolve_options(const casimir_plan_options *in, casimir_plan_options *out, bool fp64)
+// third step's extra halo work costs more than the memory it saves).  The default 3D kernel is
+// the column march for runs without CPML (73.0 against 67.4 Gcell-updates/s for the x-line
+// kernel on a closed 160^3 sphere cell) and the x-line kernel for runs with CPML (52.1 against
+// 40.5 with a 12-cell CPML shell: the march's CPML path carries 2.5 times the instructions of
+// its interior path).
+static bool has_pml3d(const casimir_problem &p)
+{
+    if (p.dims != 3) return false;
+    for (int a = 0; a < 3; ++a)
+        if (p.bc[a] == CASIMIR_BC_PML) return true;
+    return false;
+}
+
+static int resolve_options(const casimir_plan_options *in, casimir_plan_options *out, bool fp64, bool pml3d)
 {
     static const int k_env = [] {
         const char *e = std::getenv("CASIMIR_STEP2D_K");
         return e ? std::atoi(e) : 0;
     }();
     static const int l_env = [] {
+        // CASIMIR_LINE3=0: the per-cell kernel; CASIMIR_COL3=0: the x-line kernel; else the column march
         const char *e = std::getenv("CASIMIR_LINE3");
-        return (e && std::atoi(e) == 0) ? 2 : 1;
+        if (e && std::atoi(e) == 0) return 2;
+        const char *c = std::getenv("CASIMIR_COL3");
+        if (c) return std::atoi(c) == 0 ? 1 : 3;
+        return 0;   // by problem: below
     }();
     casimir_plan_options o{};
     if (in) o = *in;
     if (o.steps_per_launch == 0) o.steps_per_launch = (k_env >= 1 && k_env <= 3) ? k_env : (fp64 ? 2 : 3);
     if (o.march_rows == 0) o.march_rows = MARCH_H;
-    if (o.kernel_3d == 0) o.kernel_3d = l_env;
+    if (o.kernel_3d == 0) o.kernel_3d = l_env ? l_env : (pml3d ? 1 : 3);
     if (o.steps_per_launch < 1 || o.steps_per_launch > 3 || o.march_rows < 1 || o.march_rows > MARCH_H_MAX ||
-        (o.kernel_3d != 1 && o.kernel_3d != 2))
+        o.kernel_3d < 1 || o.kernel_3d > 3)
         return fail(CASIMIR_EINVAL, "plan options out of range");
     o.reserved = 0;
     *out = o;
@@ -1250,7 +1376,7 @@ static int make_plan(casimir_ctx_t *c, const casimir_problem *p, const casimir_p
     *out = nullptr;
     auto *P = new casimir_plan_t();
     P->ctx = c;
-    int rc = resolve_options(opts, &P->opts, p->precision == CASIMIR_FP64);
+    int rc = resolve_options(opts, &P->opts, p->precision == CASIMIR_FP64, has_pml3d(*p));
     if (rc) { delete P; return rc; }
     std::string err;
     rc = build_plan(p, &P->data, &err);
@@ -1285,12 +1411,17 @@ static casimir_plan_options autotune(casimir_ctx *c, const casimir_problem &p)
 {
     NvtxRange nvtx_("casimir.autotune");
     casimir_plan_options dflt{};
-    resolve_options(nullptr, &dflt, p.precision == CASIMIR_FP64);
+    resolve_options(nullptr, &dflt, p.precision == CASIMIR_FP64, has_pml3d(p));
     std::vector<casimir_plan_options> cand;
     if (p.dims == 3) {
-        cand = {dflt, dflt};
-        cand[0].kernel_3d = 1;
-        cand[1].kernel_3d = 2;
+        // the default first (ties keep it), then the other 3D kernels
+        cand = {dflt};
+        for (int k : {3, 1, 2})
+            if (k != dflt.kernel_3d) {
+                casimir_plan_options o = dflt;
+                o.kernel_3d = k;
+                cand.push_back(o);
+            }
     } else if (p.polarization == CASIMIR_POL_FULL) {
         for (int rows : {32, 16, 64}) {
             casimir_plan_options o = dflt;

@@ -48,6 +48,7 @@ struct HostSim {
     int full;              // six-component fields
     int march;             // two-dimensional six-component run on the march kernel (ping-pong buffers)
     int line3;             // three-dimensional run on the x-line kernel (tiles in tilesM)
+    int col3;              // three-dimensional run on the column-march kernel (tiles in tilesM, ping-pong buffers)
     int cyl;               // cylindrical (r, z) run on the march kernel's cylindrical variant
     int cplx;              // complex fields (Bloch phase)
     int magnetic;
@@ -66,6 +67,7 @@ struct HostSim {
 struct HostTile {
     int sim, i0, j0, ent0, ne;
     int variant = 0;       // march tiles: 1 = touches CPML, + 2 (4) = the most Lorentz poles of its cells is 1 (> 1)
+    int z0 = 0, z1 = 0;    // column-march tiles: planes [z0, z1)
 };
 
 struct HostTile2 {
@@ -190,7 +192,9 @@ struct casimir_ctx {
     static constexpr int G_CYL = G_LINE3 + 4;
     static constexpr int G_T3 = G_CYL + 2;          // [G_T3 + fp64] the three-step 2D kernel
     static constexpr int G_CYL2 = G_T3 + 2;         // [G_CYL2 + fp64] the two-step cylindrical march
-    static constexpr int NGROUPS = G_CYL2 + 2;
+    // [G_COL3 + COL3_VARIANTS * (2*fp64 + cplx) + variant] the column march of 3D runs
+    static constexpr int G_COL3 = G_CYL2 + 2;
+    static constexpr int NGROUPS = G_COL3 + 4 * COL3_VARIANTS;
     struct Group {
         void *sims = nullptr, *tiles = nullptr;
         size_t sims_cap = 0, tiles_cap = 0;

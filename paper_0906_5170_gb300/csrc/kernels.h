@@ -40,6 +40,7 @@ struct DevTile {
     int i0, j0;
     int ne;                // entries of the surface functional in this tile
     const DevEnt *ents;
+    int z0, z1;            // column-march tiles of 3D runs: the planes [z0, z1) of the tile
 };
 
 struct DevSrc {
@@ -132,6 +133,22 @@ void launch_inject6(int fp64, void *fields, const DevSrc6 *src, int nsrc, cudaSt
 constexpr int LINES3 = 64;
 void launch_line3(int fp64, int cplx, const DevSim6 *sims, const DevTile *tiles, int ntiles,
                   const int64_t *launch_base, int64_t launch_add, int phase, cudaStream_t st);
+
+// Six-component leapfrog of three-dimensional runs by column tiles: one warp per tile of
+// COL3_W x COL3_H cells in (x, y) over the planes [z0, z1), both half steps in one launch;
+// fields, CPML psi and Lorentz P ping-pong between two buffers (step n reads buffer (n-1)&1,
+// writes n&1) with the march's fhalf / psi_half / lor_half.  Tile entries: DevEnt with
+// loc = (y - j0) * 32 + (x - i0) in bits 0..15, the component in bits 16..18, bit 19 for the
+// weight of the imaginary part, and pad = z.  variant: as for the march (1 = CPML planes in the
+// tile's halo-extended box, + 2 = cells with one Lorentz pole at most, + 4 = up to three poles),
+// + MARCH_VARIANTS for magnetic (K) sources.  A run's planes are cut into chunks of at most
+// COL3_ZMAX.
+constexpr int COL3_W = 30;
+constexpr int COL3_H = 8;
+constexpr int COL3_ZMAX = 40;
+constexpr int COL3_VARIANTS = 12;
+void launch_col3(int fp64, int cplx, int variant, const DevSim6 *sims, const DevTile *tiles, int ntiles,
+                 const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 
 // Multi-step tiles of the 2D kernels: four warp strips of 32 - 2K interior columns (K time
 // steps per launch, K halo lanes per side); the tile's pixel entries sorted by row, with

@@ -120,8 +120,8 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
     std::vector<DevSim2D> s2;
     std::vector<DevSim6> s6;
     std::vector<DevTile> t2;
-    std::vector<DevTile> tv[MARCH_VARIANTS];    // march tiles by kernel variant
-    int voff[MARCH_VARIANTS + 1] = {};
+    std::vector<DevTile> tv[COL3_VARIANTS];     // march and column-march tiles by kernel variant
+    int voff[COL3_VARIANTS + 1] = {};
     std::vector<DevTile6> t6;
     std::vector<PlainEnt> pe;
     std::vector<PlainSim> ps;
@@ -134,6 +134,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
         // sequence) and goes faster through the one-thread-per-cell kernel, in place on buffer 0.
         bool march = P->sims[run[0]].march;
         const bool line3 = P->sims[run[0]].line3;
+        const bool col3 = P->sims[run[0]].col3;
         const bool cylr = P->sims[run[0]].cyl;   // only the march kernel has the cylindrical form
         if (march) {
             int64_t nt = 0;
@@ -148,7 +149,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
         for (size_t q : run) {
             const HostSim &hs = P->sims[q];
             int64_t N = (int64_t)hs.nx * hs.ny * hs.nz;
-            PlainSim one{hs.full ? (march ? hs.fhalf : 0) : 3 * N, (int)pe.size(), 0, acc + q};
+            PlainSim one{hs.full ? (march || col3 ? hs.fhalf : 0) : 3 * N, (int)pe.size(), 0, acc + q};
             if (!hs.full) {
                 DevSim2D d;
                 make_sim2d(P, b, acc, tail, 0, q, &d);
@@ -163,6 +164,22 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
                         int ly = loc / TILE_X, lx = loc - ly * TILE_X;
                         int64_t g = (int64_t)arr * N + (int64_t)(ht.j0 + ly) * hs.nx + ht.i0 + lx;
                         pe.push_back(PlainEnt{hs.field_off + g, -1, en.w, 0.0});
+                    }
+                }
+            } else if (hs.col3) {
+                DevSim6 d;
+                make_sim6(P, b, acc, tail, 0, q, &d);
+                int idx = (int)s6.size();
+                s6.push_back(d);
+                for (int t = hs.tile0; t < hs.tile0 + hs.ntile; ++t) {
+                    const HostTile &ht = P->tilesM[t];
+                    tv[ht.variant].push_back(DevTile{idx, ht.i0, ht.j0, 0, nullptr, ht.z0, ht.z1});   // projection runs separately
+                    for (int e = ht.ent0; e < ht.ent0 + ht.ne; ++e) {
+                        const DevEnt &en = P->entsM[e];
+                        int loc = en.loc & 0xffff, arr = (en.loc >> 16) & 7, im = (en.loc >> 19) & 1;
+                        int64_t plane = hs.cplx ? 2 * arr + im : arr;
+                        int64_t g = plane * N + ((int64_t)en.pad * hs.ny + ht.j0 + (loc >> 5)) * hs.nx + ht.i0 + (loc & 31);
+                        pe.push_back(PlainEnt{hs.field_off + g, -1, im ? -en.w : en.w, 0.0});
                     }
                 }
             } else if (hs.line3) {
@@ -238,16 +255,17 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
             one.ne = (int)pe.size() - one.ent0;
             ps.push_back(one);
         }
-        if (march) {
-            for (int v = 0; v < MARCH_VARIANTS; ++v) {
+        if (march || col3) {
+            const int nv = col3 ? COL3_VARIANTS : MARCH_VARIANTS;
+            for (int v = 0; v < nv; ++v) {
                 voff[v] = (int)t2.size();
                 t2.insert(t2.end(), tv[v].begin(), tv[v].end());
             }
-            voff[MARCH_VARIANTS] = (int)t2.size();
+            voff[nv] = (int)t2.size();
         }
         void *d_sim = nullptr, *d_tiles = nullptr, *d_pe = nullptr, *d_ps = nullptr;
         size_t bsim = align256(full ? s6.size() * sizeof(DevSim6) : s2.size() * sizeof(DevSim2D));
-        size_t btil = align256(full && !march && !line3 ? t6.size() * sizeof(DevTile6) : t2.size() * sizeof(DevTile));
+        size_t btil = align256(full && !march && !line3 && !col3 ? t6.size() * sizeof(DevTile6) : t2.size() * sizeof(DevTile));
         size_t bpe = align256(std::max<size_t>(1, pe.size()) * sizeof(PlainEnt));
         size_t bps = align256(ps.size() * sizeof(PlainSim));
         void *rb = nullptr;
@@ -260,7 +278,7 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
         d_ps = (char *)rb + bsim + btil + bpe;
         if (full) {
             CUDA_TRY(cudaMemcpyAsync(d_sim, s6.data(), s6.size() * sizeof(DevSim6), cudaMemcpyHostToDevice, s));
-            if (march || line3)
+            if (march || line3 || col3)
                 CUDA_TRY(cudaMemcpyAsync(d_tiles, t2.data(), t2.size() * sizeof(DevTile), cudaMemcpyHostToDevice, s));
             else
                 CUDA_TRY(cudaMemcpyAsync(d_tiles, t6.data(), t6.size() * sizeof(DevTile6), cudaMemcpyHostToDevice, s));
@@ -274,6 +292,13 @@ extern "C" int casimir_run_plain(casimir_plan_t *P, double F[3], double *per_sim
             if (!full) {
                 launch_step2d(P->fp64, (const DevSim2D *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, s);
                 ++launches;
+            } else if (col3) {
+                for (int v = 0; v < COL3_VARIANTS; ++v)
+                    if (voff[v + 1] > voff[v]) {
+                        launch_col3(P->fp64, cplx, v, (const DevSim6 *)d_sim, (const DevTile *)d_tiles + voff[v],
+                                    voff[v + 1] - voff[v], d_counter, n - 1, s);
+                        ++launches;
+                    }
             } else if (line3) {
                 for (int phase = 0; phase < 2; ++phase)
                     launch_line3(P->fp64, cplx, (const DevSim6 *)d_sim, (const DevTile *)d_tiles, (int)t2.size(), d_counter, n - 1, phase, s);

@@ -115,10 +115,14 @@ def test_plan_rejects_invalid_cylindrical_problems(mutate):
 def test_plan_options_defaults_and_explicit():
     p = W.piston_small()
     # three fused steps for FP32 runs, two for FP64 runs (bound by FP64 arithmetic)
-    assert pk.Plan(dict(p, precision="fp32")).options() == {"steps_per_launch": 3, "march_rows": 32, "kernel_3d": 1}
-    assert pk.Plan(dict(p, precision="fp64")).options() == {"steps_per_launch": 2, "march_rows": 32, "kernel_3d": 1}
+    assert pk.Plan(dict(p, precision="fp32")).options() == {"steps_per_launch": 3, "march_rows": 32, "kernel_3d": 3}
+    assert pk.Plan(dict(p, precision="fp64")).options() == {"steps_per_launch": 2, "march_rows": 32, "kernel_3d": 3}
+    # 3D: the column march without CPML, the x-line kernel with it
+    s3 = W.config4_sphere_notch(0.4, seed=3, resolution=6, n_cells=24, pml_cells=4, n_harm=1, n_steps=10)
+    assert pk.Plan(s3).options()["kernel_3d"] == 1
+    assert pk.Plan(dict(s3, bc=["pec", "pec", "pec"])).options()["kernel_3d"] == 3
     o = pk.Plan(p, options={"steps_per_launch": 1, "march_rows": 16}).options()
-    assert o == {"steps_per_launch": 1, "march_rows": 16, "kernel_3d": 1}
+    assert o == {"steps_per_launch": 1, "march_rows": 16, "kernel_3d": 3}
     for bad in ({"steps_per_launch": 4}, {"march_rows": 65}, {"kernel_3d": 5}):
         with pytest.raises(pk.CasimirError) as e:
             pk.Plan(p, options=bad)

@@ -236,6 +236,35 @@ def test_full_3d_sphere_notch(ctx, prec):
     _check(ctx, p, ("3d", prec), prec == "fp64")
 
 
+def _box3d_ragged(pml):
+    """A 3D cell of 37 x 19 x 45 cells: several column tiles with ragged edges along x and y and
+    two chunks of planes along z; a dielectric sphere over a PEC slab, a cubic stress surface
+    around the sphere, J and K sources (force along z); with CPML on x and z when pml."""
+    res = 8.0
+    p = W._base(3, (37, 19, 45), res, 60)
+    p["objects"] = [{"shape": "box", "lo": [0.0, 0.0, 0.0], "hi": [37 / res, 19 / res, 1.0], "kind": "pec"},
+                    {"shape": "sphere", "center": [2.3, 1.2, 3.0], "radius": 0.6, "kind": "dielectric",
+                     "eps": 3.0, "mu": 1.0}]
+    p["faces"] = W.box_faces([1.5, 0.375, 2.25], [3.125, 2.0, 3.875], 3)
+    p["n_harm"] = 2
+    p["polarization"] = "full"
+    p["force_axis"] = 2
+    if pml:
+        p["bc"] = ["pml", "pec", "pml"]
+        p["pml_cells"] = [4, 0, 4]
+    return p
+
+
+@pytest.mark.parametrize("pml", [False, True])
+def test_column_march_ragged_tiles_and_plane_chunks(ctx, pml):
+    # the fused 3D column march (kernel_3d 3) against the oracle, and against the x-line kernel
+    p = _box3d_ragged(pml)
+    _check(ctx, p, ("col3", pml), True, {"kernel_3d": 3})
+    _, per3, _ = ctx.plan(p, options={"kernel_3d": 3}).run(per_sim=True)
+    _, per1, _ = ctx.plan(p, options={"kernel_3d": 1}).run(per_sim=True)
+    assert np.allclose(per3, per1, rtol=1e-10, atol=1e-14 * np.sum(np.abs(per1)))
+
+
 def test_mixed_2d_and_full_requests_share_the_batch(ctx):
     probs = [W.piston_small(n_steps=400, precision="fp32"), _waveguides_small("fp32", (0.5,)),
              W.piston_small(h=0.8, n_steps=250, precision="fp64"), _waveguides_small("fp64", (2.0,))]
@@ -520,7 +549,7 @@ def test_execution_options_do_not_change_results(ctx):
         (W.piston_small(n_steps=300, precision="fp64"), [{"steps_per_launch": 1}, {"steps_per_launch": 2}, {"steps_per_launch": 3}]),
         (_waveguides_small("fp64", (0.0, 1.3)), [{"march_rows": 16}, {"march_rows": 32}, {"march_rows": 64}]),
         (W.config4_sphere_notch(0.4, seed=3, resolution=6, n_cells=24, pml_cells=4, n_harm=1, n_steps=60,
-                                precision="fp64", substrate_top=1.0), [{"kernel_3d": 1}, {"kernel_3d": 2}]),
+                                precision="fp64", substrate_top=1.0), [{"kernel_3d": 3}, {"kernel_3d": 1}, {"kernel_3d": 2}]),
         (W.cylinder_piston(12, [0, 1, 2], t_max=4.0), [{"march_rows": 16}, {"march_rows": 64}]),
     ]
     for p, opts in cases:

@@ -139,7 +139,7 @@ ctx.close()
     _compare(np.array(res["per"]), res["F"], p, "poles_t2", True)
 
 
-@pytest.mark.parametrize("kernel_3d", [1, 2])
+@pytest.mark.parametrize("kernel_3d", [3, 1, 2])
 def test_sphere_three_pole_3d(ctx, kernel_3d):
     p = sphere_three_pole("fp64")
     F, per, _ = ctx.plan(p, options={"kernel_3d": kernel_3d}).run(per_sim=True)
@@ -174,7 +174,7 @@ def bloch_slab_3d(prec="fp64"):
     return p
 
 
-@pytest.mark.parametrize("kernel_3d", [1, 2])
+@pytest.mark.parametrize("kernel_3d", [3, 1, 2])
 def test_bloch_three_pole_3d_complex(ctx, kernel_3d):
     p = bloch_slab_3d("fp64")
     F, per, _ = ctx.plan(p, options={"kernel_3d": kernel_3d}).run(per_sim=True)
