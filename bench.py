@@ -30,9 +30,28 @@ sys.path.insert(0, ROOT)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per cell of one launch, from one ncu capture of
 # the kernel on the piston profiling case (`--profile-case piston`, 17.0 M cells, above L2).  Traffic grows in
 # proportion to the cells (same tiles, same access pattern), so the benchmark's launch scales by its cell count.
-# Valid only for the kernel build that was captured; remove the entry when the kernel changes.
-DRAM_BYTES_PER_CELL_LAUNCH = {"k_step2d_t2<float>": (205.327e6 + 163.056e6) / 16998400,
-                              "k_step2d_tk<float, 3>": (210.452e6 + 169.787e6) / 16998400}
+# Each entry records the kernel source it was captured from and that file's SHA-256 prefix at capture time:
+# when the source has changed since, the bench reports the traffic as null (stale) instead of a wrong figure.
+DRAM_BYTES_PER_CELL_LAUNCH = {
+    "k_step2d_tk<float, 3>": {"bytes_per_cell": (210.452e6 + 169.787e6) / 16998400,
+                              "source": "paper_0906_5170_gb300/csrc/step2d_tk.cu", "sha256_16": "stale",
+                              "profile": "profiles/k_step2d_tk_piston_sweep.md"},
+}
+
+
+def traffic_per_cell(kernel):
+    """The recorded DRAM bytes per cell of `kernel`'s launch and its provenance; the figure is None
+    when the kernel source no longer matches the one captured."""
+    import hashlib
+    e = DRAM_BYTES_PER_CELL_LAUNCH.get(kernel)
+    if not e:
+        return None, None
+    with open(os.path.join(ROOT, e["source"]), "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    prov = {"profile": e["profile"], "source": e["source"], "source_sha256_16": h, "captured_sha256_16": e["sha256_16"],
+            "stale": h != e["sha256_16"]}
+    return (None if prov["stale"] else e["bytes_per_cell"]), prov
+
 
 METRIC = "forces/s and Gcell-updates/s (% HBM roofline), p50/p99 latency vs plain at 1e-4 rel"
 def workload_name(time_steps=20000):
@@ -446,9 +465,13 @@ def profile_case_problems(case, steps):
         return [W.config3_waveguides(0.5, n_harm=6, n_steps=steps, k_points=[kp[3], kp[12]])]
     if case == "sphere3d":     # 160^3 CPML cell, 1 harmonic per face: 20 simulations
         return [W.config4_sphere_notch(0.55, seed=1, n_harm=1, n_steps=steps)]
-    if case == "sphere3d_face":   # the same cell, one face normal to the force: 6 simulations (1.5 GB)
+    if case in ("sphere3d_face", "sphere3d_closed"):
+        # the same cell, one face normal to the force: 6 simulations (1.5 GB); closed: PEC walls
+        # instead of the CPML shell (the column march's default case)
         p = W.config4_sphere_notch(0.55, seed=1, n_harm=1, n_steps=steps)
         p["faces"] = [f for f in p["faces"] if f["axis"] == p["force_axis"]][:1]
+        if case == "sphere3d_closed":
+            p["bc"] = ["pec", "pec", "pec"]
         return [p]
     if case == "cylinder":     # rotationally symmetric two-block piston, h = 1: 60 x 400 (r, z), m, n <= 2
         p = W.cylinder_blocks(1.0)
@@ -607,7 +630,7 @@ def main():
     ap.add_argument("--no-serving-sweep", action="store_true", help="skip the 200-request trace and the load sweep")
     ap.add_argument("--no-autotune", action="store_true", help="default execution options instead of autotuned ones")
     ap.add_argument("--plain", action="store_true", help="profile cases: run the unbatched comparison path")
-    ap.add_argument("--profile-case", choices=["piston", "piston64", "waveguides", "sphere3d", "sphere3d_face", "grating", "grating_silica", "grating_silica_small", "cylinder"], default=None,
+    ap.add_argument("--profile-case", choices=["piston", "piston64", "waveguides", "sphere3d", "sphere3d_face", "sphere3d_closed", "grating", "grating_silica", "grating_silica_small", "cylinder"], default=None,
                     help="run one mid-size case for kernel profiling instead of the benchmark")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -684,11 +707,12 @@ def main():
     kmax = max(pl.options()["steps_per_launch"] for pl in plans)
     kernel = {1: "k_step2d<float>", 2: "k_step2d_t2<float>", 3: "k_step2d_tk<float, 3>"}[kmax]
     cells_per_launch = sum(i["n_cells"] for i, pl in zip(infos, plans) if pl.options()["steps_per_launch"] == kmax)
-    per_cell = DRAM_BYTES_PER_CELL_LAUNCH.get(kernel)
+    per_cell, traffic_prov = traffic_per_cell(kernel)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm if achieved else None,
             "traffic": per_cell * cells_per_launch if per_cell else None,
             "traffic_unit": "bytes per launch (ncu dram read + write per cell, scaled to this launch's cells)",
+            "traffic_provenance": traffic_prov,
             "kernel": kernel + f" ({kmax} time step{'s' if kmax > 1 else ''} per launch)", "bytes_per_cell_update": b_alg,
             "cells_per_launch": cells_per_launch,
             "avg_launch_ms": step_ms / max(1, launches), "peak_source": peak_kind}
@@ -763,6 +787,7 @@ def main():
                                "within_bound": bool(abs(F - Fo) <= bound)}
             if sample3 is not None:
                 # sampled simulations of the whole config-3 force against the oracle, one by one
+                import oracle
                 p3 = sample3["problem"]
                 sims = oracle.enumerate_sims(p3)
                 w = oracle.g_weights(p3)

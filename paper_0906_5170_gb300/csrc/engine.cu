@@ -685,6 +685,7 @@ void make_sim2d(const casimir_plan_t *P, char *blk, double *acc, double *tail, i
     d->T = D.prob.n_steps;
     d->tail_from = D.prob.n_steps - std::max(1, D.prob.n_steps / 8);
     d->second_u = hs.second_u;
+    d->nmat = D.geos[hs.geo].nmat;
     d->a = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt);
     d->bf = dt / (1.0 + 0.5 * sg * dt) / dx;
     d->hf = dt / dx;
@@ -1910,6 +1911,7 @@ extern "C" int casimir_run_noalloc(const casimir_plan_t *P, double *d_per_sim, v
         d->T = D.prob.n_steps;
         d->tail_from = D.prob.n_steps;
         d->second_u = hs.second_u;
+        d->nmat = D.geos[hs.geo].nmat;
         d->a = (1.0 - 0.5 * sg * dt) / (1.0 + 0.5 * sg * dt);
         d->bf = dt / (1.0 + 0.5 * sg * dt) / dx;
         d->hf = dt / dx;

@@ -23,7 +23,7 @@ struct DevSim2D {
     int T;
     int tail_from;
     int second_u;          // 1: the sigma / measured group is u; 0: it is (vx, vy)
-    int pad;
+    int nmat;              // rows of the coefficient table
     double a;              // (1 - sigma dt/2)/(1 + sigma dt/2)
     double bf;             // dt/(1 + sigma dt/2)/Delta
     double hf;             // dt/Delta (first group, halved on step 1)

@@ -100,6 +100,17 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
     // the first group's step of stage 0 is a half step at n = 1 (the impulse sits at t = 0+)
     const R hf0 = (R)(n1 == 1 ? 0.5 * S.hf : S.hf), hf = (R)S.hf;
     const R a = (R)S.a, bf = (R)S.bf;
+    // per material, the coefficients times their step factor: the first group's with hf, the
+    // sigma group's with bf ((hf c) d is the (hf * c) * d of the unfused kernels bit for bit; at
+    // stage 0 of the first launch the first group takes hf0 c = (hf c) / 2, exactly)
+    __shared__ R ctab[256][3];
+    for (int i = threadIdx.x; i < S.nmat; i += blockDim.x) {
+        const R cu = coef[3 * i], cvx = coef[3 * i + 1], cvy = coef[3 * i + 2];
+        ctab[i][0] = (S.second_u ? bf : hf) * cu;
+        ctab[i][1] = (S.second_u ? hf : bf) * cvx;
+        ctab[i][2] = (S.second_u ? hf : bf) * cvy;
+    }
+    __syncthreads();
     double p[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) p[q] = 0.0;
@@ -152,16 +163,17 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
 #pragma unroll
                     for (int q = 0; q < K; ++q) {
                         const int m = mh[q];
-                        const R cu = coef[3 * m], cvx = coef[3 * m + 1], cvy = coef[3 * m + 2];
-                        const R hq = q == 0 ? hf0 : hf;
+                        // hf c for the v group (hf0 c at stage 0 of the first launch), bf c_u
+                        const R scale = q == 0 && n1 == 1 ? (R)0.5 : (R)1;
+                        const R hcvx = ctab[m][1] * scale, hcvy = ctab[m][2] * scale, bcu = ctab[m][0];
                         // inputs: stage q-1 at rows rho (carried) and rho + 1 (this iteration)
                         const R uin = q == 0 ? u_cur : uo[q - 1];
                         const R uin1 = q == 0 ? un[i] : un_[q - 1];
                         const R vxin = q == 0 ? vxl[i] : vxo[q - 1];
                         const R vyin = q == 0 ? vyl[i] : vyo[q - 1];
-                        vxn[q] = vxin - hq * cvx * (uin1 - uin);
-                        vyn[q] = vyin + hq * cvy * (kdn(uin) - uin);
-                        un_[q] = a * uin + bf * cu * ((vyn[q] - kup(vyn[q])) - (vxn[q] - vxo[q]));
+                        vxn[q] = vxin - hcvx * (uin1 - uin);
+                        vyn[q] = vyin + hcvy * (kdn(uin) - uin);
+                        un_[q] = a * uin + bcu * ((vyn[q] - kup(vyn[q])) - (vxn[q] - vxo[q]));
                         const int rho = r - q;
                         if (q < ks && rho >= 0 && rho < h) {
                             if (q == ks - 1 && store) {
@@ -229,7 +241,7 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                     R unw[K], vxn[K], vyn[K];
 #pragma unroll
                     for (int q = 0; q < K; ++q) {
-                        const R hq = q == 0 ? hf0 : hf;
+                        const R scale = q == 0 && n1 == 1 ? (R)0.5 : (R)1;
                         // u at row r - q + 1 from stage q-1 at that row (u carried, v of this iteration) and v at row r - q
                         const R uin = q == 0 ? un[i] : uc[q - 1];
                         const R vxa = q == 0 ? vxl[i] : vxn[q - 1];
@@ -237,9 +249,9 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                         const R vxb = q == 0 ? vx_c : vxo[q - 1];
                         const R vyb = q == 0 ? vy_c : vyo[q - 1];
                         const int mu = mh[q], mv = mh[q + 1];
-                        unw[q] = uin + hq * coef[3 * mu] * ((vya - kup(vya)) - (vxa - vxb));
-                        vxn[q] = a * vxb - bf * coef[3 * mv + 1] * (unw[q] - uc[q]);
-                        vyn[q] = a * vyb + bf * coef[3 * mv + 2] * (kdn(uc[q]) - uc[q]);
+                        unw[q] = uin + ctab[mu][0] * scale * ((vya - kup(vya)) - (vxa - vxb));
+                        vxn[q] = a * vxb - ctab[mv][1] * (unw[q] - uc[q]);
+                        vyn[q] = a * vyb + ctab[mv][2] * (kdn(uc[q]) - uc[q]);
                         const int rho = r - q;
                         if (q < ks && rho >= 0 && rho < h) {
                             if (q == ks - 1 && store) {

@@ -101,6 +101,9 @@ struct RowIn {
     int m;
     Z<R, CPLX> p[3 * NP], pm[3 * NP];
     Z<R, CPLX> px[4], py[4];
+    // staged rows: this lane's P values in the row's shared-memory slot (read where they are
+    // used, so that the poles' state does not occupy registers); nullptr: p, pm above
+    const R *lp = nullptr;
 };
 
 // CYL: cylindrical (r, z) lattice (Sec. III C), x = r from the symmetry axis, y = z, stored
@@ -325,7 +328,16 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                         const R *lq = l4 + 12 * q;
                         if (q > 0 && !(q < np && lq[2] != (R)0)) continue;   // pole q absent here
                         const R ce = lq[2];
-                        const V p = in.p[3 * q + k], pm = in.pm[3 * q + k];
+                        V p, pm;
+                        if (STG > 0 && in.lp) {
+                            // slot layout: P then P_prev of pole q, component k, each CF values 32 apart
+                            const R *d = in.lp + 2 * (3 * q + k) * (CPLX ? 2 : 1) * 32;
+                            if constexpr (CPLX) { p = V(d[0], d[32]); pm = V(d[64], d[96]); }
+                            else { p = V(d[0]); pm = V(d[32]); }
+                        } else {
+                            p = in.p[3 * q + k];
+                            pm = in.pm[3 * q + k];
+                        }
                         const V pn = first_e ? (p * lq[0] + eo[k] * ce) * (R)0.5
                                              : (p * lq[0] - pm * lq[1] + eo[k] * ce) * lq[3];
                         if (wr) {
@@ -450,7 +462,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                         cur.q[k] = fv(slot, VQ + k);
                     }
                     cur.m = mr[0];
-                    fetch_lor(slot, cur, cur.m);
+                    if constexpr (LOR) cur.lp = ring + (slot * NV + VP * CF) * 32;
                     fetch_psi(slot, cur, j, 0, 4);
 #pragma unroll
                     for (int i = 0; i < STG; ++i) mr[i] = mr[i + 1];
@@ -521,7 +533,7 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                         cur.q[k] = fv(slot, VQ + k);
                     }
                     cur.m = mr[0];
-                    fetch_lor(slot, cur, cur.m);
+                    if constexpr (LOR) cur.lp = ring + (slot * NV + VP * CF) * 32;
                     fetch_psi(slot, cur, jn, 0, 2);
                     fetch_psi(slot, cur, j, 2, 4);
 #pragma unroll
@@ -764,7 +776,13 @@ struct Variants {
 
 using VarD1 = Variants<double, true, 3, 2, 2, 1, 1, 1>;
 using VarD0 = Variants<double, false, 4, 3, 3, 2, 2, 2>;
-using VarF1 = Variants<float, true, 4, 4, 3, 3, 2, 2>;
+#ifndef MARCH_F1_M1
+#define MARCH_F1_M1 4
+#endif
+#ifndef MARCH_F1_M45
+#define MARCH_F1_M45 3
+#endif
+using VarF1 = Variants<float, true, 4, MARCH_F1_M1, 3, 3, MARCH_F1_M45, MARCH_F1_M45>;
 using VarF0 = Variants<float, false, 7, 5, 6, 5, 4, 4>;
 
 }  // namespace
