@@ -780,7 +780,7 @@ using VarD0 = Variants<double, false, 4, 3, 3, 2, 2, 2>;
 #define MARCH_F1_M1 4
 #endif
 #ifndef MARCH_F1_M45
-#define MARCH_F1_M45 3
+#define MARCH_F1_M45 2
 #endif
 using VarF1 = Variants<float, true, 4, MARCH_F1_M1, 3, 3, MARCH_F1_M45, MARCH_F1_M45>;
 using VarF0 = Variants<float, false, 7, 5, 6, 5, 4, 4>;
