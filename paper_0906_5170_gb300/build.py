@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcasimir.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU = ["step2d.cu", "step2d_t2.cu", "step2d_tk.cu", "step6.cu", "step6m.cu", "step6x.cu", "step6c2.cu", "step3c.cu",
+CU = ["step2d.cu", "step2d_t2.cu", "step2d_tk.cu", "step6.cu", "step6m.cu", "step6x.cu", "step6c2.cu", "step6m2.cu", "step3c.cu",
       "engine.cu", "plain.cu"]
 CXX = ["plan.cpp"]
 

@@ -138,6 +138,7 @@ static int prepare_plan(casimir_plan_t *P)
     // sims, tiles, entries, sources
     int64_t off = 0;
     std::map<int, std::vector<int>> march_variants;   // per geometry: kernel variant of each march tile
+    std::map<int, std::vector<int>> mar2_variants;    // per geometry: variant of each two-step march tile
     for (size_t s = 0; s < D.sims.size(); ++s) {
         const Sim &sm = D.sims[s];
         const Geo &g = D.geos[sm.geo];
@@ -316,17 +317,59 @@ static int prepare_plan(casimir_plan_t *P)
                         P->entsM.insert(P->entsM.end(), b.begin(), b.end());
                     }
                 hs.nent = (int)P->entsM.size() - hs.ent0;
-                if (hs.cyl && P->opts.steps_per_launch >= 2) {
-                    // two steps per launch: MARCH_W2-wide strips, entries sorted by row with
-                    // per-row offsets (the sigma group is projected from registers)
+                // two steps per launch: cylindrical runs, and Cartesian FP32 runs whose materials have
+                // at most one Lorentz pole (the two-step march carries one pole's state per cell)
+                int geo_poles = 0;
+                for (int id = 0; id < g.nmat; ++id)
+                    for (int q = 0; q < g.npoles; ++q)
+                        for (int c = 0; c < 3; ++c)
+                            if (g.lorentz[((size_t)id * g.npoles + q) * 6 + 2 * c] != 0.0) geo_poles = std::max(geo_poles, q + 1);
+                if (P->opts.steps_per_launch >= 2 && (hs.cyl || (!P->fp64 && geo_poles <= 1))) {
+                    // MARCH_W2-wide strips, entries sorted by row with per-row offsets (the sigma
+                    // group is projected from registers)
                     const int tx2 = (hs.nx + MARCH_W2 - 1) / MARCH_W2;
+                    // kernel variant of each Cartesian tile: the CPML and Lorentz code paths only where
+                    // the box that two steps reach, [i0-2, i0+w+1] x [j0-2, j0+h+1], holds such cells
+                    auto v2 = mar2_variants.find(sm.geo);
+                    if (!hs.cyl && v2 == mar2_variants.end()) {
+                        const int dX = g.has_pml[0] ? D.prob.pml_cells[0] : 0, dY = g.has_pml[1] ? D.prob.pml_cells[1] : 0;
+                        const bool xper = D.prob.bc[0] == CASIMIR_BC_PERIODIC, yper = D.prob.bc[1] == CASIMIR_BC_PERIODIC;
+                        auto wrapc = [](int i, int n) { return ((i % n) + n) % n; };
+                        std::vector<bool> disp(g.nmat, false);
+                        for (int id = 0; id < g.nmat; ++id)
+                            for (int c = 0; c < 3 && g.npoles > 0; ++c)
+                                if (g.lorentz[((size_t)id * g.npoles) * 6 + 2 * c] != 0.0) disp[id] = true;
+                        std::vector<int> vs((size_t)tx2 * ty, 0);
+                        for (int tj = 0; tj < ty; ++tj)
+                            for (int ti = 0; ti < tx2; ++ti) {
+                                const int i0 = ti * MARCH_W2, j0 = tj * rows;
+                                const int w = std::min(MARCH_W2, hs.nx - i0), h = std::min(rows, hs.ny - j0);
+                                bool pml = false, lor = false;
+                                for (int jj = j0 - 2; jj <= j0 + h + 1; ++jj) {
+                                    const int j = wrapc(jj, hs.ny);
+                                    if (dY > 0 && (j < dY || j >= hs.ny - dY)) pml = true;
+                                    for (int ii = i0 - 2; ii <= i0 + w + 1; ++ii) {
+                                        const int i = wrapc(ii, hs.nx);
+                                        if (dX > 0 && (i < dX || i >= hs.nx - dX)) pml = true;
+                                        // across a closed wall the halo cells are wall cells: the
+                                        // components the tile uses there are masked
+                                        if ((jj != j && !yper) || (ii != i && !xper)) continue;
+                                        lor = lor || disp[g.mat[(size_t)j * hs.nx + i]];
+                                    }
+                                }
+                                vs[(size_t)tj * tx2 + ti] = (pml ? 1 : 0) + (lor ? 2 : 0);
+                            }
+                        v2 = mar2_variants.emplace(sm.geo, std::move(vs)).first;
+                    }
                     std::vector<std::vector<std::pair<int, DevEnt>>> b2((size_t)tx2 * ty);
                     for (const Entry &e : sm.meas) {
-                        if (inA(e.arr) != inA(sarr)) continue;   // real fields: the source's set only
+                        if (!hs.cplx && inA(e.arr) != inA(sarr)) continue;   // real fields: the source's set only
                         const int i = (int)(e.idx % hs.nx), j = (int)(e.idx / hs.nx);
                         const int ti = i / MARCH_W2, tj = j / rows;
                         const int loc = (j - tj * rows) * MARCH_W2 + (i - ti * MARCH_W2);
-                        b2[(size_t)tj * tx2 + ti].push_back({loc, DevEnt{loc | (e.arr << 16), 0, e.re}});
+                        auto &b = b2[(size_t)tj * tx2 + ti];
+                        if (e.re != 0.0 || !hs.cplx) b.push_back({loc, DevEnt{loc | (e.arr << 16), 0, e.re}});
+                        if (hs.cplx && e.im != 0.0) b.push_back({loc, DevEnt{loc | ((e.arr | 8) << 16), 0, e.im}});
                     }
                     hs.tile2_0 = (int)P->tiles2.size();
                     for (int tj = 0; tj < ty; ++tj)
@@ -336,6 +379,7 @@ static int prepare_plan(casimir_plan_t *P)
                                 return x.first < y.first;
                             });
                             HostTile2 ht{(int)s, ti * MARCH_W2, tj * rows, (int)P->ents2.size(), (int)b.size(), (int)P->rowptr2.size()};
+                            if (!hs.cyl) ht.variant = v2->second[(size_t)tj * tx2 + ti];
                             int k = 0;
                             for (int ly = 0; ly <= rows; ++ly) {
                                 while (k < (int)b.size() && b[k].first / MARCH_W2 < ly) ++k;
@@ -489,8 +533,10 @@ static int prepare_plan(casimir_plan_t *P)
     P->field_elems = off;
     {
         bool all2d = !P->sims.empty() && !P->sims[0].full;
-        const bool cyl = !P->sims.empty() && P->sims[0].cyl;
-        P->k2d = all2d ? P->opts.steps_per_launch : (cyl && P->opts.steps_per_launch >= 2 ? 2 : 1);
+        // six-component runs fuse two steps when every simulation has its two-step tiles
+        bool two6 = !P->sims.empty() && !all2d;
+        for (const HostSim &h : P->sims) two6 = two6 && h.march && h.ntile2 > 0;
+        P->k2d = all2d ? P->opts.steps_per_launch : (two6 ? 2 : 1);
         P->launches = (D.prob.n_steps + P->k2d - 1) / P->k2d;
     }
     P->table_bytes = (int64_t)(align256(P->ents2.size() * sizeof(DevEnt)) + align256(P->rowptr2.size() * sizeof(int)) +
@@ -774,6 +820,8 @@ static int rebuild(casimir_ctx *c)
     std::vector<DevTile> tc6[2];
     std::vector<DevSim6> sc2[2];    // cylindrical, two steps per launch
     std::vector<DevTile2> tc2[2];
+    std::vector<DevSim6> sm2[2 * MAR2_VARIANTS];    // Cartesian march, two steps per launch
+    std::vector<DevTile2> tm2[2 * MAR2_VARIANTS];
     for (auto &aw : c->active_waves) {
         casimir_request *r = aw.first;
         const casimir_request::Wave &w = r->waves[aw.second];
@@ -844,6 +892,21 @@ static int rebuild(casimir_ctx *c)
                         tc6[gi].push_back(DevTile{idx, ht.i0, ht.j0, ht.ne, P->dev.entsM + ht.ent0});
                     }
                 }
+            } else if (hs.march && P->k2d == 2) {
+                // two steps per launch: the descriptor goes to each variant group holding one of its tiles
+                DevSim6 d;
+                make_sim6(P, blk, r->acc, r->tail, w.s0, s, &d);
+                int idx[MAR2_VARIANTS];
+                std::fill(idx, idx + MAR2_VARIANTS, -1);
+                for (int t = hs.tile2_0; t < hs.tile2_0 + hs.ntile2; ++t) {
+                    const HostTile2 &ht = P->tiles2[t];
+                    const int gi = MAR2_VARIANTS * hs.cplx + ht.variant;
+                    if (idx[ht.variant] < 0) {
+                        idx[ht.variant] = (int)sm2[gi].size();
+                        sm2[gi].push_back(d);
+                    }
+                    tm2[gi].push_back(DevTile2{idx[ht.variant], ht.i0, ht.j0, ht.ne, P->dev.ents2 + ht.ent0, P->dev.rowptr2 + ht.rp0});
+                }
             } else if (hs.march) {
                 // the simulation's descriptor goes to each variant group that holds one of its tiles
                 DevSim6 d;
@@ -897,9 +960,12 @@ static int rebuild(casimir_ctx *c)
         } else if (gi < casimir_ctx::G_COL3) {
             const int v = gi - casimir_ctx::G_CYL2;
             ns = sc2[v].size(); nt = tc2[v].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile2); sp = sc2[v].data(); tp = tc2[v].data();
-        } else {
+        } else if (gi < casimir_ctx::G_MAR2) {
             const int v = gi - casimir_ctx::G_COL3;
             ns = scol[v].size(); nt = tcol[v].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile); sp = scol[v].data(); tp = tcol[v].data();
+        } else {
+            const int v = gi - casimir_ctx::G_MAR2;
+            ns = sm2[v].size(); nt = tm2[v].size(); ss = sizeof(DevSim6); ts = sizeof(DevTile2); sp = sm2[v].data(); tp = tm2[v].data();
         }
         int rc = grow(c, &G.sims, &G.sims_cap, ns * ss);
         if (rc) return rc;
@@ -951,10 +1017,14 @@ static void launch_unit(casimir_ctx *c, int gi, int j, cudaStream_t st)
         launch_step2d_t3(f, (const DevSim2D *)c->groups[f].sims, (const DevTile2 *)G.tiles, G.ntiles, c->d_launch, j, st);
     } else if (gi < casimir_ctx::G_COL3) {
         launch_march6_cyl2(gi - casimir_ctx::G_CYL2, (const DevSim6 *)G.sims, (const DevTile2 *)G.tiles, G.ntiles, c->d_launch, j, st);
-    } else {
+    } else if (gi < casimir_ctx::G_MAR2) {
         const int v = gi - casimir_ctx::G_COL3, fc = v / COL3_VARIANTS;   // 2 * fp64 + cplx
         launch_col3(fc >> 1, fc & 1, v % COL3_VARIANTS, (const DevSim6 *)G.sims, (const DevTile *)G.tiles, G.ntiles,
                     c->d_launch, j, st);
+    } else {
+        const int v = gi - casimir_ctx::G_MAR2;
+        launch_march6_2(v / MAR2_VARIANTS, v % MAR2_VARIANTS, (const DevSim6 *)G.sims, (const DevTile2 *)G.tiles, G.ntiles,
+                        c->d_launch, j, st);
     }
 }
 

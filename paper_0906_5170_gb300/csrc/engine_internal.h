@@ -72,6 +72,7 @@ struct HostTile {
 
 struct HostTile2 {
     int sim, i0, j0, ent0, ne, rp0;
+    int variant = 0;       // two-step march tiles of Cartesian runs: 1 = touches CPML, + 2 = Lorentz cells
 };
 
 struct HostTile6 {
@@ -194,7 +195,9 @@ struct casimir_ctx {
     static constexpr int G_CYL2 = G_T3 + 2;         // [G_CYL2 + fp64] the two-step cylindrical march
     // [G_COL3 + COL3_VARIANTS * (2*fp64 + cplx) + variant] the column march of 3D runs
     static constexpr int G_COL3 = G_CYL2 + 2;
-    static constexpr int NGROUPS = G_COL3 + 4 * COL3_VARIANTS;
+    // [G_MAR2 + MAR2_VARIANTS * cplx + variant] the two-step march of Cartesian 2D runs (FP32)
+    static constexpr int G_MAR2 = G_COL3 + 4 * COL3_VARIANTS;
+    static constexpr int NGROUPS = G_MAR2 + 2 * MAR2_VARIANTS;
     struct Group {
         void *sims = nullptr, *tiles = nullptr;
         size_t sims_cap = 0, tiles_cap = 0;

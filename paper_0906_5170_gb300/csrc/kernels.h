@@ -179,6 +179,13 @@ void launch_step2d_t3(int fp64, const DevSim2D *sims, const DevTile2 *tiles, int
 constexpr int MARCH_W2 = 28;
 void launch_march6_cyl2(int fp64, const DevSim6 *sims, const DevTile2 *tiles, int ntiles,
                         const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
+// Two steps per launch of the Cartesian six-component march (k_z, Bloch, CPML, one Lorentz pole
+// at most per cell), FP32: the tiles of launch_march6_cyl2, with bit 19 of an entry's loc set for
+// the weight of the imaginary part (complex fields).  variant: 1 = CPML planes in the tile's
+// two-step halo box, + 2 = dispersive cells there.
+constexpr int MAR2_VARIANTS = 4;
+void launch_march6_2(int cplx, int variant, const DevSim6 *sims, const DevTile2 *tiles, int ntiles,
+                     const int64_t *launch_base, int64_t launch_add, cudaStream_t st);
 
 void launch_step2d(int fp64, const DevSim2D *sims, const DevTile *tiles, int ntiles,
                    const int64_t *launch_base, int64_t launch_add, cudaStream_t st);

@@ -28,7 +28,11 @@ FP64 mode
   contours of the piston sum_j |c_j| / |F| reaches 1e6-3e7, which no choice of summation
   can undo, because each c_i is itself only known to FP64 precision.
 FP32 fields, FP64 accumulation
-  * the force: |F(GPU) - F(oracle)| <= 1e-4 |F(oracle)|;
+  * the force: |F(GPU) - F(oracle)| <= 1e-4 |F(oracle)| + m u sqrt(T) sum_j |c_j| (u = 2^-53:
+    the rounding floor of the FP64 sums, which both sides form in FP64 as in FP64 mode; it
+    matters only where the contributions cancel exactly, as in the first steps of a run
+    whose sources have not yet reached an asymmetric object: there the oracle's force is 0.0
+    and the GPU's a residual of order 1e-18 sum_j |c_j|);
   * per simulation: max_i |c_i(GPU) - c_i(oracle)| <= 2e-5 max_i |c_i(oracle)|, the same
     floor with u = 2^-24, m of about 5 and sqrt(T) of about 60 (T of a few thousand steps).
 """
@@ -72,5 +76,7 @@ def assert_parity(per, F_gpu, parts, F_oracle, n_steps, fp64, what=""):
         dmax = float(np.max(np.abs(per - parts))) if len(parts) else 0.0
         assert dmax <= 2e-5 * float(np.max(np.abs(parts))), (
             f"{what}: per-simulation error {dmax:.3e} > 2e-5 of the largest {float(np.max(np.abs(parts))):.3e}")
-        assert dF <= 1e-4 * abs(F_oracle), (f"{what}: force {F_gpu!r} vs oracle {F_oracle!r}: relative {frel:.3e} > 1e-4")
+        bound = 1e-4 * abs(F_oracle) + fp64_force_floor(parts, n_steps)
+        assert dF <= bound, (f"{what}: force {F_gpu!r} vs oracle {F_oracle!r}: |dF| {dF:.3e} > bound {bound:.3e} "
+                             f"(relative {frel:.3e})")
     return frel

@@ -3,8 +3,8 @@ simulation by simulation and for the force, on seeded synthetic geometries.
 
 Tolerances (tests/parity_bounds.py): FP64 mode 1e-10 relative per simulation, and
 for the force 1e-10 relative plus the FP64 rounding floor of a cancelling sum; FP32
-fields with FP64 accumulation: the force within 1e-4 of itself, each simulation within
-2e-5 of the largest contribution."""
+fields with FP64 accumulation: the force within 1e-4 of itself (plus the same floor of
+its FP64 sum), each simulation within 2e-5 of the largest contribution."""
 import numpy as np
 import pytest
 

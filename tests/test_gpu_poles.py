@@ -5,7 +5,8 @@ path) against the FP64 oracle, simulation by simulation.
 
 Tolerances as in the other parity tests (tests/parity_bounds.py): FP64 1e-10 relative per
 simulation and for the force (plus the rounding floor of a cancelling sum); FP32 fields with
-FP64 accumulation 2e-5 of the largest simulation per simulation and 1e-4 of the force itself."""
+FP64 accumulation 2e-5 of the largest simulation per simulation and 1e-4 of the force itself
+(plus the rounding floor of its FP64 sum)."""
 import json
 import os
 import subprocess
