@@ -482,10 +482,14 @@ def profile_case_problems(case, steps):
         p = W.grating_silica(0.5, nk_x=4 if case == "grating_silica" else 1)
         p["n_steps"] = steps
         return [p]
-    if case == "grating":      # 128 x 512 Bloch cell, 16 k_x (complex fields), CPML along y, 8 harmonics
+    if case in ("grating", "grating_small"):
+        # 128 x 512 Bloch cell, 16 k_x (complex fields), CPML along y, 8 harmonics; small: 2 of the
+        # k_x points (192 simulations, 1.2 GB of fields)
         import numpy as np
         p = W._serving_grating(1.0, np.random.default_rng(0))
         p["n_steps"] = steps
+        if case == "grating_small":
+            p["k_points"] = p["k_points"][::8]
         return [p]
     raise ValueError(case)
 
@@ -630,7 +634,7 @@ def main():
     ap.add_argument("--no-serving-sweep", action="store_true", help="skip the 200-request trace and the load sweep")
     ap.add_argument("--no-autotune", action="store_true", help="default execution options instead of autotuned ones")
     ap.add_argument("--plain", action="store_true", help="profile cases: run the unbatched comparison path")
-    ap.add_argument("--profile-case", choices=["piston", "piston64", "waveguides", "sphere3d", "sphere3d_face", "sphere3d_closed", "grating", "grating_silica", "grating_silica_small", "cylinder"], default=None,
+    ap.add_argument("--profile-case", choices=["piston", "piston64", "waveguides", "sphere3d", "sphere3d_face", "sphere3d_closed", "grating", "grating_small", "grating_silica", "grating_silica_small", "cylinder"], default=None,
                     help="run one mid-size case for kernel profiling instead of the benchmark")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -261,8 +261,10 @@ int casimir_plan_pml(const casimir_plan_t *plan, int axis, int half, double *b, 
 typedef struct {
     int steps_per_launch;   /* time steps fused into one pass over memory: 2D TM/TE runs 1, 2 or 3
                                (default 3 for FP32 runs, 2 for FP64 runs); cylindrical runs 1 or 2
-                               (any value >= 2 fuses two; the default fuses two); other
-                               six-component runs take one step per launch */
+                               (any value >= 2 fuses two; the default fuses two); other 2D
+                               six-component runs in FP32 whose materials have at most one
+                               Lorentz pole 1 or 2 (any value >= 2 fuses two; the default fuses
+                               two); all other six-component runs take one step per launch */
     int march_rows;         /* 2D six-component and cylindrical runs: rows per strip tile, 16, 32 or 64 (default 32) */
     int kernel_3d;          /* 3D runs: 3 = column march, both half steps per pass (the default without
                                CPML); 1 = x-line kernel, one half step per pass (the default with

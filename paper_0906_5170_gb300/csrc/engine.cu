@@ -1499,8 +1499,9 @@ static casimir_plan_options autotune(casimir_ctx *c, const casimir_problem &p)
             o.march_rows = rows;
             cand.push_back(o);
         }
-        if (p.coords == CASIMIR_COORDS_CYLINDRICAL && dflt.steps_per_launch >= 2) {
-            // the cylindrical march also runs one step per launch
+        if (dflt.steps_per_launch >= 2) {
+            // the two-step marches (cylindrical runs; Cartesian FP32 runs with at most one pole
+            // per material) also run one step per launch
             casimir_plan_options o = dflt;
             o.steps_per_launch = 1;
             cand.push_back(o);

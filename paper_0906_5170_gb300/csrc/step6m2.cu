@@ -30,19 +30,19 @@ constexpr int WARPS_M2 = 4;   // warps (strips) per CTA
 #define MAR2_R0 5
 #endif
 #ifndef MAR2_R1
-#define MAR2_R1 3
+#define MAR2_R1 4
 #endif
 #ifndef MAR2_R2
 #define MAR2_R2 4
 #endif
 #ifndef MAR2_R3
-#define MAR2_R3 3
+#define MAR2_R3 4
 #endif
 #ifndef MAR2_C0
-#define MAR2_C0 3
+#define MAR2_C0 4
 #endif
 #ifndef MAR2_C1
-#define MAR2_C1 2
+#define MAR2_C1 3
 #endif
 #ifndef MAR2_C2
 #define MAR2_C2 3
