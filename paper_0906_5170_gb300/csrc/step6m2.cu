@@ -26,6 +26,10 @@ constexpr int WARPS_M2 = 4;   // warps (strips) per CTA
 
 // resident CTAs per SM of each variant (registers without spills): real / complex fields,
 // 0 = interior, 1 = CPML, 2 = Lorentz, 3 = both
+// row steps whose inputs are staged ahead (0: register prefetch of the next row)
+#ifndef MAR2_STG
+#define MAR2_STG 1
+#endif
 #ifndef MAR2_R0
 #define MAR2_R0 5
 #endif
@@ -36,7 +40,7 @@ constexpr int WARPS_M2 = 4;   // warps (strips) per CTA
 #define MAR2_R2 4
 #endif
 #ifndef MAR2_R3
-#define MAR2_R3 4
+#define MAR2_R3 3
 #endif
 #ifndef MAR2_C0
 #define MAR2_C0 4
@@ -97,6 +101,18 @@ __device__ __forceinline__ void sty(R *__restrict__ p, int plane, unsigned NN, u
     else p[(unsigned)plane * NN + g] = v.x;
 }
 
+// Asynchronous global -> shared copy of one element (cp.async of the lane's own value): staged
+// rows keep the inputs of the next STG row steps in flight in shared memory instead of registers.
+template <typename R>
+__device__ __forceinline__ void cpa(R *sdst, const R *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // Projection of the sigma group's three components at tile row ly (entries rowptr[ly] ..
 // rowptr[ly+1], loc = ly * MARCH_W2 + lx, the component in bits 16..18, bit 19 for the weight of
 // the imaginary part): lanes 2 .. w + 1 hold the strip's columns.
@@ -135,8 +151,11 @@ struct Psi {
     Y<R, CPLX> x[2], y[2];
 };
 
-// LOR: one undamped Lorentz pole at most (P, P_prev per E component)
-template <typename R, bool CPLX, bool PML, bool LOR, int MINB>
+// LOR: one undamped Lorentz pole at most (P, P_prev per E component).
+// STG > 0: the inputs of the next STG row steps (fields, CPML psi, P) are in flight in a per-lane
+// shared-memory ring of STG + 1 slots, copied by cp.async; STG = 0: the next row's fields are
+// prefetched into registers and psi and P are loaded where they are used.
+template <typename R, bool CPLX, bool PML, bool LOR, int MINB, int STG>
 __global__ void __launch_bounds__(WARPS_M2 * 32, MINB)
 k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int ntiles,
        const int64_t *__restrict__ launch_base, int64_t launch_add)
@@ -240,6 +259,60 @@ k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
             if (iny(j)) { const unsigned g = gyi(j); sty<R, CPLX>(pyout, lo, PY, g, p.y[0]); sty<R, CPLX>(pyout, lo + 1, PY, g, p.y[1]); }
         }
     };
+
+    // staged rows: slot layout in values V of CF reals each, 32 apart per real: fields 0..5, then
+    // psi x planes 0..3 and y planes 0..3 (CPML), then P, P_prev of E_x..E_z (Lorentz)
+    constexpr int CF = CPLX ? 2 : 1;
+    constexpr int VX = 6, VY = 10, VL = PML ? 14 : 6;
+    constexpr int NV = CF * (VL + (LOR ? 6 : 0));
+    constexpr int NSLOT = STG > 0 ? STG + 1 : 1;
+    __shared__ __align__(16) R ring_s[STG > 0 ? WARPS_M2 * NSLOT * NV * 32 : 1];
+    R *const ring = ring_s + (STG > 0 ? warp * NSLOT * NV * 32 + lane : 0);
+    auto sg = [&](int sl, int v, const R *p, int plane, unsigned NN, unsigned g) {
+        R *d = ring + (sl * NV + v * CF) * 32;
+        if constexpr (CPLX) { cpa(d, p + (2u * plane) * NN + g); cpa(d + 32, p + (2u * plane + 1u) * NN + g); }
+        else cpa(d, p + (unsigned)plane * NN + g);
+    };
+    auto fv = [&](int sl, int v) -> V {
+        const R *d = ring + (sl * NV + v * CF) * 32;
+        if constexpr (CPLX) return V(d[0], d[32]);
+        else return V(d[0]);
+    };
+    auto disp = [&](int m, int k) -> bool { if constexpr (LOR) return lc[12 * np * m + 4 * k + 2] != (R)0; else return false; };
+    // psi planes lo.. of x at row jx and of y at row jy into slot values VX + lo.., VY + lo..
+    auto stage_psi = [&](int sl, int jx, int jy, int lo, int hi) {
+        if constexpr (PML) {
+            if (inx) { const unsigned g = gxi(jx); for (int q = lo; q < hi; ++q) sg(sl, VX + q, pxin, q, PX, g); }
+            if (iny(jy)) { const unsigned g = gyi(jy); for (int q = lo; q < hi; ++q) sg(sl, VY + q, pyin, q, PY, g); }
+        }
+    };
+    auto stage_lor = [&](int sl, int j, int m) {
+        if constexpr (LOR) {
+            const unsigned g = (unsigned)(j * nx + col);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (disp(m, k)) { sg(sl, VL + 2 * k, lin, k, N, g); sg(sl, VL + 2 * k + 1, lin, 3 + k, N, g); }
+        }
+    };
+    // the psi of group planes lo, lo + 1 (x at row j's column, y at row j) from slot sl
+    auto psi_slot = [&](int sl, int j, int lo) -> PS {
+        PS p;
+        if constexpr (PML) {
+            if (inx) { p.x[0] = fv(sl, VX + lo); p.x[1] = fv(sl, VX + lo + 1); }
+            if (iny(j)) { p.y[0] = fv(sl, VY + lo); p.y[1] = fv(sl, VY + lo + 1); }
+        }
+        return p;
+    };
+    auto lor_slot = [&](int sl, int m, V pp[3], V pm[3]) {
+        if constexpr (LOR) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                if (disp(m, k)) { pp[k] = fv(sl, VL + 2 * k); pm[k] = fv(sl, VL + 2 * k + 1); }
+                else { pp[k] = V(); pm[k] = V(); }
+            }
+        }
+    };
+    auto matw = [&](int row) -> int { return mat[(unsigned)(wrow(row) * nx + col)]; };
 
     // H at (wrapped) row j from E at rows j and j+1 (E_x, E_z of row j+1: exn, ezn); psi planes 2, 3
     auto updH = [&](int j, int m, const V e[3], V exn, V ezn, const V hq[3], R aa, R bb, const PS &pi, PS &po, V ho[3]) {
@@ -359,7 +432,30 @@ k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
             V en_c[3], hq_c[3];
             int mn_c;
             int jr = wrow(j0 - 1), jp = wrow(j0 - 2);   // rows r and r-1, wrapped
-            {
+            // staged rows: iteration r's slot holds E(r+1), H(r), psi and P of row r; mq[k] is the
+            // material of row r + 1 + k (the rows staged ahead need theirs for the P copies)
+            int mq[STG + 2];
+            int sl = 0, js = 0, jq = 0;   // wrapped rows r + STG (staged next) and r + STG + 3 (its material next)
+            auto stage_e = [&](int slot, int j, int m) {   // j: the staged iteration's row, wrapped
+                const int jn = j + 1 == ny ? 0 : j + 1;
+                const unsigned g = (unsigned)(j * nx + col), gn = (unsigned)(jn * nx + col);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { sg(slot, k, fin, k, N, gn); sg(slot, 3 + k, fin, 3 + k, N, g); }
+                stage_psi(slot, j, j, 0, 4);
+                stage_lor(slot, j, m);
+            };
+            if constexpr (STG > 0) {
+#pragma unroll
+                for (int k = 0; k < STG + 2; ++k) mq[k] = matw(j0 + k);
+#pragma unroll
+                for (int q = 0; q < STG; ++q) {
+                    if (j0 - 1 + q <= j0 + h) stage_e(q, wrow(j0 - 1 + q), q == 0 ? m_r : mq[q - 1]);
+                    cpa_commit();
+                }
+                mn_c = mq[0];
+                js = wrow(j0 - 1 + STG);
+                jq = wrow(j0 + STG + 2);
+            } else {
                 const int jn = jr + 1 == ny ? 0 : jr + 1;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) { en_c[k] = ldf(k, jn); hq_c[k] = ldf(3 + k, jr); }
@@ -369,18 +465,32 @@ k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                 const int jn = jr + 1 == ny ? 0 : jr + 1;
                 V en_n[3], hq_n[3];
                 int mn_n = 0;
-                if (r + 1 <= j0 + h) {   // the next iteration's inputs, loaded ahead
-                    const int jnn = jn + 1 == ny ? 0 : jn + 1;
+                PS piH, piE;
+                V p0r[3], pmr[3];
+                if constexpr (STG > 0) {
+                    if (r + STG <= j0 + h) stage_e(sl == 0 ? STG : sl - 1, js, mq[STG - 1]);
+                    cpa_commit();
+                    cpa_wait<STG>();
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) { en_n[k] = ldf(k, jnn); hq_n[k] = ldf(3 + k, jn); }
-                    mn_n = mat[(unsigned)(jnn * nx + col)];
+                    for (int k = 0; k < 3; ++k) { en_c[k] = fv(sl, k); hq_c[k] = fv(sl, 3 + k); }
+                    piH = psi_slot(sl, jr, 2);
+                    piE = psi_slot(sl, jr, 0);
+                    lor_slot(sl, m_r, p0r, pmr);
+                } else {
+                    if (r + 1 <= j0 + h) {   // the next iteration's inputs, loaded ahead
+                        const int jnn = jn + 1 == ny ? 0 : jn + 1;
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) { en_n[k] = ldf(k, jnn); hq_n[k] = ldf(3 + k, jn); }
+                        mn_n = mat[(unsigned)(jnn * nx + col)];
+                    }
+                    piH = psi_in_row(jr, 2);
+                    piE = psi_in_row(jr, 0);
+                    lor_in(jr, m_r, p0r, pmr);
                 }
-                V hA[3], eA[3], pAr[3], p0r[3];
+                V hA[3], eA[3], pAr[3];
                 PS sHA, sEA;
-                updH(jr, m_r, e0c, en_c[0], en_c[2], hq_c, (R)1, hA0, psi_in_row(jr, 2), sHA, hA);
-                V pmr[3];
-                lor_in(jr, m_r, p0r, pmr);
-                updE(jr, m_r, hA, hAm[0], hAm[2], e0c, a, bs, psi_in_row(jr, 0), sEA, p0r, pmr, firstA, pAr, eA);
+                updH(jr, m_r, e0c, en_c[0], en_c[2], hq_c, (R)1, hA0, piH, sHA, hA);
+                updE(jr, m_r, hA, hAm[0], hAm[2], e0c, a, bs, piE, sEA, p0r, pmr, firstA, pAr, eA);
                 const bool inA = r >= j0 && r < j0 + h;
                 if (inA && t.ne > 0) pA += project_row_m2<R, CPLX>(t, r - j0, w, grp, eA[0], eA[1], eA[2]);
                 if (!two) {
@@ -414,8 +524,7 @@ k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                     eAm[k] = eA[k];
                     hAm[k] = hA[k];
                     e0c[k] = en_c[k];
-                    en_c[k] = en_n[k];
-                    hq_c[k] = hq_n[k];
+                    if constexpr (STG == 0) { en_c[k] = en_n[k]; hq_c[k] = hq_n[k]; }
                     pAm[k] = pAr[k];
                     p0m[k] = p0r[k];
                 }
@@ -423,7 +532,17 @@ k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                 sEAm = sEA;
                 m_rm = m_r;
                 m_r = mn_c;
-                mn_c = mn_n;
+                if constexpr (STG > 0) {
+#pragma unroll
+                    for (int k = 0; k < STG + 1; ++k) mq[k] = mq[k + 1];
+                    mq[STG + 1] = mat[(unsigned)(jq * nx + col)];
+                    mn_c = mq[0];
+                    sl = sl == STG ? 0 : sl + 1;
+                    js = js + 1 == ny ? 0 : js + 1;
+                    jq = jq + 1 == ny ? 0 : jq + 1;
+                } else {
+                    mn_c = mn_n;
+                }
                 jp = jr;
                 jr = jn;
             }
@@ -449,7 +568,31 @@ k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
             // inputs of iteration r: the buffer's H and E at row r+1, material of row r+1
             V hn_c[3], en_c[3];
             int mn_c;
-            {
+            // staged rows: iteration r's slot holds H(r+1), E(r+1), the E-group psi and P of row r+1,
+            // the H-group psi of row r; mq[k] is the material of row r + 1 + k
+            int mq[STG + 2];
+            int sl = 0, js = 0, jq = 0;   // wrapped rows r + STG (staged next) and r + STG + 3 (its material next)
+            auto stage_m = [&](int slot, int j, int m) {   // j: the staged iteration's row, wrapped
+                const int jn = j + 1 == ny ? 0 : j + 1;
+                const unsigned gn = (unsigned)(jn * nx + col);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { sg(slot, k, fin, 3 + k, N, gn); sg(slot, 3 + k, fin, k, N, gn); }
+                stage_psi(slot, jn, jn, 0, 2);
+                stage_psi(slot, j, j, 2, 4);
+                stage_lor(slot, jn, m);
+            };
+            if constexpr (STG > 0) {
+#pragma unroll
+                for (int k = 0; k < STG + 2; ++k) mq[k] = matw(j0 + k);
+#pragma unroll
+                for (int q = 0; q < STG; ++q) {
+                    if (j0 - 1 + q <= j0 + h) stage_m(q, wrow(j0 - 1 + q), mq[q]);
+                    cpa_commit();
+                }
+                mn_c = mq[0];
+                js = wrow(j0 - 1 + STG);
+                jq = wrow(j0 + STG + 2);
+            } else {
                 const int jn = jr + 1 == ny ? 0 : jr + 1;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) { hn_c[k] = ldf(3 + k, jn); en_c[k] = ldf(k, jn); }
@@ -459,17 +602,30 @@ k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                 const int jn = jr + 1 == ny ? 0 : jr + 1;
                 V hn_n[3], en_n[3];
                 int mn_n = 0;
-                if (r + 1 <= j0 + h) {
-                    const int jnn = jn + 1 == ny ? 0 : jn + 1;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) { hn_n[k] = ldf(3 + k, jnn); en_n[k] = ldf(k, jnn); }
-                    mn_n = mat[(unsigned)(jnn * nx + col)];
-                }
                 V eAn[3], hA[3], pAn[3], p0n[3], pmn[3];
-                PS sEAn, sHA;
-                lor_in(jn, mn_c, p0n, pmn);
-                updE(jn, mn_c, hn_c, h0c[0], h0c[2], en_c, (R)1, hA0, psi_in_row(jn, 0), sEAn, p0n, pmn, false, pAn, eAn);   // E_A(r+1)
-                updH(jr, m_r, eAc, eAn[0], eAn[2], h0c, a, bs, psi_in_row(jr, 2), sHA, hA);          // H_A(r)
+                PS sEAn, sHA, piE, piH;
+                if constexpr (STG > 0) {
+                    if (r + STG <= j0 + h) stage_m(sl == 0 ? STG : sl - 1, js, mq[STG]);
+                    cpa_commit();
+                    cpa_wait<STG>();
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) { hn_c[k] = fv(sl, k); en_c[k] = fv(sl, 3 + k); }
+                    piE = psi_slot(sl, jn, 0);
+                    piH = psi_slot(sl, jr, 2);
+                    lor_slot(sl, mn_c, p0n, pmn);
+                } else {
+                    if (r + 1 <= j0 + h) {
+                        const int jnn = jn + 1 == ny ? 0 : jn + 1;
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) { hn_n[k] = ldf(3 + k, jnn); en_n[k] = ldf(k, jnn); }
+                        mn_n = mat[(unsigned)(jnn * nx + col)];
+                    }
+                    piE = psi_in_row(jn, 0);
+                    piH = psi_in_row(jr, 2);
+                    lor_in(jn, mn_c, p0n, pmn);
+                }
+                updE(jn, mn_c, hn_c, h0c[0], h0c[2], en_c, (R)1, hA0, piE, sEAn, p0n, pmn, false, pAn, eAn);   // E_A(r+1)
+                updH(jr, m_r, eAc, eAn[0], eAn[2], h0c, a, bs, piH, sHA, hA);          // H_A(r)
                 const bool inA = r >= j0 && r < j0 + h;
                 if (inA && t.ne > 0) pA += project_row_m2<R, CPLX>(t, r - j0, w, grp, hA[0], hA[1], hA[2]);
                 if (!two) {
@@ -506,8 +662,7 @@ k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                     hAm[k] = hA[k];
                     eAc[k] = eAn[k];
                     h0c[k] = hn_c[k];
-                    hn_c[k] = hn_n[k];
-                    en_c[k] = en_n[k];
+                    if constexpr (STG == 0) { hn_c[k] = hn_n[k]; en_c[k] = en_n[k]; }
                     pAc[k] = pAn[k];
                     p0c[k] = p0n[k];
                 }
@@ -515,7 +670,17 @@ k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                 sHAm = sHA;
                 m_rm = m_r;
                 m_r = mn_c;
-                mn_c = mn_n;
+                if constexpr (STG > 0) {
+#pragma unroll
+                    for (int k = 0; k < STG + 1; ++k) mq[k] = mq[k + 1];
+                    mq[STG + 1] = mat[(unsigned)(jq * nx + col)];
+                    mn_c = mq[0];
+                    sl = sl == STG ? 0 : sl + 1;
+                    js = js + 1 == ny ? 0 : js + 1;
+                    jq = jq + 1 == ny ? 0 : jq + 1;
+                } else {
+                    mn_c = mn_n;
+                }
                 jp = jr;
                 jr = jn;
             }
@@ -539,7 +704,10 @@ k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
 template <typename R, bool CPLX, bool PML, bool LOR, int MINB>
 void launch_one(const DevSim6 *sims, const DevTile2 *tiles, int ntiles, const int64_t *lb, int64_t la, cudaStream_t st)
 {
-    k_mar2<R, CPLX, PML, LOR, MINB><<<(ntiles + WARPS_M2 - 1) / WARPS_M2, WARPS_M2 * 32, 0, st>>>(sims, tiles, ntiles, lb, la);
+    // MAR2_STG staged rows while the ring stays within 48 KB of static shared memory per CTA
+    constexpr int NV = (CPLX ? 2 : 1) * (6 + (PML ? 8 : 0) + (LOR ? 6 : 0));
+    constexpr int STG = MAR2_STG == 0 ? 0 : (WARPS_M2 * (MAR2_STG + 1) * NV * 32 * 4 <= 48 * 1024 ? MAR2_STG : 1);
+    k_mar2<R, CPLX, PML, LOR, MINB, STG><<<(ntiles + WARPS_M2 - 1) / WARPS_M2, WARPS_M2 * 32, 0, st>>>(sims, tiles, ntiles, lb, la);
 }
 
 }  // namespace
