@@ -3,7 +3,9 @@
 // harmonic and polarisation family (every face and source component) -- with
 // the field updates of each time step launched for that run alone, a separate
 // projection launch per step, and no CUDA graph.  The field updates are the
-// same kernels the batched path uses, so the two differ only in scheduling.
+// one-step kernels (where the batched path fuses two or three steps into one
+// launch, it runs the fused kernels of the same update), so the two differ in
+// scheduling, not in arithmetic.
 #include <cuda_runtime.h>
 
 #include <algorithm>
