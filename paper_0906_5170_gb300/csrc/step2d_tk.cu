@@ -14,7 +14,8 @@
 // give the x neighbours, carried registers the y neighbours.  Every stage's sigma group is
 // projected on the fly (row-sorted entries, shuffle hand-over from the lane holding the
 // entry's column).  Fields read buffer (L-1)&1 and write buffer L&1; a launch that holds
-// fewer than K steps (the end of the run) stores its last real stage.
+// fewer than K steps (the end of the run) stores every real stage as it passes a row, so the
+// last real stage's values remain.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -27,6 +28,11 @@ template <typename R>
 __device__ __forceinline__ R kdn(R v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 template <typename R>
 __device__ __forceinline__ R kup(R v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+
+template <bool B>
+struct Flag {
+    static constexpr bool value = B;
+};
 
 // any row index to [0, n)
 __device__ __forceinline__ int wrapk(int i, int n)
@@ -115,166 +121,173 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
 #pragma unroll
     for (int q = 0; q < K; ++q) p[q] = 0.0;
 
-    if (w > 0) {
-        const int j0 = t.j0;
-        // rows of stage 0: r = -(K-1) .. h + K - 2 (relative to j0)
-        const int r_first = -(K - 1), r_last = h + K - 2;
-        if (S.second_u) {
-            // ---- sigma on u: v first.  Stage q at row rho = r - q:
-            //   vx_q(rho) = vx_{q-1}(rho) - h cvx (u_{q-1}(rho+1) - u_{q-1}(rho))
-            //   vy_q(rho) = vy_{q-1}(rho) + h cvy (u_{q-1}(x+1, rho) - u_{q-1}(rho))
-            //   u_q(rho)  = a u_{q-1}(rho) + bf cu ((vy_q(rho) - vy_q(x-1, rho)) - (vx_q(rho) - vx_q(rho-1)))
-            // with q - 1 = -1 the buffer's values.  Carried: uo/vxo/vyo[q] = stage q at its previous row.
-            R uo[K], vxo[K], vyo[K];
-            int mh[K];   // material of row r - q
-#pragma unroll
-            for (int q = 0; q < K; ++q) { uo[q] = (R)0; vxo[q] = (R)0; vyo[q] = (R)0; mh[q] = 0; }
-            R u_cur;     // the buffer's u at row r
-            {
-                const unsigned ga = (unsigned)(wrapk(j0 - K, ny) * nx + col), gb = (unsigned)(wrapk(j0 - K + 1, ny) * nx + col);
-                u_cur = su[gb];
-                vxo[0] = svx[ga] - hf0 * coef[3 * mat[ga] + 1] * (u_cur - su[ga]);   // vx of stage 0 at row -K
-            }
-            int jl = wrapk(j0 + r_first, ny);   // the next row to load, wrapped (advanced one row at a time)
-            for (int rb = r_first; rb <= r_last; rb += ROWS) {
-                R un[ROWS], vxl[ROWS], vyl[ROWS];
-                int mt[ROWS];
-#pragma unroll
-                for (int i = 0; i < ROWS; ++i) {
-                    const int r = rb + i;
-                    if (r <= r_last) {
-                        const int jn = jl + 1 == ny ? 0 : jl + 1;
-                        const unsigned g = (unsigned)(jl * nx + col);
-                        un[i] = su[(unsigned)(jn * nx + col)];
-                        vxl[i] = svx[g];
-                        vyl[i] = svy[g];
-                        mt[i] = mat[g];
-                        jl = jn;
-                    }
+    // the stage whose values are stored is K - 1 on every launch but a run's last one (fewer real
+    // steps); a compile-time FULL keeps the stored stage static, so the stage values stay in registers
+    auto march = [&](auto full_tag) {
+        constexpr bool FULL = decltype(full_tag)::value;
+        if (w > 0) {
+            const int j0 = t.j0;
+            // rows of stage 0: r = -(K-1) .. h + K - 2 (relative to j0)
+            const int r_first = -(K - 1), r_last = h + K - 2;
+            if (S.second_u) {
+                // ---- sigma on u: v first.  Stage q at row rho = r - q:
+                //   vx_q(rho) = vx_{q-1}(rho) - h cvx (u_{q-1}(rho+1) - u_{q-1}(rho))
+                //   vy_q(rho) = vy_{q-1}(rho) + h cvy (u_{q-1}(x+1, rho) - u_{q-1}(rho))
+                //   u_q(rho)  = a u_{q-1}(rho) + bf cu ((vy_q(rho) - vy_q(x-1, rho)) - (vx_q(rho) - vx_q(rho-1)))
+                // with q - 1 = -1 the buffer's values.  Carried: uo/vxo/vyo[q] = stage q at its previous row.
+                R uo[K], vxo[K], vyo[K];
+                int mh[K];   // material of row r - q
+    #pragma unroll
+                for (int q = 0; q < K; ++q) { uo[q] = (R)0; vxo[q] = (R)0; vyo[q] = (R)0; mh[q] = 0; }
+                R u_cur;     // the buffer's u at row r
+                {
+                    const unsigned ga = (unsigned)(wrapk(j0 - K, ny) * nx + col), gb = (unsigned)(wrapk(j0 - K + 1, ny) * nx + col);
+                    u_cur = su[gb];
+                    vxo[0] = svx[ga] - hf0 * coef[3 * mat[ga] + 1] * (u_cur - su[ga]);   // vx of stage 0 at row -K
                 }
-#pragma unroll
-                for (int i = 0; i < ROWS; ++i) {
-                    const int r = rb + i;
-                    if (r > r_last) break;
-#pragma unroll
-                    for (int q = K - 1; q > 0; --q) mh[q] = mh[q - 1];
-                    mh[0] = mt[i];
-                    R un_[K], vxn[K], vyn[K];
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        const int m = mh[q];
-                        // hf c for the v group (hf0 c at stage 0 of the first launch), bf c_u
-                        const R scale = q == 0 && n1 == 1 ? (R)0.5 : (R)1;
-                        const R hcvx = ctab[m][1] * scale, hcvy = ctab[m][2] * scale, bcu = ctab[m][0];
-                        // inputs: stage q-1 at rows rho (carried) and rho + 1 (this iteration)
-                        const R uin = q == 0 ? u_cur : uo[q - 1];
-                        const R uin1 = q == 0 ? un[i] : un_[q - 1];
-                        const R vxin = q == 0 ? vxl[i] : vxo[q - 1];
-                        const R vyin = q == 0 ? vyl[i] : vyo[q - 1];
-                        vxn[q] = vxin - hcvx * (uin1 - uin);
-                        vyn[q] = vyin + hcvy * (kdn(uin) - uin);
-                        un_[q] = a * uin + bcu * ((vyn[q] - kup(vyn[q])) - (vxn[q] - vxo[q]));
-                        const int rho = r - q;
-                        if (q < ks && rho >= 0 && rho < h) {
-                            if (q == ks - 1 && store) {
-                                const unsigned g = (unsigned)((j0 + rho) * nx + col);
-                                du[g] = un_[q];
-                                dvx[g] = vxn[q];
-                                dvy[g] = vyn[q];
-                            }
-                            if (t.ne > 0) p[q] += project_row_k<R, TX, K>(t, rho, strip_lo, w, un_[q], vxn[q], vyn[q]);
+                int jl = wrapk(j0 + r_first, ny);   // the next row to load, wrapped (advanced one row at a time)
+                for (int rb = r_first; rb <= r_last; rb += ROWS) {
+                    R un[ROWS], vxl[ROWS], vyl[ROWS];
+                    int mt[ROWS];
+    #pragma unroll
+                    for (int i = 0; i < ROWS; ++i) {
+                        const int r = rb + i;
+                        if (r <= r_last) {
+                            const int jn = jl + 1 == ny ? 0 : jl + 1;
+                            const unsigned g = (unsigned)(jl * nx + col);
+                            un[i] = su[(unsigned)(jn * nx + col)];
+                            vxl[i] = svx[g];
+                            vyl[i] = svy[g];
+                            mt[i] = mat[g];
+                            jl = jn;
                         }
                     }
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        uo[q] = un_[q];
-                        vxo[q] = vxn[q];
-                        vyo[q] = vyn[q];
-                    }
-                    u_cur = un[i];
-                }
-            }
-        } else {
-            // ---- sigma on v: u first.  Stage q at iteration r: u at row r - q + 1, then v at row r - q:
-            //   u_q(rho+1) = u_{q-1}(rho+1) + h cu ((vy_{q-1}(rho+1) - vy_{q-1}(x-1, rho+1)) - (vx_{q-1}(rho+1) - vx_{q-1}(rho)))
-            //   vx_q(rho) = a vx_{q-1}(rho) - bf cvx (u_q(rho+1) - u_q(rho))
-            //   vy_q(rho) = a vy_{q-1}(rho) + bf cvy (u_q(x+1, rho) - u_q(rho))
-            // Carried: uc[q] = u_q at row r - q (the row its v is made for), vxo/vyo[q] = v_q at row r - q - 1.
-            R uc[K], vxo[K], vyo[K];
-            int mh[K + 1];   // material of row r + 1 - i
-#pragma unroll
-            for (int q = 0; q < K; ++q) { uc[q] = (R)0; vxo[q] = (R)0; vyo[q] = (R)0; }
-#pragma unroll
-            for (int q = 0; q <= K; ++q) mh[q] = 0;
-            R vx_c, vy_c;   // the buffer's v at row r
-            {
-                const unsigned ga = (unsigned)(wrapk(j0 - K, ny) * nx + col), gb = (unsigned)(wrapk(j0 - K + 1, ny) * nx + col);
-                vx_c = svx[gb];
-                vy_c = svy[gb];
-                const int mb = mat[gb];
-                mh[0] = mb;
-                uc[0] = su[gb] + hf0 * coef[3 * mb] * ((vy_c - kup(vy_c)) - (vx_c - svx[ga]));   // u of stage 0 at row -(K-1)
-            }
-            int jl = wrapk(j0 + r_first + 1, ny);   // the next row to load, wrapped
-            for (int rb = r_first; rb <= r_last; rb += ROWS) {
-                R un[ROWS], vxl[ROWS], vyl[ROWS];
-                int mt[ROWS];
-#pragma unroll
-                for (int i = 0; i < ROWS; ++i) {
-                    const int r = rb + i;
-                    if (r <= r_last) {
-                        const unsigned g = (unsigned)(jl * nx + col);
-                        jl = jl + 1 == ny ? 0 : jl + 1;
-                        un[i] = su[g];
-                        vxl[i] = svx[g];
-                        vyl[i] = svy[g];
-                        mt[i] = mat[g];
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < ROWS; ++i) {
-                    const int r = rb + i;
-                    if (r > r_last) break;
-#pragma unroll
-                    for (int q = K; q > 0; --q) mh[q] = mh[q - 1];
-                    mh[0] = mt[i];
-                    R unw[K], vxn[K], vyn[K];
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        const R scale = q == 0 && n1 == 1 ? (R)0.5 : (R)1;
-                        // u at row r - q + 1 from stage q-1 at that row (u carried, v of this iteration) and v at row r - q
-                        const R uin = q == 0 ? un[i] : uc[q - 1];
-                        const R vxa = q == 0 ? vxl[i] : vxn[q - 1];
-                        const R vya = q == 0 ? vyl[i] : vyn[q - 1];
-                        const R vxb = q == 0 ? vx_c : vxo[q - 1];
-                        const R vyb = q == 0 ? vy_c : vyo[q - 1];
-                        const int mu = mh[q], mv = mh[q + 1];
-                        unw[q] = uin + ctab[mu][0] * scale * ((vya - kup(vya)) - (vxa - vxb));
-                        vxn[q] = a * vxb - ctab[mv][1] * (unw[q] - uc[q]);
-                        vyn[q] = a * vyb + ctab[mv][2] * (kdn(uc[q]) - uc[q]);
-                        const int rho = r - q;
-                        if (q < ks && rho >= 0 && rho < h) {
-                            if (q == ks - 1 && store) {
-                                const unsigned g = (unsigned)((j0 + rho) * nx + col);
-                                du[g] = uc[q];
-                                dvx[g] = vxn[q];
-                                dvy[g] = vyn[q];
+    #pragma unroll
+                    for (int i = 0; i < ROWS; ++i) {
+                        const int r = rb + i;
+                        if (r > r_last) break;
+    #pragma unroll
+                        for (int q = K - 1; q > 0; --q) mh[q] = mh[q - 1];
+                        mh[0] = mt[i];
+                        R un_[K], vxn[K], vyn[K];
+    #pragma unroll
+                        for (int q = 0; q < K; ++q) {
+                            const int m = mh[q];
+                            // hf c for the v group (hf0 c at stage 0 of the first launch), bf c_u
+                            const R scale = q == 0 && n1 == 1 ? (R)0.5 : (R)1;
+                            const R hcvx = ctab[m][1] * scale, hcvy = ctab[m][2] * scale, bcu = ctab[m][0];
+                            // inputs: stage q-1 at rows rho (carried) and rho + 1 (this iteration)
+                            const R uin = q == 0 ? u_cur : uo[q - 1];
+                            const R uin1 = q == 0 ? un[i] : un_[q - 1];
+                            const R vxin = q == 0 ? vxl[i] : vxo[q - 1];
+                            const R vyin = q == 0 ? vyl[i] : vyo[q - 1];
+                            vxn[q] = vxin - hcvx * (uin1 - uin);
+                            vyn[q] = vyin + hcvy * (kdn(uin) - uin);
+                            un_[q] = a * uin + bcu * ((vyn[q] - kup(vyn[q])) - (vxn[q] - vxo[q]));
+                            const int rho = r - q;
+                            if ((FULL || q < ks) && rho >= 0 && rho < h) {
+                                if ((FULL ? q == K - 1 : q < ks) && store) {
+                                    const unsigned g = (unsigned)((j0 + rho) * nx + col);
+                                    du[g] = un_[q];
+                                    dvx[g] = vxn[q];
+                                    dvy[g] = vyn[q];
+                                }
+                                if (t.ne > 0) p[q] += project_row_k<R, TX, K>(t, rho, strip_lo, w, un_[q], vxn[q], vyn[q]);
                             }
-                            if (t.ne > 0) p[q] += project_row_k<R, TX, K>(t, rho, strip_lo, w, uc[q], vxn[q], vyn[q]);
+                        }
+    #pragma unroll
+                        for (int q = 0; q < K; ++q) {
+                            uo[q] = un_[q];
+                            vxo[q] = vxn[q];
+                            vyo[q] = vyn[q];
+                        }
+                        u_cur = un[i];
+                    }
+                }
+            } else {
+                // ---- sigma on v: u first.  Stage q at iteration r: u at row r - q + 1, then v at row r - q:
+                //   u_q(rho+1) = u_{q-1}(rho+1) + h cu ((vy_{q-1}(rho+1) - vy_{q-1}(x-1, rho+1)) - (vx_{q-1}(rho+1) - vx_{q-1}(rho)))
+                //   vx_q(rho) = a vx_{q-1}(rho) - bf cvx (u_q(rho+1) - u_q(rho))
+                //   vy_q(rho) = a vy_{q-1}(rho) + bf cvy (u_q(x+1, rho) - u_q(rho))
+                // Carried: uc[q] = u_q at row r - q (the row its v is made for), vxo/vyo[q] = v_q at row r - q - 1.
+                R uc[K], vxo[K], vyo[K];
+                int mh[K + 1];   // material of row r + 1 - i
+    #pragma unroll
+                for (int q = 0; q < K; ++q) { uc[q] = (R)0; vxo[q] = (R)0; vyo[q] = (R)0; }
+    #pragma unroll
+                for (int q = 0; q <= K; ++q) mh[q] = 0;
+                R vx_c, vy_c;   // the buffer's v at row r
+                {
+                    const unsigned ga = (unsigned)(wrapk(j0 - K, ny) * nx + col), gb = (unsigned)(wrapk(j0 - K + 1, ny) * nx + col);
+                    vx_c = svx[gb];
+                    vy_c = svy[gb];
+                    const int mb = mat[gb];
+                    mh[0] = mb;
+                    uc[0] = su[gb] + hf0 * coef[3 * mb] * ((vy_c - kup(vy_c)) - (vx_c - svx[ga]));   // u of stage 0 at row -(K-1)
+                }
+                int jl = wrapk(j0 + r_first + 1, ny);   // the next row to load, wrapped
+                for (int rb = r_first; rb <= r_last; rb += ROWS) {
+                    R un[ROWS], vxl[ROWS], vyl[ROWS];
+                    int mt[ROWS];
+    #pragma unroll
+                    for (int i = 0; i < ROWS; ++i) {
+                        const int r = rb + i;
+                        if (r <= r_last) {
+                            const unsigned g = (unsigned)(jl * nx + col);
+                            jl = jl + 1 == ny ? 0 : jl + 1;
+                            un[i] = su[g];
+                            vxl[i] = svx[g];
+                            vyl[i] = svy[g];
+                            mt[i] = mat[g];
                         }
                     }
-#pragma unroll
-                    for (int q = 0; q < K; ++q) {
-                        uc[q] = unw[q];
-                        vxo[q] = vxn[q];
-                        vyo[q] = vyn[q];
+    #pragma unroll
+                    for (int i = 0; i < ROWS; ++i) {
+                        const int r = rb + i;
+                        if (r > r_last) break;
+    #pragma unroll
+                        for (int q = K; q > 0; --q) mh[q] = mh[q - 1];
+                        mh[0] = mt[i];
+                        R unw[K], vxn[K], vyn[K];
+    #pragma unroll
+                        for (int q = 0; q < K; ++q) {
+                            const R scale = q == 0 && n1 == 1 ? (R)0.5 : (R)1;
+                            // u at row r - q + 1 from stage q-1 at that row (u carried, v of this iteration) and v at row r - q
+                            const R uin = q == 0 ? un[i] : uc[q - 1];
+                            const R vxa = q == 0 ? vxl[i] : vxn[q - 1];
+                            const R vya = q == 0 ? vyl[i] : vyn[q - 1];
+                            const R vxb = q == 0 ? vx_c : vxo[q - 1];
+                            const R vyb = q == 0 ? vy_c : vyo[q - 1];
+                            const int mu = mh[q], mv = mh[q + 1];
+                            unw[q] = uin + ctab[mu][0] * scale * ((vya - kup(vya)) - (vxa - vxb));
+                            vxn[q] = a * vxb - ctab[mv][1] * (unw[q] - uc[q]);
+                            vyn[q] = a * vyb + ctab[mv][2] * (kdn(uc[q]) - uc[q]);
+                            const int rho = r - q;
+                            if ((FULL || q < ks) && rho >= 0 && rho < h) {
+                                if ((FULL ? q == K - 1 : q < ks) && store) {
+                                    const unsigned g = (unsigned)((j0 + rho) * nx + col);
+                                    du[g] = uc[q];
+                                    dvx[g] = vxn[q];
+                                    dvy[g] = vyn[q];
+                                }
+                                if (t.ne > 0) p[q] += project_row_k<R, TX, K>(t, rho, strip_lo, w, uc[q], vxn[q], vyn[q]);
+                            }
+                        }
+    #pragma unroll
+                        for (int q = 0; q < K; ++q) {
+                            uc[q] = unw[q];
+                            vxo[q] = vxn[q];
+                            vyo[q] = vyn[q];
+                        }
+                        vx_c = vxl[i];
+                        vy_c = vyl[i];
                     }
-                    vx_c = vxl[i];
-                    vy_c = vyl[i];
                 }
             }
         }
-    }
+    };
+    if (ks == K) march(Flag<true>{});
+    else march(Flag<false>{});
 
     if (t.ne > 0) {
 #pragma unroll
