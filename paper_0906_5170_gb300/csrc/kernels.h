@@ -6,7 +6,10 @@
 namespace cas {
 
 constexpr int TILE_X = 120;   // four warp strips of 30 interior columns
-constexpr int TILE_Y = 32;
+#ifndef CAS_TILE_Y
+#define CAS_TILE_Y 32
+#endif
+constexpr int TILE_Y = CAS_TILE_Y;   // rows of a 2D TM/TE tile
 
 // One simulation of a TM-form 2D kernel (TM, or TE on the dual lattice).
 // Fields: two buffers (ping-pong by step parity) of three arrays u, vx, vy,

@@ -313,6 +313,14 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
 
 }  // namespace
 
+// FP32: rows whose loads are in flight together, resident CTAs per SM asked of the register allocator
+#ifndef STEP2D_TK_ROWS
+#define STEP2D_TK_ROWS 3
+#endif
+#ifndef STEP2D_TK_MINB
+#define STEP2D_TK_MINB 8
+#endif
+
 void launch_step2d_t3(int fp64, const DevSim2D *sims, const DevTile2 *tiles, int ntiles,
                       const int64_t *launch_base, int64_t launch_add, cudaStream_t st)
 {
@@ -320,7 +328,7 @@ void launch_step2d_t3(int fp64, const DevSim2D *sims, const DevTile2 *tiles, int
     if (fp64)
         k_step2d_tk<double, 3, 3, 4><<<ntiles, WARPS_K * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
     else
-        k_step2d_tk<float, 3, 3, 7><<<ntiles, WARPS_K * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
+        k_step2d_tk<float, 3, STEP2D_TK_ROWS, STEP2D_TK_MINB><<<ntiles, WARPS_K * 32, 0, st>>>(sims, tiles, launch_base, launch_add);
 }
 
 }  // namespace cas
