@@ -108,8 +108,13 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
     const R a = (R)S.a, bf = (R)S.bf;
     // per material, the coefficients times their step factor: the first group's with hf, the
     // sigma group's with bf ((hf c) d is the (hf * c) * d of the unfused kernels bit for bit; at
-    // stage 0 of the first launch the first group takes hf0 c = (hf c) / 2, exactly)
-    __shared__ R ctab[256][3];
+    // stage 0 of the first launch the first group takes hf0 c = (hf c) / 2, exactly), padded to
+    // four values so that one 16-byte shared load fetches a material's three coefficients
+    struct alignas(4 * sizeof(R)) C4 {
+        R c[4];
+    };
+    __shared__ C4 ctab4[256];
+    R (*ctab)[4] = reinterpret_cast<R (*)[4]>(ctab4);
     for (int i = threadIdx.x; i < S.nmat; i += blockDim.x) {
         const R cu = coef[3 * i], cvx = coef[3 * i + 1], cvy = coef[3 * i + 2];
         ctab[i][0] = (S.second_u ? bf : hf) * cu;
@@ -121,10 +126,14 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
 #pragma unroll
     for (int q = 0; q < K; ++q) p[q] = 0.0;
 
-    // the stage whose values are stored is K - 1 on every launch but a run's last one (fewer real
-    // steps); a compile-time FULL keeps the stored stage static, so the stage values stay in registers
-    auto march = [&](auto full_tag) {
-        constexpr bool FULL = decltype(full_tag)::value;
+    // FAST: a launch of K real steps that is not the run's first (the stored stage is K - 1 and no
+    // coefficient is halved); a compile-time stored stage keeps the stage values in registers (a
+    // run-time one made the compiler index them in local memory).  PROJ: the tile holds entries
+    // of the surface functional.  The general path (the run's first and last launches) stores every
+    // real stage as it passes a row and halves the first group's coefficients at stage 0 of step 1.
+    auto march = [&](auto fast_tag, auto proj_tag) {
+        constexpr bool FULL = decltype(fast_tag)::value;
+        constexpr bool PROJ = decltype(proj_tag)::value;
         if (w > 0) {
             const int j0 = t.j0;
             // rows of stage 0: r = -(K-1) .. h + K - 2 (relative to j0)
@@ -174,8 +183,9 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                         for (int q = 0; q < K; ++q) {
                             const int m = mh[q];
                             // hf c for the v group (hf0 c at stage 0 of the first launch), bf c_u
-                            const R scale = q == 0 && n1 == 1 ? (R)0.5 : (R)1;
-                            const R hcvx = ctab[m][1] * scale, hcvy = ctab[m][2] * scale, bcu = ctab[m][0];
+                            const R scale = !FULL && q == 0 && n1 == 1 ? (R)0.5 : (R)1;
+                            const C4 cm = ctab4[m];
+                            const R hcvx = cm.c[1] * scale, hcvy = cm.c[2] * scale, bcu = cm.c[0];
                             // inputs: stage q-1 at rows rho (carried) and rho + 1 (this iteration)
                             const R uin = q == 0 ? u_cur : uo[q - 1];
                             const R uin1 = q == 0 ? un[i] : un_[q - 1];
@@ -192,7 +202,7 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                                     dvx[g] = vxn[q];
                                     dvy[g] = vyn[q];
                                 }
-                                if (t.ne > 0) p[q] += project_row_k<R, TX, K>(t, rho, strip_lo, w, un_[q], vxn[q], vyn[q]);
+                                if (PROJ && t.ne > 0) p[q] += project_row_k<R, TX, K>(t, rho, strip_lo, w, un_[q], vxn[q], vyn[q]);
                             }
                         }
     #pragma unroll
@@ -251,7 +261,7 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                         R unw[K], vxn[K], vyn[K];
     #pragma unroll
                         for (int q = 0; q < K; ++q) {
-                            const R scale = q == 0 && n1 == 1 ? (R)0.5 : (R)1;
+                            const R scale = !FULL && q == 0 && n1 == 1 ? (R)0.5 : (R)1;
                             // u at row r - q + 1 from stage q-1 at that row (u carried, v of this iteration) and v at row r - q
                             const R uin = q == 0 ? un[i] : uc[q - 1];
                             const R vxa = q == 0 ? vxl[i] : vxn[q - 1];
@@ -259,9 +269,10 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                             const R vxb = q == 0 ? vx_c : vxo[q - 1];
                             const R vyb = q == 0 ? vy_c : vyo[q - 1];
                             const int mu = mh[q], mv = mh[q + 1];
-                            unw[q] = uin + ctab[mu][0] * scale * ((vya - kup(vya)) - (vxa - vxb));
-                            vxn[q] = a * vxb - ctab[mv][1] * (unw[q] - uc[q]);
-                            vyn[q] = a * vyb + ctab[mv][2] * (kdn(uc[q]) - uc[q]);
+                            const C4 cmv = ctab4[mv];
+                            unw[q] = uin + ctab4[mu].c[0] * scale * ((vya - kup(vya)) - (vxa - vxb));
+                            vxn[q] = a * vxb - cmv.c[1] * (unw[q] - uc[q]);
+                            vyn[q] = a * vyb + cmv.c[2] * (kdn(uc[q]) - uc[q]);
                             const int rho = r - q;
                             if ((FULL || q < ks) && rho >= 0 && rho < h) {
                                 if ((FULL ? q == K - 1 : q < ks) && store) {
@@ -270,7 +281,7 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                                     dvx[g] = vxn[q];
                                     dvy[g] = vyn[q];
                                 }
-                                if (t.ne > 0) p[q] += project_row_k<R, TX, K>(t, rho, strip_lo, w, uc[q], vxn[q], vyn[q]);
+                                if (PROJ && t.ne > 0) p[q] += project_row_k<R, TX, K>(t, rho, strip_lo, w, uc[q], vxn[q], vyn[q]);
                             }
                         }
     #pragma unroll
@@ -286,8 +297,12 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
             }
         }
     };
-    if (ks == K) march(Flag<true>{});
-    else march(Flag<false>{});
+    if (ks == K && n1 != 1) {
+        if (t.ne > 0) march(Flag<true>{}, Flag<true>{});
+        else march(Flag<true>{}, Flag<false>{});
+    } else {
+        march(Flag<false>{}, Flag<true>{});
+    }
 
     if (t.ne > 0) {
 #pragma unroll
