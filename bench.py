@@ -33,8 +33,8 @@ sys.path.insert(0, ROOT)
 # Each entry records the kernel source it was captured from and that file's SHA-256 prefix at capture time:
 # when the source has changed since, the bench reports the traffic as null (stale) instead of a wrong figure.
 DRAM_BYTES_PER_CELL_LAUNCH = {
-    "k_step2d_tk<float, 3>": {"bytes_per_cell": (208.469e6 + 161.741e6) / 16998400,
-                              "source": "paper_0906_5170_gb300/csrc/step2d_tk.cu", "sha256_16": "f774c2d017264bfe",
+    "k_step2d_tk<float, 3>": {"bytes_per_cell": (211.063e6 + 162.221e6) / 16998400,
+                              "source": "paper_0906_5170_gb300/csrc/step2d_tk.cu", "sha256_16": "78d8356d7697ee99",
                               "profile": "profiles/k_step2d_tk_piston_sweep.md"},
 }
 

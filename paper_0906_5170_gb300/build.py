@@ -30,7 +30,7 @@ def _nvcc():
 
 def sources():
     return [os.path.join(CSRC, f) for f in CU + CXX] + [
-        os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")] + [os.path.join(ROOT, "include", "casimir.h")]
+        os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] + [os.path.join(ROOT, "include", "casimir.h")]
 
 
 def up_to_date():

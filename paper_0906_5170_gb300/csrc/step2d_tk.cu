@@ -122,9 +122,6 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
         ctab[i][2] = (S.second_u ? hf : bf) * cvy;
     }
     __syncthreads();
-    double p[K];
-#pragma unroll
-    for (int q = 0; q < K; ++q) p[q] = 0.0;
 
     // FAST: a launch of K real steps that is not the run's first (the stored stage is K - 1 and no
     // coefficient is halved); a compile-time stored stage keeps the stage values in registers (a
@@ -134,6 +131,11 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
     auto march = [&](auto fast_tag, auto proj_tag) {
         constexpr bool FULL = decltype(fast_tag)::value;
         constexpr bool PROJ = decltype(proj_tag)::value;
+        // the projection's partial sums live in the bodies that project (kept live through a body
+        // that does not, they cost it registers)
+        double p[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) p[q] = 0.0;
         if (w > 0) {
             const int j0 = t.j0;
             // rows of stage 0: r = -(K-1) .. h + K - 2 (relative to j0)
@@ -296,6 +298,27 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
                 }
             }
         }
+        // every warp of the CTA (one tile) runs the same body, so the barrier is uniform
+        if (PROJ && t.ne > 0) {
+    #pragma unroll
+            for (int q = 0; q < K; ++q) {
+                for (int o = 16; o > 0; o >>= 1) p[q] += __shfl_down_sync(0xffffffffu, p[q], o);
+                if (lane == 0) red[q][warp] = p[q];
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double c = 0.0, ct = 0.0;
+                for (int q = 0; q < ks; ++q) {
+                    double s = 0.0;
+                    for (int v = 0; v < WARPS_K; ++v) s += red[q][v];
+                    const double cq = S.gw[n1 - 1 + q] * s;
+                    c += cq;
+                    if (n1 + q > S.tail_from) ct += cq;
+                }
+                atomicAdd(S.acc, c);
+                if (ct != 0.0) atomicAdd(S.tail, ct);
+            }
+        }
     };
     if (ks == K && n1 != 1) {
         if (t.ne > 0) march(Flag<true>{}, Flag<true>{});
@@ -304,26 +327,6 @@ k_step2d_tk(const DevSim2D *__restrict__ sims, const DevTile2 *__restrict__ tile
         march(Flag<false>{}, Flag<true>{});
     }
 
-    if (t.ne > 0) {
-#pragma unroll
-        for (int q = 0; q < K; ++q) {
-            for (int o = 16; o > 0; o >>= 1) p[q] += __shfl_down_sync(0xffffffffu, p[q], o);
-            if (lane == 0) red[q][warp] = p[q];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double c = 0.0, ct = 0.0;
-            for (int q = 0; q < ks; ++q) {
-                double s = 0.0;
-                for (int v = 0; v < WARPS_K; ++v) s += red[q][v];
-                const double cq = S.gw[n1 - 1 + q] * s;
-                c += cq;
-                if (n1 + q > S.tail_from) ct += cq;
-            }
-            atomicAdd(S.acc, c);
-            if (ct != 0.0) atomicAdd(S.tail, ct);
-        }
-    }
 }
 
 }  // namespace
