@@ -24,6 +24,11 @@ namespace {
 
 constexpr int WARPS_M2 = 4;   // warps (strips) per CTA
 
+template <bool B>
+struct Flag {
+    static constexpr bool value = B;
+};
+
 // resident CTAs per SM of each variant (registers without spills): real / complex fields,
 // 0 = interior, 1 = CPML, 2 = Lorentz, 3 = both
 // row steps whose inputs are staged ahead (0: register prefetch of the next row)
@@ -408,297 +413,304 @@ k_mar2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
         }
     };
 
-    double pA = 0.0, pB = 0.0;
-    const int j0 = t.j0;
-    if (w > 0) {
-        if (electric) {
-            // carried: the buffer's E at row r, H_A at r-1, E_A at r-1, H_B at r-2 (+ materials), and
-            // step A's psi (H and E groups) and P of row r-1, the buffer's P of row r-1
-            V e0c[3], hAm[3], eAm[3], hBm[3];
-            PS sHAm, sEAm;
-            V pAm[3], p0m[3];
-            int m_r, m_rm = 0;
-            {
-                const int ja = wrow(j0 - 2), jb = wrow(j0 - 1);
-                const V ea[3] = {ldf(0, ja), ldf(1, ja), ldf(2, ja)};
-                const V ha[3] = {ldf(3, ja), ldf(4, ja), ldf(5, ja)};
-#pragma unroll
-                for (int k = 0; k < 3; ++k) e0c[k] = ldf(k, jb);
-                PS po;
-                updH(ja, mat[(unsigned)(ja * nx + col)], ea, e0c[0], e0c[2], ha, (R)1, hA0, psi_in_row(ja, 2), po, hAm);   // H_A(j0-2)
-                m_r = mat[(unsigned)(jb * nx + col)];
-            }
-            // inputs of iteration r: the buffer's E at row r+1, H at row r, material of row r+1
-            V en_c[3], hq_c[3];
-            int mn_c;
-            int jr = wrow(j0 - 1), jp = wrow(j0 - 2);   // rows r and r-1, wrapped
-            // staged rows: iteration r's slot holds E(r+1), H(r), psi and P of row r; mq[k] is the
-            // material of row r + 1 + k (the rows staged ahead need theirs for the P copies)
-            int mq[STG + 2];
-            int sl = 0, js = 0, jq = 0;   // wrapped rows r + STG (staged next) and r + STG + 3 (its material next)
-            auto stage_e = [&](int slot, int j, int m) {   // j: the staged iteration's row, wrapped
-                const int jn = j + 1 == ny ? 0 : j + 1;
-                const unsigned g = (unsigned)(j * nx + col), gn = (unsigned)(jn * nx + col);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) { sg(slot, k, fin, k, N, gn); sg(slot, 3 + k, fin, 3 + k, N, g); }
-                stage_psi(slot, j, j, 0, 4);
-                stage_lor(slot, j, m);
-            };
-            if constexpr (STG > 0) {
-#pragma unroll
-                for (int k = 0; k < STG + 2; ++k) mq[k] = matw(j0 + k);
-#pragma unroll
-                for (int q = 0; q < STG; ++q) {
-                    if (j0 - 1 + q <= j0 + h) stage_e(q, wrow(j0 - 1 + q), q == 0 ? m_r : mq[q - 1]);
-                    cpa_commit();
-                }
-                mn_c = mq[0];
-                js = wrow(j0 - 1 + STG);
-                jq = wrow(j0 + STG + 2);
-            } else {
-                const int jn = jr + 1 == ny ? 0 : jr + 1;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) { en_c[k] = ldf(k, jn); hq_c[k] = ldf(3 + k, jr); }
-                mn_c = mat[(unsigned)(jn * nx + col)];
-            }
-            for (int r = j0 - 1; r <= j0 + h; ++r) {
-                const int jn = jr + 1 == ny ? 0 : jr + 1;
-                V en_n[3], hq_n[3];
-                int mn_n = 0;
-                PS piH, piE;
-                V p0r[3], pmr[3];
-                if constexpr (STG > 0) {
-                    if (r + STG <= j0 + h) stage_e(sl == 0 ? STG : sl - 1, js, mq[STG - 1]);
-                    cpa_commit();
-                    cpa_wait<STG>();
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) { en_c[k] = fv(sl, k); hq_c[k] = fv(sl, 3 + k); }
-                    piH = psi_slot(sl, jr, 2);
-                    piE = psi_slot(sl, jr, 0);
-                    lor_slot(sl, m_r, p0r, pmr);
-                } else {
-                    if (r + 1 <= j0 + h) {   // the next iteration's inputs, loaded ahead
-                        const int jnn = jn + 1 == ny ? 0 : jn + 1;
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) { en_n[k] = ldf(k, jnn); hq_n[k] = ldf(3 + k, jn); }
-                        mn_n = mat[(unsigned)(jnn * nx + col)];
-                    }
-                    piH = psi_in_row(jr, 2);
-                    piE = psi_in_row(jr, 0);
-                    lor_in(jr, m_r, p0r, pmr);
-                }
-                V hA[3], eA[3], pAr[3];
-                PS sHA, sEA;
-                updH(jr, m_r, e0c, en_c[0], en_c[2], hq_c, (R)1, hA0, piH, sHA, hA);
-                updE(jr, m_r, hA, hAm[0], hAm[2], e0c, a, bs, piE, sEA, p0r, pmr, firstA, pAr, eA);
-                const bool inA = r >= j0 && r < j0 + h;
-                if (inA && t.ne > 0) pA += project_row_m2<R, CPLX>(t, r - j0, w, grp, eA[0], eA[1], eA[2]);
-                if (!two) {
-                    if (inA) {
-                        store(jr, eA, hA);
-                        psi_store(jr, 2, sHA);
-                        psi_store(jr, 0, sEA);
-                        lor_store(jr, m_r, pAr, p0r);
-                    }
-                } else if (r == j0) {
+    // the march, compiled with and without the projection of the sigma group (most tiles hold no
+    // entries; their FP64 sums would otherwise stay live through the whole march)
+    auto march = [&](auto proj_tag) {
+        constexpr bool PROJ = decltype(proj_tag)::value;
+        double pA = 0.0, pB = 0.0;
+        const int j0 = t.j0;
+        if (w > 0) {
+            if (electric) {
+                // carried: the buffer's E at row r, H_A at r-1, E_A at r-1, H_B at r-2 (+ materials), and
+                // step A's psi (H and E groups) and P of row r-1, the buffer's P of row r-1
+                V e0c[3], hAm[3], eAm[3], hBm[3];
+                PS sHAm, sEAm;
+                V pAm[3], p0m[3];
+                int m_r, m_rm = 0;
+                {
+                    const int ja = wrow(j0 - 2), jb = wrow(j0 - 1);
+                    const V ea[3] = {ldf(0, ja), ldf(1, ja), ldf(2, ja)};
+                    const V ha[3] = {ldf(3, ja), ldf(4, ja), ldf(5, ja)};
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) e0c[k] = ldf(k, jb);
                     PS po;
-                    updH(jp, m_rm, eAm, eA[0], eA[2], hAm, (R)1, hB0, sHAm, po, hBm);   // H_B(j0-1)
-                } else if (r > j0) {
-                    const int jm = jp;
-                    V hB[3], eB[3], pBr[3];
-                    PS sHB, sEB;
-                    updH(jm, m_rm, eAm, eA[0], eA[2], hAm, (R)1, hB0, sHAm, sHB, hB);
-                    updE(jm, m_rm, hB, hBm[0], hBm[2], eAm, a, bs, sEAm, sEB, pAm, p0m, false, pBr, eB);
-                    if (r - 1 < j0 + h) {
-                        store(jm, eB, hB);
-                        psi_store(jm, 2, sHB);
-                        psi_store(jm, 0, sEB);
-                        lor_store(jm, m_rm, pBr, pAm);
-                        if (t.ne > 0) pB += project_row_m2<R, CPLX>(t, r - 1 - j0, w, grp, eB[0], eB[1], eB[2]);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) hBm[k] = hB[k];
+                    updH(ja, mat[(unsigned)(ja * nx + col)], ea, e0c[0], e0c[2], ha, (R)1, hA0, psi_in_row(ja, 2), po, hAm);   // H_A(j0-2)
+                    m_r = mat[(unsigned)(jb * nx + col)];
                 }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    eAm[k] = eA[k];
-                    hAm[k] = hA[k];
-                    e0c[k] = en_c[k];
-                    if constexpr (STG == 0) { en_c[k] = en_n[k]; hq_c[k] = hq_n[k]; }
-                    pAm[k] = pAr[k];
-                    p0m[k] = p0r[k];
-                }
-                sHAm = sHA;
-                sEAm = sEA;
-                m_rm = m_r;
-                m_r = mn_c;
+                // inputs of iteration r: the buffer's E at row r+1, H at row r, material of row r+1
+                V en_c[3], hq_c[3];
+                int mn_c;
+                int jr = wrow(j0 - 1), jp = wrow(j0 - 2);   // rows r and r-1, wrapped
+                // staged rows: iteration r's slot holds E(r+1), H(r), psi and P of row r; mq[k] is the
+                // material of row r + 1 + k (the rows staged ahead need theirs for the P copies)
+                int mq[STG + 2];
+                int sl = 0, js = 0, jq = 0;   // wrapped rows r + STG (staged next) and r + STG + 3 (its material next)
+                auto stage_e = [&](int slot, int j, int m) {   // j: the staged iteration's row, wrapped
+                    const int jn = j + 1 == ny ? 0 : j + 1;
+                    const unsigned g = (unsigned)(j * nx + col), gn = (unsigned)(jn * nx + col);
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) { sg(slot, k, fin, k, N, gn); sg(slot, 3 + k, fin, 3 + k, N, g); }
+                    stage_psi(slot, j, j, 0, 4);
+                    stage_lor(slot, j, m);
+                };
                 if constexpr (STG > 0) {
-#pragma unroll
-                    for (int k = 0; k < STG + 1; ++k) mq[k] = mq[k + 1];
-                    mq[STG + 1] = mat[(unsigned)(jq * nx + col)];
+    #pragma unroll
+                    for (int k = 0; k < STG + 2; ++k) mq[k] = matw(j0 + k);
+    #pragma unroll
+                    for (int q = 0; q < STG; ++q) {
+                        if (j0 - 1 + q <= j0 + h) stage_e(q, wrow(j0 - 1 + q), q == 0 ? m_r : mq[q - 1]);
+                        cpa_commit();
+                    }
                     mn_c = mq[0];
-                    sl = sl == STG ? 0 : sl + 1;
-                    js = js + 1 == ny ? 0 : js + 1;
-                    jq = jq + 1 == ny ? 0 : jq + 1;
+                    js = wrow(j0 - 1 + STG);
+                    jq = wrow(j0 + STG + 2);
                 } else {
-                    mn_c = mn_n;
+                    const int jn = jr + 1 == ny ? 0 : jr + 1;
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) { en_c[k] = ldf(k, jn); hq_c[k] = ldf(3 + k, jr); }
+                    mn_c = mat[(unsigned)(jn * nx + col)];
                 }
-                jp = jr;
-                jr = jn;
-            }
-        } else {
-            // carried: E_A at row r, the buffer's H at row r, H_A at r-1, E_B at r-1 (+ materials),
-            // step A's E psi and P of row r (made one iteration ahead), step A's H psi of row r-1
-            V eAc[3], h0c[3], hAm[3], eBm[3];
-            PS sEAc, sHAm;
-            V pAc[3], p0c[3];
-            int m_r, m_rm = 0;
-            int jr = wrow(j0 - 1), jp = wrow(j0 - 2);   // rows r and r-1, wrapped
-            {
-                const int ja = jp;
-                const V hb2[3] = {ldf(3, ja), ldf(4, ja), ldf(5, ja)};
-                const V e0[3] = {ldf(0, jr), ldf(1, jr), ldf(2, jr)};
-#pragma unroll
-                for (int k = 0; k < 3; ++k) h0c[k] = ldf(3 + k, jr);
-                m_r = mat[(unsigned)(jr * nx + col)];
-                V pm0[3];
-                lor_in(jr, m_r, p0c, pm0);
-                updE(jr, m_r, h0c, hb2[0], hb2[2], e0, (R)1, hA0, psi_in_row(jr, 0), sEAc, p0c, pm0, false, pAc, eAc);   // E_A(j0-1)
-            }
-            // inputs of iteration r: the buffer's H and E at row r+1, material of row r+1
-            V hn_c[3], en_c[3];
-            int mn_c;
-            // staged rows: iteration r's slot holds H(r+1), E(r+1), the E-group psi and P of row r+1,
-            // the H-group psi of row r; mq[k] is the material of row r + 1 + k
-            int mq[STG + 2];
-            int sl = 0, js = 0, jq = 0;   // wrapped rows r + STG (staged next) and r + STG + 3 (its material next)
-            auto stage_m = [&](int slot, int j, int m) {   // j: the staged iteration's row, wrapped
-                const int jn = j + 1 == ny ? 0 : j + 1;
-                const unsigned gn = (unsigned)(jn * nx + col);
-#pragma unroll
-                for (int k = 0; k < 3; ++k) { sg(slot, k, fin, 3 + k, N, gn); sg(slot, 3 + k, fin, k, N, gn); }
-                stage_psi(slot, jn, jn, 0, 2);
-                stage_psi(slot, j, j, 2, 4);
-                stage_lor(slot, jn, m);
-            };
-            if constexpr (STG > 0) {
-#pragma unroll
-                for (int k = 0; k < STG + 2; ++k) mq[k] = matw(j0 + k);
-#pragma unroll
-                for (int q = 0; q < STG; ++q) {
-                    if (j0 - 1 + q <= j0 + h) stage_m(q, wrow(j0 - 1 + q), mq[q]);
-                    cpa_commit();
-                }
-                mn_c = mq[0];
-                js = wrow(j0 - 1 + STG);
-                jq = wrow(j0 + STG + 2);
-            } else {
-                const int jn = jr + 1 == ny ? 0 : jr + 1;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) { hn_c[k] = ldf(3 + k, jn); en_c[k] = ldf(k, jn); }
-                mn_c = mat[(unsigned)(jn * nx + col)];
-            }
-            for (int r = j0 - 1; r <= j0 + h; ++r) {
-                const int jn = jr + 1 == ny ? 0 : jr + 1;
-                V hn_n[3], en_n[3];
-                int mn_n = 0;
-                V eAn[3], hA[3], pAn[3], p0n[3], pmn[3];
-                PS sEAn, sHA, piE, piH;
-                if constexpr (STG > 0) {
-                    if (r + STG <= j0 + h) stage_m(sl == 0 ? STG : sl - 1, js, mq[STG]);
-                    cpa_commit();
-                    cpa_wait<STG>();
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) { hn_c[k] = fv(sl, k); en_c[k] = fv(sl, 3 + k); }
-                    piE = psi_slot(sl, jn, 0);
-                    piH = psi_slot(sl, jr, 2);
-                    lor_slot(sl, mn_c, p0n, pmn);
-                } else {
-                    if (r + 1 <= j0 + h) {
-                        const int jnn = jn + 1 == ny ? 0 : jn + 1;
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) { hn_n[k] = ldf(3 + k, jnn); en_n[k] = ldf(k, jnn); }
-                        mn_n = mat[(unsigned)(jnn * nx + col)];
-                    }
-                    piE = psi_in_row(jn, 0);
-                    piH = psi_in_row(jr, 2);
-                    lor_in(jn, mn_c, p0n, pmn);
-                }
-                updE(jn, mn_c, hn_c, h0c[0], h0c[2], en_c, (R)1, hA0, piE, sEAn, p0n, pmn, false, pAn, eAn);   // E_A(r+1)
-                updH(jr, m_r, eAc, eAn[0], eAn[2], h0c, a, bs, piH, sHA, hA);          // H_A(r)
-                const bool inA = r >= j0 && r < j0 + h;
-                if (inA && t.ne > 0) pA += project_row_m2<R, CPLX>(t, r - j0, w, grp, hA[0], hA[1], hA[2]);
-                if (!two) {
-                    if (inA) {
-                        store(jr, eAc, hA);
-                        psi_store(jr, 0, sEAc);
-                        psi_store(jr, 2, sHA);
-                        lor_store(jr, m_r, pAc, p0c);
-                    }
-                } else if (r >= j0) {
-                    V eB[3], pBr[3];
-                    PS sEB;
-                    updE(jr, m_r, hA, hAm[0], hAm[2], eAc, (R)1, hB0, sEAc, sEB, pAc, p0c, false, pBr, eB);   // E_B(r)
-                    if (r > j0) {
-                        const int jm = jp;
-                        V hB[3];
-                        PS sHB;
-                        updH(jm, m_rm, eBm, eB[0], eB[2], hAm, a, bs, sHAm, sHB, hB);    // H_B(r-1)
-                        if (r - 1 < j0 + h) {
-                            store(jm, eBm, hB);
-                            psi_store(jm, 2, sHB);
-                            if (t.ne > 0) pB += project_row_m2<R, CPLX>(t, r - 1 - j0, w, grp, hB[0], hB[1], hB[2]);
+                for (int r = j0 - 1; r <= j0 + h; ++r) {
+                    const int jn = jr + 1 == ny ? 0 : jr + 1;
+                    V en_n[3], hq_n[3];
+                    int mn_n = 0;
+                    PS piH, piE;
+                    V p0r[3], pmr[3];
+                    if constexpr (STG > 0) {
+                        if (r + STG <= j0 + h) stage_e(sl == 0 ? STG : sl - 1, js, mq[STG - 1]);
+                        cpa_commit();
+                        cpa_wait<STG>();
+    #pragma unroll
+                        for (int k = 0; k < 3; ++k) { en_c[k] = fv(sl, k); hq_c[k] = fv(sl, 3 + k); }
+                        piH = psi_slot(sl, jr, 2);
+                        piE = psi_slot(sl, jr, 0);
+                        lor_slot(sl, m_r, p0r, pmr);
+                    } else {
+                        if (r + 1 <= j0 + h) {   // the next iteration's inputs, loaded ahead
+                            const int jnn = jn + 1 == ny ? 0 : jn + 1;
+    #pragma unroll
+                            for (int k = 0; k < 3; ++k) { en_n[k] = ldf(k, jnn); hq_n[k] = ldf(3 + k, jn); }
+                            mn_n = mat[(unsigned)(jnn * nx + col)];
                         }
+                        piH = psi_in_row(jr, 2);
+                        piE = psi_in_row(jr, 0);
+                        lor_in(jr, m_r, p0r, pmr);
                     }
-                    if (r < j0 + h) {
-                        psi_store(jr, 0, sEB);
-                        lor_store(jr, m_r, pBr, pAc);
+                    V hA[3], eA[3], pAr[3];
+                    PS sHA, sEA;
+                    updH(jr, m_r, e0c, en_c[0], en_c[2], hq_c, (R)1, hA0, piH, sHA, hA);
+                    updE(jr, m_r, hA, hAm[0], hAm[2], e0c, a, bs, piE, sEA, p0r, pmr, firstA, pAr, eA);
+                    const bool inA = r >= j0 && r < j0 + h;
+                    if (PROJ && inA && t.ne > 0) pA += project_row_m2<R, CPLX>(t, r - j0, w, grp, eA[0], eA[1], eA[2]);
+                    if (!two) {
+                        if (inA) {
+                            store(jr, eA, hA);
+                            psi_store(jr, 2, sHA);
+                            psi_store(jr, 0, sEA);
+                            lor_store(jr, m_r, pAr, p0r);
+                        }
+                    } else if (r == j0) {
+                        PS po;
+                        updH(jp, m_rm, eAm, eA[0], eA[2], hAm, (R)1, hB0, sHAm, po, hBm);   // H_B(j0-1)
+                    } else if (r > j0) {
+                        const int jm = jp;
+                        V hB[3], eB[3], pBr[3];
+                        PS sHB, sEB;
+                        updH(jm, m_rm, eAm, eA[0], eA[2], hAm, (R)1, hB0, sHAm, sHB, hB);
+                        updE(jm, m_rm, hB, hBm[0], hBm[2], eAm, a, bs, sEAm, sEB, pAm, p0m, false, pBr, eB);
+                        if (r - 1 < j0 + h) {
+                            store(jm, eB, hB);
+                            psi_store(jm, 2, sHB);
+                            psi_store(jm, 0, sEB);
+                            lor_store(jm, m_rm, pBr, pAm);
+                            if (PROJ && t.ne > 0) pB += project_row_m2<R, CPLX>(t, r - 1 - j0, w, grp, eB[0], eB[1], eB[2]);
+                        }
+    #pragma unroll
+                        for (int k = 0; k < 3; ++k) hBm[k] = hB[k];
                     }
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) eBm[k] = eB[k];
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        eAm[k] = eA[k];
+                        hAm[k] = hA[k];
+                        e0c[k] = en_c[k];
+                        if constexpr (STG == 0) { en_c[k] = en_n[k]; hq_c[k] = hq_n[k]; }
+                        pAm[k] = pAr[k];
+                        p0m[k] = p0r[k];
+                    }
+                    sHAm = sHA;
+                    sEAm = sEA;
+                    m_rm = m_r;
+                    m_r = mn_c;
+                    if constexpr (STG > 0) {
+    #pragma unroll
+                        for (int k = 0; k < STG + 1; ++k) mq[k] = mq[k + 1];
+                        mq[STG + 1] = mat[(unsigned)(jq * nx + col)];
+                        mn_c = mq[0];
+                        sl = sl == STG ? 0 : sl + 1;
+                        js = js + 1 == ny ? 0 : js + 1;
+                        jq = jq + 1 == ny ? 0 : jq + 1;
+                    } else {
+                        mn_c = mn_n;
+                    }
+                    jp = jr;
+                    jr = jn;
                 }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    hAm[k] = hA[k];
-                    eAc[k] = eAn[k];
-                    h0c[k] = hn_c[k];
-                    if constexpr (STG == 0) { hn_c[k] = hn_n[k]; en_c[k] = en_n[k]; }
-                    pAc[k] = pAn[k];
-                    p0c[k] = p0n[k];
+            } else {
+                // carried: E_A at row r, the buffer's H at row r, H_A at r-1, E_B at r-1 (+ materials),
+                // step A's E psi and P of row r (made one iteration ahead), step A's H psi of row r-1
+                V eAc[3], h0c[3], hAm[3], eBm[3];
+                PS sEAc, sHAm;
+                V pAc[3], p0c[3];
+                int m_r, m_rm = 0;
+                int jr = wrow(j0 - 1), jp = wrow(j0 - 2);   // rows r and r-1, wrapped
+                {
+                    const int ja = jp;
+                    const V hb2[3] = {ldf(3, ja), ldf(4, ja), ldf(5, ja)};
+                    const V e0[3] = {ldf(0, jr), ldf(1, jr), ldf(2, jr)};
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) h0c[k] = ldf(3 + k, jr);
+                    m_r = mat[(unsigned)(jr * nx + col)];
+                    V pm0[3];
+                    lor_in(jr, m_r, p0c, pm0);
+                    updE(jr, m_r, h0c, hb2[0], hb2[2], e0, (R)1, hA0, psi_in_row(jr, 0), sEAc, p0c, pm0, false, pAc, eAc);   // E_A(j0-1)
                 }
-                sEAc = sEAn;
-                sHAm = sHA;
-                m_rm = m_r;
-                m_r = mn_c;
+                // inputs of iteration r: the buffer's H and E at row r+1, material of row r+1
+                V hn_c[3], en_c[3];
+                int mn_c;
+                // staged rows: iteration r's slot holds H(r+1), E(r+1), the E-group psi and P of row r+1,
+                // the H-group psi of row r; mq[k] is the material of row r + 1 + k
+                int mq[STG + 2];
+                int sl = 0, js = 0, jq = 0;   // wrapped rows r + STG (staged next) and r + STG + 3 (its material next)
+                auto stage_m = [&](int slot, int j, int m) {   // j: the staged iteration's row, wrapped
+                    const int jn = j + 1 == ny ? 0 : j + 1;
+                    const unsigned gn = (unsigned)(jn * nx + col);
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) { sg(slot, k, fin, 3 + k, N, gn); sg(slot, 3 + k, fin, k, N, gn); }
+                    stage_psi(slot, jn, jn, 0, 2);
+                    stage_psi(slot, j, j, 2, 4);
+                    stage_lor(slot, jn, m);
+                };
                 if constexpr (STG > 0) {
-#pragma unroll
-                    for (int k = 0; k < STG + 1; ++k) mq[k] = mq[k + 1];
-                    mq[STG + 1] = mat[(unsigned)(jq * nx + col)];
+    #pragma unroll
+                    for (int k = 0; k < STG + 2; ++k) mq[k] = matw(j0 + k);
+    #pragma unroll
+                    for (int q = 0; q < STG; ++q) {
+                        if (j0 - 1 + q <= j0 + h) stage_m(q, wrow(j0 - 1 + q), mq[q]);
+                        cpa_commit();
+                    }
                     mn_c = mq[0];
-                    sl = sl == STG ? 0 : sl + 1;
-                    js = js + 1 == ny ? 0 : js + 1;
-                    jq = jq + 1 == ny ? 0 : jq + 1;
+                    js = wrow(j0 - 1 + STG);
+                    jq = wrow(j0 + STG + 2);
                 } else {
-                    mn_c = mn_n;
+                    const int jn = jr + 1 == ny ? 0 : jr + 1;
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) { hn_c[k] = ldf(3 + k, jn); en_c[k] = ldf(k, jn); }
+                    mn_c = mat[(unsigned)(jn * nx + col)];
                 }
-                jp = jr;
-                jr = jn;
+                for (int r = j0 - 1; r <= j0 + h; ++r) {
+                    const int jn = jr + 1 == ny ? 0 : jr + 1;
+                    V hn_n[3], en_n[3];
+                    int mn_n = 0;
+                    V eAn[3], hA[3], pAn[3], p0n[3], pmn[3];
+                    PS sEAn, sHA, piE, piH;
+                    if constexpr (STG > 0) {
+                        if (r + STG <= j0 + h) stage_m(sl == 0 ? STG : sl - 1, js, mq[STG]);
+                        cpa_commit();
+                        cpa_wait<STG>();
+    #pragma unroll
+                        for (int k = 0; k < 3; ++k) { hn_c[k] = fv(sl, k); en_c[k] = fv(sl, 3 + k); }
+                        piE = psi_slot(sl, jn, 0);
+                        piH = psi_slot(sl, jr, 2);
+                        lor_slot(sl, mn_c, p0n, pmn);
+                    } else {
+                        if (r + 1 <= j0 + h) {
+                            const int jnn = jn + 1 == ny ? 0 : jn + 1;
+    #pragma unroll
+                            for (int k = 0; k < 3; ++k) { hn_n[k] = ldf(3 + k, jnn); en_n[k] = ldf(k, jnn); }
+                            mn_n = mat[(unsigned)(jnn * nx + col)];
+                        }
+                        piE = psi_in_row(jn, 0);
+                        piH = psi_in_row(jr, 2);
+                        lor_in(jn, mn_c, p0n, pmn);
+                    }
+                    updE(jn, mn_c, hn_c, h0c[0], h0c[2], en_c, (R)1, hA0, piE, sEAn, p0n, pmn, false, pAn, eAn);   // E_A(r+1)
+                    updH(jr, m_r, eAc, eAn[0], eAn[2], h0c, a, bs, piH, sHA, hA);          // H_A(r)
+                    const bool inA = r >= j0 && r < j0 + h;
+                    if (PROJ && inA && t.ne > 0) pA += project_row_m2<R, CPLX>(t, r - j0, w, grp, hA[0], hA[1], hA[2]);
+                    if (!two) {
+                        if (inA) {
+                            store(jr, eAc, hA);
+                            psi_store(jr, 0, sEAc);
+                            psi_store(jr, 2, sHA);
+                            lor_store(jr, m_r, pAc, p0c);
+                        }
+                    } else if (r >= j0) {
+                        V eB[3], pBr[3];
+                        PS sEB;
+                        updE(jr, m_r, hA, hAm[0], hAm[2], eAc, (R)1, hB0, sEAc, sEB, pAc, p0c, false, pBr, eB);   // E_B(r)
+                        if (r > j0) {
+                            const int jm = jp;
+                            V hB[3];
+                            PS sHB;
+                            updH(jm, m_rm, eBm, eB[0], eB[2], hAm, a, bs, sHAm, sHB, hB);    // H_B(r-1)
+                            if (r - 1 < j0 + h) {
+                                store(jm, eBm, hB);
+                                psi_store(jm, 2, sHB);
+                                if (PROJ && t.ne > 0) pB += project_row_m2<R, CPLX>(t, r - 1 - j0, w, grp, hB[0], hB[1], hB[2]);
+                            }
+                        }
+                        if (r < j0 + h) {
+                            psi_store(jr, 0, sEB);
+                            lor_store(jr, m_r, pBr, pAc);
+                        }
+    #pragma unroll
+                        for (int k = 0; k < 3; ++k) eBm[k] = eB[k];
+                    }
+    #pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        hAm[k] = hA[k];
+                        eAc[k] = eAn[k];
+                        h0c[k] = hn_c[k];
+                        if constexpr (STG == 0) { hn_c[k] = hn_n[k]; en_c[k] = en_n[k]; }
+                        pAc[k] = pAn[k];
+                        p0c[k] = p0n[k];
+                    }
+                    sEAc = sEAn;
+                    sHAm = sHA;
+                    m_rm = m_r;
+                    m_r = mn_c;
+                    if constexpr (STG > 0) {
+    #pragma unroll
+                        for (int k = 0; k < STG + 1; ++k) mq[k] = mq[k + 1];
+                        mq[STG + 1] = mat[(unsigned)(jq * nx + col)];
+                        mn_c = mq[0];
+                        sl = sl == STG ? 0 : sl + 1;
+                        js = js + 1 == ny ? 0 : js + 1;
+                        jq = jq + 1 == ny ? 0 : jq + 1;
+                    } else {
+                        mn_c = mn_n;
+                    }
+                    jp = jr;
+                    jr = jn;
+                }
             }
         }
-    }
 
-    if (t.ne > 0) {
-        for (int o = 16; o > 0; o >>= 1) {
-            pA += __shfl_down_sync(0xffffffffu, pA, o);
-            pB += __shfl_down_sync(0xffffffffu, pB, o);
+        if (PROJ && t.ne > 0) {
+            for (int o = 16; o > 0; o >>= 1) {
+                pA += __shfl_down_sync(0xffffffffu, pA, o);
+                pB += __shfl_down_sync(0xffffffffu, pB, o);
+            }
+            if (lane == 0) {
+                const double c = S.gw[nA - 1] * pA + (two ? S.gw[nA] * pB : 0.0);
+                atomicAdd(S.acc, c);
+                const double ct = (nA > S.tail_from ? S.gw[nA - 1] * pA : 0.0) + (two && nA + 1 > S.tail_from ? S.gw[nA] * pB : 0.0);
+                if (ct != 0.0) atomicAdd(S.tail, ct);
+            }
         }
-        if (lane == 0) {
-            const double c = S.gw[nA - 1] * pA + (two ? S.gw[nA] * pB : 0.0);
-            atomicAdd(S.acc, c);
-            const double ct = (nA > S.tail_from ? S.gw[nA - 1] * pA : 0.0) + (two && nA + 1 > S.tail_from ? S.gw[nA] * pB : 0.0);
-            if (ct != 0.0) atomicAdd(S.tail, ct);
-        }
-    }
+    };
+    if (t.ne > 0) march(Flag<true>{});
+    else march(Flag<false>{});
 }
 
 template <typename R, bool CPLX, bool PML, bool LOR, int MINB>
