@@ -170,6 +170,11 @@ typedef struct {
     int64_t bytes_per_step;    /* algorithmic bytes of one time step over all simulations: every
                                   stored field, CPML auxiliary and Lorentz (P, P_prev per present
                                   pole) value read and written once, plus the material ids */
+    int64_t launches;          /* launch indices one request of the plan takes: ceil(n_steps / k)
+                                  for the k time steps its kernels fuse into one launch (2D TM/TE
+                                  runs k = steps_per_launch; cylindrical runs and FP32 Cartesian
+                                  six-component runs with at most one Lorentz pole per material
+                                  k = 2 when steps_per_launch >= 2; other runs k = 1) */
 } casimir_plan_info;
 
 typedef struct {

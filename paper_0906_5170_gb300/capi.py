@@ -88,7 +88,7 @@ class Problem(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [("n_sims", ctypes.c_int64), ("n_cells", ctypes.c_int64), ("cell_updates", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("bytes_per_update", ctypes.c_int64),
-                ("upload_bytes", ctypes.c_int64), ("bytes_per_step", ctypes.c_int64)]
+                ("upload_bytes", ctypes.c_int64), ("bytes_per_step", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
 
 class PlanOptions(ctypes.Structure):

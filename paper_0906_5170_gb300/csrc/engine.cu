@@ -1663,6 +1663,7 @@ int casimir_plan_get_info(const casimir_plan_t *P, casimir_plan_info *info)
     int cf = full && P->sims[0].cplx ? 2 : 1;
     info->bytes_per_update = (full ? 12 * cf : 6) * (int64_t)P->rsize + 1;
     info->upload_bytes = P->table_bytes;
+    info->launches = P->launches;
     // one step over every simulation: the field planes, the CPML psi planes of the slab cells
     // (4 per PML axis) and P, P_prev of every (site, pole) pair, each read and written once
     int64_t bps = 0;

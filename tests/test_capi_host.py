@@ -112,6 +112,34 @@ def test_plan_rejects_invalid_cylindrical_problems(mutate):
     assert e.value.code == -1
 
 
+def test_time_steps_fused_per_launch_by_run_kind():
+    # launch indices per request, ceil(T / k): k = steps_per_launch for 2D TM/TE runs; two for the
+    # two-step marches (cylindrical runs; FP32 Cartesian six-component runs whose materials have at
+    # most one Lorentz pole) when steps_per_launch >= 2; one for every other run
+    def launches(p, opts=None):
+        return pk.Plan(p, options=opts).info()["launches"]
+
+    T = 301
+    tm = W.piston_small(n_steps=T)
+    assert launches(dict(tm, precision="fp32")) == (T + 2) // 3
+    assert launches(dict(tm, precision="fp64")) == (T + 1) // 2
+    assert launches(dict(tm, precision="fp32"), {"steps_per_launch": 1}) == T
+    wg = W.config3_waveguides(0.5, resolution=8, n_cells=48, pml_units=0.75, n_harm=2, n_steps=T,
+                              k_points=[{"k": [0, 0, 1.3], "weight": 0.3}], precision="fp32")
+    assert launches(wg) == (T + 1) // 2                                   # one pole, FP32
+    assert launches(wg, {"steps_per_launch": 2}) == (T + 1) // 2
+    assert launches(wg, {"steps_per_launch": 1}) == T
+    assert launches(dict(wg, precision="fp64")) == T                      # FP64: one step
+    silica = W.grating_silica(0.5, resolution=16, nk_x=1, nk_z=1, n_harm=1, t_max=1.0, courant=0.2,
+                              pml_units=0.25, precision="fp32")
+    assert launches(silica) == silica["n_steps"]                          # three poles: one step
+    cyl = W.cylinder_piston(12, [0, 1], t_max=2.0, precision="fp64")
+    assert launches(cyl) == (cyl["n_steps"] + 1) // 2
+    assert launches(cyl, {"steps_per_launch": 1}) == cyl["n_steps"]
+    s3 = W.config4_sphere_notch(0.4, seed=3, resolution=6, n_cells=24, pml_cells=4, n_harm=1, n_steps=T)
+    assert launches(s3) == T                                              # 3D: one step per launch
+
+
 def test_plan_options_defaults_and_explicit():
     p = W.piston_small()
     # three fused steps for FP32 runs, two for FP64 runs (bound by FP64 arithmetic)
