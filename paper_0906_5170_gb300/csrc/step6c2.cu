@@ -20,11 +20,27 @@ namespace cas {
 namespace {
 
 constexpr int WARPS_C2 = 4;   // warps (strips) per CTA
+// 1: the next iteration's field values staged by cp.async; 0: loaded into registers ahead
+#ifndef CYL2_STG
+#define CYL2_STG 1
+#endif
 
 template <typename R>
 __device__ __forceinline__ R cdn(R v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 template <typename R>
 __device__ __forceinline__ R cup(R v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+
+// Asynchronous copy of one element, global -> shared (cp.async of the lane's own value)
+template <typename R>
+__device__ __forceinline__ void cpa(R *sdst, const R *gsrc)
+{
+    const unsigned a = (unsigned)__cvta_generic_to_shared(sdst);
+    if constexpr (sizeof(R) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gsrc) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Projection of the sigma group's three components at tile row ly (entries rowptr[ly] ..
 // rowptr[ly+1], loc = ly * MARCH_W2 + lx, the component in bits 16..18): lanes 2 .. w + 1
@@ -54,7 +70,10 @@ __device__ __forceinline__ double project_row_c2(const DevTile2 &t, int ly, int 
     return part;
 }
 
-template <typename R, int MINB>
+// STG = 1: the next iteration's six field values are copied by cp.async into a per-lane
+// shared-memory ring of two slots while the current one computes; STG = 0: they are loaded
+// into registers one iteration ahead
+template <typename R, int MINB, int STG>
 __global__ void __launch_bounds__(WARPS_C2 * 32, MINB)
 k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int ntiles,
        const int64_t *__restrict__ launch_base, int64_t launch_add)
@@ -104,6 +123,10 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
     // any row index to [0, ny)
     auto wrow = [&](int j) { j %= ny; return j < 0 ? j + ny : j; };
     auto ldr = [&](int plane, int j) -> R { return fin[(unsigned)plane * N + (unsigned)(j * nx + col)]; };
+    // staged inputs: [slot][value][lane], six field values per iteration
+    __shared__ __align__(16) R ring_s[STG > 0 ? WARPS_C2 : 1][2][6][32];
+    auto sg = [&](int slot, int v, int plane, int j) { cpa(&ring_s[warp][slot][v][lane], fin + (unsigned)plane * N + (unsigned)(j * nx + col)); };
+    auto fv = [&](int slot, int v) -> R { return ring_s[warp][slot][v][lane]; };
 
     // H at row j (wrapped) from E at rows j and j+1 (E_r, E_phi of row j+1: exn, ezn)
     auto updH = [&](int j, int m, const R e[3], R exn, R ezn, const R hq[3], R aa, R bb, R ho[3]) {
@@ -160,10 +183,22 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
             R en_c[3], hq_c[3];
             int mn_c;
             int jr = wrow(j0 - 1), jp = wrow(j0 - 2);   // rows r and r-1, wrapped
+            // staged: slot `sl` holds this iteration's E(r+1) (values 0..2) and H(r) (3..5)
+            int sl = 0;
+            auto stage_e = [&](int slot, int j) {   // iteration of row j (wrapped)
+                const int jn_ = j + 1 == ny ? 0 : j + 1;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { sg(slot, k, k, jn_); sg(slot, 3 + k, 3 + k, j); }
+            };
             {
                 const int jn = jr + 1 == ny ? 0 : jr + 1;
+                if constexpr (STG > 0) {
+                    stage_e(0, jr);
+                    cpa_commit();
+                } else {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) { en_c[k] = ldr(k, jn); hq_c[k] = ldr(3 + k, jr); }
+                    for (int k = 0; k < 3; ++k) { en_c[k] = ldr(k, jn); hq_c[k] = ldr(3 + k, jr); }
+                }
                 mn_c = mat[(unsigned)(jn * nx + col)];
             }
             for (int r = j0 - 1; r <= j0 + h; ++r) {
@@ -172,9 +207,20 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                 int mn_n = 0;
                 if (r + 1 <= j0 + h) {   // the next iteration's inputs, loaded ahead
                     const int jnn = jn + 1 == ny ? 0 : jn + 1;
+                    if constexpr (STG > 0) {
+                        stage_e(sl ^ 1, jn);
+                    } else {
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) { en_n[k] = ldr(k, jnn); hq_n[k] = ldr(3 + k, jn); }
+                        for (int k = 0; k < 3; ++k) { en_n[k] = ldr(k, jnn); hq_n[k] = ldr(3 + k, jn); }
+                    }
                     mn_n = mat[(unsigned)(jnn * nx + col)];
+                }
+                if constexpr (STG > 0) {
+                    cpa_commit();
+                    cpa_wait<1>();
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) { en_c[k] = fv(sl, k); hq_c[k] = fv(sl, 3 + k); }
+                    sl ^= 1;
                 }
                 R hA[3], eA[3];
                 updH(jr, m_r, e0c, en_c[0], en_c[2], hq_c, (R)1, hA0, hA);
@@ -202,8 +248,10 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                     eAm[k] = eA[k];
                     hAm[k] = hA[k];
                     e0c[k] = en_c[k];
-                    en_c[k] = en_n[k];
-                    hq_c[k] = hq_n[k];
+                    if constexpr (STG == 0) {
+                        en_c[k] = en_n[k];
+                        hq_c[k] = hq_n[k];
+                    }
                 }
                 m_rm = m_r;
                 m_r = mn_c;
@@ -228,10 +276,21 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
             // inputs of iteration r: the buffer's H and E at row r+1, material of row r+1
             R hn_c[3], en_c[3];
             int mn_c;
+            // staged: slot `sl` holds this iteration's H(r+1) (values 0..2) and E(r+1) (3..5)
+            int sl = 0;
+            auto stage_m = [&](int slot, int jn_) {   // row r+1 (wrapped) of the staged iteration
+#pragma unroll
+                for (int k = 0; k < 3; ++k) { sg(slot, k, 3 + k, jn_); sg(slot, 3 + k, k, jn_); }
+            };
             {
                 const int jn = jr + 1 == ny ? 0 : jr + 1;
+                if constexpr (STG > 0) {
+                    stage_m(0, jn);
+                    cpa_commit();
+                } else {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) { hn_c[k] = ldr(3 + k, jn); en_c[k] = ldr(k, jn); }
+                    for (int k = 0; k < 3; ++k) { hn_c[k] = ldr(3 + k, jn); en_c[k] = ldr(k, jn); }
+                }
                 mn_c = mat[(unsigned)(jn * nx + col)];
             }
             for (int r = j0 - 1; r <= j0 + h; ++r) {
@@ -240,9 +299,20 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                 int mn_n = 0;
                 if (r + 1 <= j0 + h) {
                     const int jnn = jn + 1 == ny ? 0 : jn + 1;
+                    if constexpr (STG > 0) {
+                        stage_m(sl ^ 1, jnn);
+                    } else {
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) { hn_n[k] = ldr(3 + k, jnn); en_n[k] = ldr(k, jnn); }
+                        for (int k = 0; k < 3; ++k) { hn_n[k] = ldr(3 + k, jnn); en_n[k] = ldr(k, jnn); }
+                    }
                     mn_n = mat[(unsigned)(jnn * nx + col)];
+                }
+                if constexpr (STG > 0) {
+                    cpa_commit();
+                    cpa_wait<1>();
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) { hn_c[k] = fv(sl, k); en_c[k] = fv(sl, 3 + k); }
+                    sl ^= 1;
                 }
                 R eAn[3], hA[3];
                 updE(jn, mn_c, hn_c, h0c[0], h0c[2], en_c, (R)1, hA0, eAn);   // E_A(r+1)
@@ -271,8 +341,10 @@ k_cyl2(const DevSim6 *__restrict__ sims, const DevTile2 *__restrict__ tiles, int
                     hAm[k] = hA[k];
                     eAc[k] = eAn[k];
                     h0c[k] = hn_c[k];
-                    hn_c[k] = hn_n[k];
-                    en_c[k] = en_n[k];
+                    if constexpr (STG == 0) {
+                        hn_c[k] = hn_n[k];
+                        en_c[k] = en_n[k];
+                    }
                 }
                 m_rm = m_r;
                 m_r = mn_c;
@@ -304,8 +376,8 @@ void launch_march6_cyl2(int fp64, const DevSim6 *sims, const DevTile2 *tiles, in
 {
     if (ntiles <= 0) return;
     const int grid = (ntiles + WARPS_C2 - 1) / WARPS_C2;
-    if (fp64) k_cyl2<double, 4><<<grid, WARPS_C2 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
-    else k_cyl2<float, 5><<<grid, WARPS_C2 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
+    if (fp64) k_cyl2<double, 4, CYL2_STG><<<grid, WARPS_C2 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
+    else k_cyl2<float, 5, CYL2_STG><<<grid, WARPS_C2 * 32, 0, st>>>(sims, tiles, ntiles, launch_base, launch_add);
 }
 
 }  // namespace cas
