@@ -76,6 +76,23 @@ __device__ __forceinline__ void st(R *__restrict__ p, int plane, unsigned N, uns
     else p[(unsigned)plane * N + g] = v.x;
 }
 
+// The four Lorentz coefficients [cp, cpm, ce, cd] of one pole and component: a 16-byte aligned
+// group of the table (one load in FP32, two in FP64)
+template <typename R>
+struct Four {
+    R v[4];
+};
+__device__ __forceinline__ Four<float> ld4(const float *__restrict__ p)
+{
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    return Four<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Four<double> ld4(const double *__restrict__ p)
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    return Four<double>{{a.x, a.y, b.x, b.y}};
+}
+
 // Asynchronous global -> shared copies of one element (cp.async, the thread's own data): the
 // staged march keeps the rows in flight in shared memory instead of registers.
 template <typename R>
@@ -325,9 +342,10 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                     V sp = c3[k] * bb;
 #pragma unroll
                     for (int q = 0; q < NPL; ++q) {
-                        const R *lq = l4 + 12 * q;
-                        if (q > 0 && !(q < np && lq[2] != (R)0)) continue;   // pole q absent here
-                        const R ce = lq[2];
+                        if (q > 0 && q >= np) continue;                      // beyond the plan's poles
+                        const Four<R> lq = ld4(l4 + 12 * q);                 // cp, cpm, ce, cd
+                        if (q > 0 && lq.v[2] == (R)0) continue;              // pole q absent here
+                        const R ce = lq.v[2];
                         V p, pm;
                         if (STG > 0 && in.lp) {
                             // slot layout: P then P_prev of pole q, component k, each CF values 32 apart
@@ -338,8 +356,8 @@ k_march6(const DevSim6 *__restrict__ sims, const DevTile *__restrict__ tiles, in
                             p = in.p[3 * q + k];
                             pm = in.pm[3 * q + k];
                         }
-                        const V pn = first_e ? (p * lq[0] + eo[k] * ce) * (R)0.5
-                                             : (p * lq[0] - pm * lq[1] + eo[k] * ce) * lq[3];
+                        const V pn = first_e ? (p * lq.v[0] + eo[k] * ce) * (R)0.5
+                                             : (p * lq.v[0] - pm * lq.v[1] + eo[k] * ce) * lq.v[3];
                         if (wr) {
                             st<R, CPLX>(lout, 6 * q + k, N, g, pn);
                             st<R, CPLX>(lout, 6 * q + 3 + k, N, g, p);
